@@ -1,0 +1,374 @@
+"""Benchmark of the B300-native VMAS world step.
+
+One "step" = one world step (all substeps fused) of every environment of the
+paper-scale workload: 30,000 envs x (16 agent spheres + 4 movable boxes +
+4 fixed line walls), 5 substeps, synthetic seeded scenes and uniform [-1, 1]
+actions.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Timing: W untimed warm-up steps; then K steps, each preceded by an L2 flush
+(a write and then a read of a buffer twice the L2 size, outside the timed
+events) and bracketed by CUDA events on the launching stream; the whole
+region is bracketed by a barrier and a device synchronize.  value = env-steps
+of all ranks / max over ranks of the summed event time.  Multi-GPU: one
+process per GPU (torchrun), each with its own 30,000 envs (weak scaling, no
+collective on the data path).
+
+--impl reference times the FP64 oracle (the plain CPU statement of the
+method) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s on 1 B300, plain fused step vs surrogate at stated error; % roofline"
+UNIT = "env-steps/s"
+# Algorithmic bytes per env-step of the paper-scale workload: state read +
+# write (2 x 24 entities x 6 FP32) + the useful action floats
+# (16 agents x 2 + 4 boxes x 3).
+ENTITIES, AGENTS, BOXES = 24, 16, 4
+B_ALG_PER_ENV = 2 * ENTITIES * 6 * 4 + (AGENTS * 2 + BOXES * 3) * 4  # 1328
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _kernel_digest():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "world_step_paper30k.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel sources sha256[:16]") != _kernel_digest():
+        return None
+    try:
+        return float(fields["dram bytes per launch (read+write)"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """Polls NVML for SM clock and throttle reasons on a background thread."""
+
+    def __init__(self, index, period=0.002):
+        self.samples, self.reasons = [], set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+        self.ok = False
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.period = period
+            self.ok = True
+        except Exception as e:  # pragma: no cover - no NVML here
+            self.err = str(e)
+
+    def _run(self):
+        nv = self.nv
+        names = {
+            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
+            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
+            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
+            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
+            "hw_power_brake_slowdown": getattr(nv, "nvmlClocksEventReasonHwPowerBrakeSlowdown", 0x80),
+        }
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
+                bits = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                for n, b in names.items():
+                    if bits & b:
+                        self.reasons.add(n)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self._t:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(n_envs, substeps, seed, budget_s=12.0):
+    """Oracle (FP64 C, OpenMP over envs) on the host cores, on a bounded
+    sample of the workload: the first E_s envs of the same scene for T_s
+    steps, sized to about `budget_s` seconds."""
+    import oracle
+    from paper_2207_03530_b300 import scenes
+
+    cores = oracle.max_threads()
+    sc = scenes.paper_scene(n_envs, seed, substeps=substeps)
+    probe = sc.subset(np.arange(min(n_envs, 2000)))
+    act = scenes.make_actions(probe, 1, seed)
+    t0 = time.perf_counter()
+    oracle.step(probe, probe.init_state, act, threads=cores)
+    per_env_step = (time.perf_counter() - t0) / probe.n_envs
+    E_s = min(n_envs, max(1, int(budget_s / per_env_step)))
+    T_s = max(1, min(20, int(budget_s / (per_env_step * E_s))))
+    sample = sc.subset(np.arange(E_s))
+    act = scenes.make_actions(sample, T_s, seed)
+    t0 = time.perf_counter()
+    oracle.step(sample, sample.init_state, act, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": E_s * T_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d envs x %d steps of the same workload, FP64, %.1f s"
+                      % (E_s, n_envs, T_s, dt)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is one FP64 world step of
+    the first E_s envs of the same workload on the host cores (state carried
+    across steps), E_s sized so the whole run takes about two minutes."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2207_03530_b300 import scenes
+
+    cores = oracle.max_threads()
+    sc = scenes.paper_scene(args.envs, args.seed, substeps=args.substeps)
+    probe = sc.subset(np.arange(min(args.envs, 1000)))
+    t0 = time.perf_counter()
+    oracle.step(probe, probe.init_state, scenes.make_actions(probe, 1, args.seed), threads=cores)
+    per_env_step = (time.perf_counter() - t0) / probe.n_envs
+    n = args.warmup + args.steps
+    budget = min(20.0, max(0.05, 120.0 / max(1, n)))
+    E_s = int(min(args.envs, max(8, budget / per_env_step)))
+    sample = sc.subset(np.arange(E_s))
+    act = scenes.make_actions(sample, n, args.seed)
+    state = sample.init_state.astype(np.float64)
+    times = []
+    for k in range(n):
+        t0 = time.perf_counter()
+        state = oracle.step(sample, state, act[k], threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = E_s * len(times) / sum(times)
+    base = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d envs of the same workload, %d timed steps, FP64 C + OpenMP"
+                      % (E_s, args.envs, len(times))}
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.envs / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(args), "cpu_baseline": base,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args):
+    return {"workload": "paper-scale plain step: %d envs x (16 agent spheres + 4 movable boxes "
+                        "+ 4 fixed line walls), %d substeps" % (args.envs, args.substeps),
+            "n_envs_per_gpu": args.envs, "entities_per_env": ENTITIES, "substeps": args.substeps,
+            "seed": args.seed, "parallelism": "env-sharded replicas, no collective",
+            "l2": "flushed before every timed step (write+read of 2x L2)"}
+
+
+def run_native(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2207_03530_b300 import World, build, scenes
+
+    build.build()
+    sc = scenes.paper_scene(args.envs, args.seed + rank, substeps=args.substeps)
+    world = World(sc)
+    E, A = sc.n_envs, sc.n_actuated
+    T = args.warmup + args.steps
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + args.seed + rank)
+    actions = torch.rand((T, E, A, 3), device=dev, generator=gen) * 2 - 1
+    props = torch.cuda.get_device_properties(dev)
+    l2 = getattr(props, "L2_cache_size", 126 << 20) or (126 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.zero_()
+        flush.sum()
+
+    for t in range(args.warmup):
+        world.step(actions[t])
+    world.check()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with sampler:
+        for k in range(args.steps):
+            flush_l2()
+            starts[k].record()
+            world.step(actions[args.warmup + k])
+            ends[k].record()
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    world.check()
+    kern_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(kern_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = E * args.steps * ws / (total_ms / 1e3)
+
+    # warm-L2 figure (no flush), for context only
+    torch.cuda.synchronize()
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record()
+    for k in range(args.steps):
+        world.step(actions[args.warmup + k])
+    w1.record()
+    torch.cuda.synchronize()
+    warm = E * args.steps / (w0.elapsed_time(w1) / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned actions up,
+    # kernel, full state back to pinned host memory, every step
+    K2 = min(args.steps, 50)
+    h_act = torch.empty((K2, E, A, 3), dtype=torch.float32).pin_memory()
+    h_act.copy_(actions[args.warmup:args.warmup + K2].cpu())
+    h_state = torch.empty((E, sc.n_entities, 6), dtype=torch.float32).pin_memory()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K2):
+        world.step_host(h_act[k])
+        world.state(out=h_state)  # waits for the copy
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = E * K2 * ws / e2e_s
+
+    peak, peak_kind = _peaks()
+    avg_ms = statistics.mean(kern_ms)
+    achieved = B_ALG_PER_ENV * E / (avg_ms / 1e3) / 1e9
+    traffic = _recorded_traffic()
+    clocks = sampler.summary()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(args),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
+                         "bytes_per_env_step": B_ALG_PER_ENV, "kernel": "world_step_kernel"},
+            "e2e": {"value": e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": int(h_act[0].numel() * 4),
+                    "d2h_bytes_per_step": int(h_state.numel() * 4)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "warm_l2_value": warm,
+            "wall_s_timed_region": wall,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.envs, args.substeps, args.seed)
+        print(json.dumps(line), flush=True)
+    world.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--envs", type=int, default=30000)
+    ap.add_argument("--substeps", type=int, default=5)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.steps > 2:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * vmas.h -- C ABI of the B300-native VMAS world step.
+ *
+ * The library steps many independent 2D worlds ("environments") at once on
+ * one CUDA device.  Each world holds n_entities bodies (spheres, boxes,
+ * lines) with state (x, y, vx, vy, theta, omega); one world step applies the
+ * VMAS core of Bettini et al. (section 3, "Core"):
+ *
+ *   Eq. 1  f_i = f^a_i + m_i g + sum_j f^e_ij,   v <- (1-zeta) v + f/m dt,
+ *          x <- x + v dt                           (semi-implicit Euler)
+ *   Eq. 2  f^e_ij = c k log(1 + exp(-gap/k)) n_ij  when gap <= 0, else 0,
+ *          gap = |x_ij| - d_min between the closest points of i and j
+ *   Eq. 3  tau_i = sum_j r_ij x f^e_ij,  omega <- (1-zeta) omega + tau/I dt,
+ *          theta <- theta + omega dt
+ *
+ * repeated `substeps` times per call with dt / substeps (actions held).
+ * The torque of Eq. 3 is the signed 2D cross product; a box or line pair's
+ * closest points come from its separating-axis penetration, with the
+ * contact point on the incident edge clipped to the reference face.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (VMAS_OK) on success or a negative VMAS_E* code; the message
+ *    of the last failure on the calling thread is vmas_last_error().
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it and the call returns without waiting unless stated.
+ *  - Device pointers are borrowed: they must stay valid until the work
+ *    enqueued on `stream` has finished.  Host pointers are read or written
+ *    before the call returns unless stated.
+ *  - All floating-point data is FP32, little-endian, C order.
+ *  - A world is not thread-safe: serialise calls on one world.
+ */
+#ifndef VMAS_H_
+#define VMAS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VMAS_ABI_VERSION 1
+
+/* Entity shapes (section 3: "Entities have a shape (sphere, box, or line)"). */
+enum { VMAS_SPHERE = 0, VMAS_BOX = 1, VMAS_LINE = 2 };
+
+/* Entity flags (section 3: movable, rotatable, collidable; actuated = takes an
+ * action row).  An entity with none of the bits set is inert padding. */
+enum {
+  VMAS_MOVABLE = 1,
+  VMAS_ROTATABLE = 2,
+  VMAS_COLLIDABLE = 4,
+  VMAS_ACTUATED = 8
+};
+
+/* Status codes. */
+enum {
+  VMAS_OK = 0,
+  VMAS_EINVAL = -1,  /* bad argument or world description              */
+  VMAS_ENOMEM = -2,  /* device or host allocation failed                */
+  VMAS_ECUDA = -3,   /* a CUDA runtime call failed                      */
+  VMAS_EDEVICE = -4  /* a kernel raised its device error word (see below) */
+};
+
+/* Bits of the device error word reported through VMAS_EDEVICE. */
+enum {
+  VMAS_DEVERR_NONFINITE = 1 /* a state value became NaN or Inf */
+};
+
+/* Largest supported entity count per environment. */
+#define VMAS_MAX_ENTITIES 128
+
+typedef struct vmas_world vmas_world; /* opaque, owned by the library */
+
+/* World description, read by vmas_world_create and not kept.
+ * Per-entity arrays are host arrays of n_envs * n_entities elements, entity
+ * index fastest.  The k-th actuated entity of an env (in entity order) reads
+ * action row k; an env may have fewer actuated entities than n_actuated,
+ * never more. */
+typedef struct {
+  int32_t n_envs;      /* >= 0                                            */
+  int32_t n_entities;  /* 1 .. VMAS_MAX_ENTITIES                          */
+  int32_t n_actuated;  /* action rows per env, >= 0                       */
+  int32_t substeps;    /* >= 1                                            */
+  float dt;            /* step length delta t (> 0)                       */
+  float drag;          /* velocity damping zeta, applied every substep     */
+  float gx, gy;        /* gravity g                                        */
+  float contact_force; /* c of Eq. 2 (>= 0)                                */
+  float contact_margin;/* k of Eq. 2 (> 0)                                 */
+  float max_speed;     /* |v| cap applied after the velocity update; 0 = off */
+  const uint8_t *shape;   /* VMAS_SPHERE / VMAS_BOX / VMAS_LINE            */
+  const uint8_t *flags;   /* VMAS_MOVABLE | ...                            */
+  const float *size_a;    /* sphere radius | box width | line length (> 0) */
+  const float *size_b;    /* box height (> 0 for boxes, ignored otherwise) */
+  const float *mass;      /* > 0 for movable entities                      */
+  const float *inertia;   /* moment of inertia; 0 selects box m(w^2+h^2)/12,
+                             line m L^2/12, sphere m r^2/2                 */
+  const float *init_state;/* [n_envs][n_entities][6]: x y vx vy theta omega */
+} vmas_world_desc;
+
+/* Create a world on the current CUDA device: validates the description,
+ * allocates the device state and parameter planes and copies them in
+ * (synchronously).  On failure *out is NULL and nothing is leaked. */
+int vmas_world_create(const vmas_world_desc *desc, vmas_world **out);
+
+/* Free a world and its device memory (waits for the device).  NULL is a
+ * no-op. */
+int vmas_world_destroy(vmas_world *world);
+
+/* Sizes of a world; any pointer may be NULL.  n_pairs = N (N - 1) / 2. */
+int vmas_world_info(const vmas_world *world, int32_t *n_envs, int32_t *n_entities,
+                    int32_t *n_actuated, int32_t *substeps, int32_t *n_pairs);
+
+/* One world step of every environment (section 3, Eqs. 1-3, substeps fused
+ * on chip).  d_actions: device [n_envs][n_actuated][3] (fx, fy, torque); the
+ * torque is applied to rotatable actuated entities only.  May be NULL when
+ * n_actuated == 0.  Enqueues one kernel on `stream`. */
+int vmas_step(vmas_world *world, const float *d_actions, void *stream);
+
+/* As vmas_step with a HOST action array of the same layout: the actions are
+ * copied into a library-owned device buffer on `stream` first.  The host
+ * array must stay valid until that copy has run (pinned memory makes the
+ * copy asynchronous; pageable memory makes it synchronous). */
+int vmas_step_host(vmas_world *world, const float *h_actions, void *stream);
+
+/* T consecutive world steps: d_actions is device [T][n_envs][n_actuated][3].
+ * Enqueues T kernels on `stream`. */
+int vmas_rollout(vmas_world *world, const float *d_actions, int32_t n_steps, void *stream);
+
+/* Read the state into caller memory as [n_envs][n_entities][6]
+ * (x y vx vy theta omega).  out_is_device != 0: `out` is device memory and
+ * the copy is enqueued on `stream`.  out_is_device == 0: `out` is host
+ * memory; the call waits for `stream` and then returns VMAS_EDEVICE if a
+ * kernel has raised the device error word since the last check. */
+int vmas_state(vmas_world *world, float *out, int32_t out_is_device, void *stream);
+
+/* Overwrite the state of the environments selected by env_mask (the reset of
+ * section 3's scenario interface, reset_world_at).  state: [n_envs]
+ * [n_entities][6], device if state_is_device else host.  env_mask: HOST
+ * uint8 [n_envs] (non-zero = reset this env) or NULL for all envs.  Host
+ * inputs are consumed before the call returns. */
+int vmas_set_state(vmas_world *world, const float *state, int32_t state_is_device,
+                   const uint8_t *env_mask, void *stream);
+
+/* First-substep contact mask of the current state: d_mask is device uint8
+ * [n_envs][n_pairs], pairs (i < j) in row-major order; 1 where the pair is
+ * active (both collidable, one movable or rotatable) and gap <= 0 with a
+ * defined normal.  Does not change the state. */
+int vmas_debug_pairs(vmas_world *world, uint8_t *d_mask, void *stream);
+
+/* The canonical pair list into host arrays of n_pairs elements. */
+int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
+
+/* Wait for `stream` and return VMAS_EDEVICE (clearing the word) if a kernel
+ * has raised the device error word since the last check; *bits (may be NULL)
+ * receives the VMAS_DEVERR_* bits seen. */
+int vmas_check(vmas_world *world, void *stream, int32_t *bits);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *vmas_last_error(void);
+
+/* VMAS_ABI_VERSION of the loaded library. */
+int vmas_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMAS_H_ */

@@ -1,0 +1,84 @@
+"""ctypes declarations of the C ABI in include/vmas.h (argument marshalling only).
+
+Loading fails loudly when libvmas.so is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvmas.so")
+
+VMAS_OK, VMAS_EINVAL, VMAS_ENOMEM, VMAS_ECUDA, VMAS_EDEVICE = 0, -1, -2, -3, -4
+MAX_ENTITIES = 128
+ABI_VERSION = 1
+
+# Every symbol include/vmas.h declares.
+SYMBOLS = (
+    "vmas_world_create", "vmas_world_destroy", "vmas_world_info", "vmas_step",
+    "vmas_step_host", "vmas_rollout", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
+    "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
+)
+
+
+class WorldDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_envs", ctypes.c_int32), ("n_entities", ctypes.c_int32),
+        ("n_actuated", ctypes.c_int32), ("substeps", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("drag", ctypes.c_float), ("gx", ctypes.c_float),
+        ("gy", ctypes.c_float), ("contact_force", ctypes.c_float),
+        ("contact_margin", ctypes.c_float), ("max_speed", ctypes.c_float),
+        ("shape", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("size_a", ctypes.c_void_p),
+        ("size_b", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("inertia", ctypes.c_void_p),
+        ("init_state", ctypes.c_void_p),
+    ]
+
+
+class VmasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("vmas error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """The loaded library (ctypes.CDLL) with prototypes set."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libvmas.so is not built (expected at %s); build it with "
+                          "paper_2207_03530_b300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, P = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
+    sig = {
+        "vmas_world_create": ([P(WorldDesc), P(vp)], ctypes.c_int),
+        "vmas_world_destroy": ([vp], ctypes.c_int),
+        "vmas_world_info": ([vp, P(i32), P(i32), P(i32), P(i32), P(i32)], ctypes.c_int),
+        "vmas_step": ([vp, vp, vp], ctypes.c_int),
+        "vmas_step_host": ([vp, vp, vp], ctypes.c_int),
+        "vmas_rollout": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_state": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_set_state": ([vp, vp, i32, vp, vp], ctypes.c_int),
+        "vmas_debug_pairs": ([vp, vp, vp], ctypes.c_int),
+        "vmas_pair_table": ([vp, vp, vp], ctypes.c_int),
+        "vmas_check": ([vp, vp, P(i32)], ctypes.c_int),
+        "vmas_last_error": ([], ctypes.c_char_p),
+        "vmas_abi_version": ([], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    if L.vmas_abi_version() != ABI_VERSION:
+        raise ImportError("libvmas.so ABI %d, binding expects %d" % (L.vmas_abi_version(), ABI_VERSION))
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc != VMAS_OK:
+        raise VmasError(rc, load().vmas_last_error().decode())
+    return rc

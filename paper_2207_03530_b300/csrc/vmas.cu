@@ -1,0 +1,431 @@
+// Host side of the VMAS C ABI (include/vmas.h): world creation, device
+// layout, launches and error handling.  The physics lives in step.cuh and
+// contact.cuh.
+//
+// Device layout of a world (all library-owned, allocated once at create):
+//   state   6 FP32 planes px, py, vx, vy, th, om, each [E * N], env-major
+//           (entity i of env e at e * N + i), so a warp reads an env's plane
+//           as one contiguous run;
+//   phys    float4 [E * N] {m, 1/m or 0, 1/I or 0, 0};
+//   geom    float4 [E * N] {half size a, half size b, bounding radius, 0};
+//   kind    uint8  [E * N] shape | flags << 2;
+//   pairs   uint16 [P] canonical pair list i | j << 8;
+//   err     int32 device error word;
+//   act     FP32 [E * A * 3] staging for host actions;
+//   stage   FP32 [E * N * 6] staging for host state transfers (lazy).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "step.cuh"
+#include "vmas.h"
+
+using vmas::StepParams;
+
+struct vmas_world {
+  int device = 0;
+  int E = 0, N = 0, A = 0, S = 0, P = 0;
+  float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0;
+  float *planes = nullptr;  // 6 * E * N
+  float4 *phys = nullptr;
+  float4 *geom = nullptr;
+  uint8_t *kind = nullptr;
+  uint16_t *pairs = nullptr;
+  int *err = nullptr;
+  float *act = nullptr;
+  float *stage = nullptr;
+  uint8_t *env_mask = nullptr;
+  std::vector<int32_t> pi, pj;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(VMAS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define VMAS_CUDA(call)                          \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void free_world(vmas_world *w) {
+  if (!w) return;
+  cudaFree(w->planes);
+  cudaFree(w->phys);
+  cudaFree(w->geom);
+  cudaFree(w->kind);
+  cudaFree(w->pairs);
+  cudaFree(w->err);
+  cudaFree(w->act);
+  cudaFree(w->stage);
+  cudaFree(w->env_mask);
+  delete w;
+}
+
+StepParams make_params(const vmas_world *w) {
+  StepParams p{};
+  p.E = w->E;
+  p.N = w->N;
+  p.A = w->A;
+  p.S = w->S;
+  p.P = w->P;
+  p.h = (float)((double)w->dt / (double)w->S);
+  p.damp = (float)(1.0 - (double)w->drag);
+  p.gx = w->gx;
+  p.gy = w->gy;
+  p.ck = (float)((double)w->c * (double)w->k);
+  p.inv_k = (float)(1.0 / (double)w->k);
+  p.vmax = w->vmax;
+  const size_t EN = (size_t)w->E * w->N;
+  p.px = w->planes;
+  p.py = w->planes + EN;
+  p.vx = w->planes + 2 * EN;
+  p.vy = w->planes + 3 * EN;
+  p.th = w->planes + 4 * EN;
+  p.om = w->planes + 5 * EN;
+  p.phys = w->phys;
+  p.geom = w->geom;
+  p.kind = w->kind;
+  p.pairs = w->pairs;
+  p.err = w->err;
+  return p;
+}
+
+template <int SLOTS, bool MASK_ONLY>
+int launch_slots(const StepParams &p, cudaStream_t st) {
+  const int smem = vmas::cta_smem_bytes(p.N, p.P);
+  auto kern = vmas::world_step_kernel<SLOTS, MASK_ONLY>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  const int grid = (p.E + vmas::kWarpsPerCta - 1) / vmas::kWarpsPerCta;
+  kern<<<grid, vmas::kWarpsPerCta * 32, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "world_step_kernel launch");
+  return VMAS_OK;
+}
+
+template <bool MASK_ONLY>
+int launch(const StepParams &p, cudaStream_t st) {
+  if (p.E == 0) return VMAS_OK;
+  const int slots = (p.N + 31) / 32;
+  switch (slots) {
+    case 1: return launch_slots<1, MASK_ONLY>(p, st);
+    case 2: return launch_slots<2, MASK_ONLY>(p, st);
+    case 3: return launch_slots<3, MASK_ONLY>(p, st);
+    default: return launch_slots<4, MASK_ONLY>(p, st);
+  }
+}
+
+// [E][N][6] AoS -> planes, for envs whose mask byte is non-zero (or all).
+__global__ void scatter_state_kernel(float *planes, const float *aos, const uint8_t *mask,
+                                     size_t EN, int N) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= EN) return;
+  if (mask && !mask[t / N]) return;
+  for (int f = 0; f < 6; ++f) planes[f * EN + t] = aos[t * 6 + f];
+}
+
+// planes -> [E][N][6] AoS.
+__global__ void gather_state_kernel(float *aos, const float *planes, size_t EN) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= EN) return;
+  for (int f = 0; f < 6; ++f) aos[t * 6 + f] = planes[f * EN + t];
+}
+
+int ensure_stage(vmas_world *w) {
+  if (w->stage) return VMAS_OK;
+  const size_t n = (size_t)w->E * w->N * 6;
+  VMAS_CUDA(cudaMalloc(&w->stage, n * sizeof(float) + 16));
+  return VMAS_OK;
+}
+
+int read_err(vmas_world *w, cudaStream_t st, int32_t *bits) {
+  int h = 0;
+  VMAS_CUDA(cudaMemcpyAsync(&h, w->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VMAS_CUDA(cudaStreamSynchronize(st));
+  if (bits) *bits = h;
+  if (h) {
+    VMAS_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+    VMAS_CUDA(cudaStreamSynchronize(st));
+    return fail(VMAS_EDEVICE, "device error word set (bits " + std::to_string(h) + ")");
+  }
+  return VMAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vmas_last_error(void) { return g_last_error.c_str(); }
+
+int vmas_abi_version(void) { return VMAS_ABI_VERSION; }
+
+int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
+  if (!out) return fail(VMAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(VMAS_EINVAL, "desc is NULL");
+  if (d->n_envs < 0) return fail(VMAS_EINVAL, "n_envs < 0");
+  if (d->n_entities < 1 || d->n_entities > VMAS_MAX_ENTITIES)
+    return fail(VMAS_EINVAL, "n_entities outside 1.." + std::to_string(VMAS_MAX_ENTITIES));
+  if (d->n_actuated < 0) return fail(VMAS_EINVAL, "n_actuated < 0");
+  if (d->substeps < 1) return fail(VMAS_EINVAL, "substeps < 1");
+  if (!(d->dt > 0) || !std::isfinite(d->dt)) return fail(VMAS_EINVAL, "dt must be > 0");
+  if (!std::isfinite(d->drag) || !std::isfinite(d->gx) || !std::isfinite(d->gy))
+    return fail(VMAS_EINVAL, "drag / gravity not finite");
+  if (!(d->contact_force >= 0) || !std::isfinite(d->contact_force))
+    return fail(VMAS_EINVAL, "contact_force must be >= 0");
+  if (!(d->contact_margin > 0) || !std::isfinite(d->contact_margin))
+    return fail(VMAS_EINVAL, "contact_margin must be > 0");
+  if (!(d->max_speed >= 0)) return fail(VMAS_EINVAL, "max_speed must be >= 0");
+  const int E = d->n_envs, N = d->n_entities;
+  const size_t EN = (size_t)E * N;
+  if (EN > 0 && (!d->shape || !d->flags || !d->size_a || !d->size_b || !d->mass ||
+                 !d->inertia || !d->init_state))
+    return fail(VMAS_EINVAL, "a per-entity array is NULL");
+
+  std::vector<float4> phys(EN), geom(EN);
+  std::vector<uint8_t> kind(EN);
+  for (int e = 0; e < E; ++e) {
+    int n_act = 0;
+    for (int i = 0; i < N; ++i) {
+      const size_t t = (size_t)e * N + i;
+      const int sh = d->shape[t];
+      const int fl = d->flags[t];
+      if (sh > 2) return fail(VMAS_EINVAL, "bad shape id at entity " + std::to_string(t));
+      if (fl & ~15) return fail(VMAS_EINVAL, "unknown flag bits at entity " + std::to_string(t));
+      const double a = d->size_a[t], b = d->size_b[t], m = d->mass[t];
+      if (!(a > 0) || !std::isfinite(a))
+        return fail(VMAS_EINVAL, "size_a must be > 0 at entity " + std::to_string(t));
+      if (sh == VMAS_BOX && (!(b > 0) || !std::isfinite(b)))
+        return fail(VMAS_EINVAL, "box size_b must be > 0 at entity " + std::to_string(t));
+      if ((fl & VMAS_MOVABLE) && (!(m > 0) || !std::isfinite(m)))
+        return fail(VMAS_EINVAL, "movable entity needs mass > 0 at " + std::to_string(t));
+      double I = d->inertia[t];
+      if (I == 0) {
+        if (sh == VMAS_BOX) I = m * (a * a + b * b) / 12.0;
+        else if (sh == VMAS_LINE) I = m * a * a / 12.0;
+        else I = 0.5 * m * a * a;
+      }
+      if ((fl & VMAS_ROTATABLE) && (!(I > 0) || !std::isfinite(I)))
+        return fail(VMAS_EINVAL, "rotatable entity needs inertia > 0 at " + std::to_string(t));
+      if (fl & VMAS_ACTUATED) ++n_act;
+      phys[t] = make_float4((float)m, (fl & VMAS_MOVABLE) ? (float)(1.0 / m) : 0.f,
+                            (fl & VMAS_ROTATABLE) ? (float)(1.0 / I) : 0.f, 0.f);
+      double ha, hb, R;
+      if (sh == VMAS_SPHERE) { ha = a; hb = 0; R = a; }
+      else if (sh == VMAS_BOX) { ha = 0.5 * a; hb = 0.5 * b; R = std::sqrt(ha * ha + hb * hb); }
+      else { ha = 0.5 * a; hb = 0; R = ha; }
+      // round the bounding radius up so it never undercuts the shape
+      float Rf = (float)R;
+      if ((double)Rf < R) Rf = std::nextafter(Rf, INFINITY);
+      geom[t] = make_float4((float)ha, (float)hb, Rf, 0.f);
+      kind[t] = (uint8_t)(sh | (fl << 2));
+    }
+    if (n_act > d->n_actuated)
+      return fail(VMAS_EINVAL, "env " + std::to_string(e) + " has more actuated entities (" +
+                                   std::to_string(n_act) + ") than n_actuated");
+  }
+  for (size_t t = 0; t < EN * 6; ++t)
+    if (!std::isfinite(d->init_state[t])) return fail(VMAS_EINVAL, "init_state not finite");
+
+  vmas_world *w = new vmas_world();
+  cudaGetDevice(&w->device);
+  w->E = E;
+  w->N = N;
+  w->A = d->n_actuated;
+  w->S = d->substeps;
+  w->P = N * (N - 1) / 2;
+  w->dt = d->dt;
+  w->drag = d->drag;
+  w->gx = d->gx;
+  w->gy = d->gy;
+  w->c = d->contact_force;
+  w->k = d->contact_margin;
+  w->vmax = d->max_speed;
+  std::vector<uint16_t> pairs(w->P > 0 ? w->P : 1);
+  w->pi.resize(w->P);
+  w->pj.resize(w->P);
+  {
+    int q = 0;
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j, ++q) {
+        pairs[q] = (uint16_t)(i | (j << 8));
+        w->pi[q] = i;
+        w->pj[q] = j;
+      }
+  }
+  std::vector<float> planes(EN * 6);
+  for (size_t t = 0; t < EN; ++t)
+    for (int f = 0; f < 6; ++f) planes[f * EN + t] = d->init_state[t * 6 + f];
+
+  auto alloc = [&](void **ptr, size_t bytes) -> bool {
+    return cudaMalloc(ptr, bytes > 0 ? bytes : 16) == cudaSuccess;
+  };
+  bool ok = alloc((void **)&w->planes, EN * 6 * sizeof(float)) &&
+            alloc((void **)&w->phys, EN * sizeof(float4)) &&
+            alloc((void **)&w->geom, EN * sizeof(float4)) &&
+            alloc((void **)&w->kind, EN) &&
+            alloc((void **)&w->pairs, pairs.size() * sizeof(uint16_t)) &&
+            alloc((void **)&w->err, sizeof(int)) &&
+            alloc((void **)&w->act, (size_t)E * w->A * 3 * sizeof(float)) &&
+            alloc((void **)&w->env_mask, (size_t)E);
+  if (!ok) {
+    cudaGetLastError();
+    free_world(w);
+    return fail(VMAS_ENOMEM, "cudaMalloc failed while creating the world");
+  }
+  cudaError_t e = cudaSuccess;
+  if (EN) {
+    if (e == cudaSuccess) e = cudaMemcpy(w->planes, planes.data(), EN * 6 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w->phys, phys.data(), EN * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w->geom, geom.data(), EN * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w->kind, kind.data(), EN, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(w->pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(w->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_world(w);
+    return cuda_fail(e, "world upload");
+  }
+  *out = w;
+  return VMAS_OK;
+}
+
+int vmas_world_destroy(vmas_world *w) {
+  if (!w) return VMAS_OK;
+  cudaDeviceSynchronize();
+  free_world(w);
+  return VMAS_OK;
+}
+
+int vmas_world_info(const vmas_world *w, int32_t *n_envs, int32_t *n_entities,
+                    int32_t *n_actuated, int32_t *substeps, int32_t *n_pairs) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (n_envs) *n_envs = w->E;
+  if (n_entities) *n_entities = w->N;
+  if (n_actuated) *n_actuated = w->A;
+  if (substeps) *substeps = w->S;
+  if (n_pairs) *n_pairs = w->P;
+  return VMAS_OK;
+}
+
+int vmas_step(vmas_world *w, const float *d_actions, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (w->A > 0 && w->E > 0 && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
+  StepParams p = make_params(w);
+  p.actions = d_actions;
+  return launch<false>(p, as_stream(stream));
+}
+
+int vmas_step_host(vmas_world *w, const float *h_actions, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  const size_t bytes = (size_t)w->E * w->A * 3 * sizeof(float);
+  if (bytes) {
+    if (!h_actions) return fail(VMAS_EINVAL, "h_actions is NULL");
+    VMAS_CUDA(cudaMemcpyAsync(w->act, h_actions, bytes, cudaMemcpyHostToDevice, as_stream(stream)));
+  }
+  return vmas_step(w, w->act, stream);
+}
+
+int vmas_rollout(vmas_world *w, const float *d_actions, int32_t n_steps, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (n_steps < 0) return fail(VMAS_EINVAL, "n_steps < 0");
+  const size_t per = (size_t)w->E * w->A * 3;
+  for (int t = 0; t < n_steps; ++t) {
+    const int rc = vmas_step(w, d_actions ? d_actions + per * t : nullptr, stream);
+    if (rc) return rc;
+  }
+  return VMAS_OK;
+}
+
+int vmas_state(vmas_world *w, float *out, int32_t out_is_device, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  const size_t EN = (size_t)w->E * w->N;
+  if (EN && !out) return fail(VMAS_EINVAL, "out is NULL");
+  cudaStream_t st = as_stream(stream);
+  if (EN) {
+    float *dst = out;
+    if (!out_is_device) {
+      const int rc = ensure_stage(w);
+      if (rc) return rc;
+      dst = w->stage;
+    }
+    gather_state_kernel<<<(unsigned)((EN + 255) / 256), 256, 0, st>>>(dst, w->planes, EN);
+    VMAS_CUDA(cudaGetLastError());
+    if (!out_is_device)
+      VMAS_CUDA(cudaMemcpyAsync(out, w->stage, EN * 6 * sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  if (!out_is_device) return read_err(w, st, nullptr);
+  return VMAS_OK;
+}
+
+int vmas_set_state(vmas_world *w, const float *state, int32_t state_is_device,
+                   const uint8_t *env_mask, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  const size_t EN = (size_t)w->E * w->N;
+  if (!EN) return VMAS_OK;
+  if (!state) return fail(VMAS_EINVAL, "state is NULL");
+  cudaStream_t st = as_stream(stream);
+  const float *src = state;
+  if (!state_is_device) {
+    const int rc = ensure_stage(w);
+    if (rc) return rc;
+    VMAS_CUDA(cudaMemcpyAsync(w->stage, state, EN * 6 * sizeof(float), cudaMemcpyHostToDevice, st));
+    src = w->stage;
+  }
+  const uint8_t *dmask = nullptr;
+  if (env_mask) {
+    VMAS_CUDA(cudaMemcpyAsync(w->env_mask, env_mask, (size_t)w->E, cudaMemcpyHostToDevice, st));
+    dmask = w->env_mask;
+  }
+  scatter_state_kernel<<<(unsigned)((EN + 255) / 256), 256, 0, st>>>(w->planes, src, dmask, EN, w->N);
+  VMAS_CUDA(cudaGetLastError());
+  // host inputs are consumed before returning
+  if (!state_is_device || env_mask) VMAS_CUDA(cudaStreamSynchronize(st));
+  return VMAS_OK;
+}
+
+int vmas_debug_pairs(vmas_world *w, uint8_t *d_mask, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if ((size_t)w->E * w->P && !d_mask) return fail(VMAS_EINVAL, "d_mask is NULL");
+  if (w->P == 0) return VMAS_OK;
+  StepParams p = make_params(w);
+  p.mask = d_mask;
+  return launch<true>(p, as_stream(stream));
+}
+
+int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (w->P && (!pair_i || !pair_j)) return fail(VMAS_EINVAL, "output is NULL");
+  if (w->P) {
+    std::memcpy(pair_i, w->pi.data(), w->P * sizeof(int32_t));
+    std::memcpy(pair_j, w->pj.data(), w->P * sizeof(int32_t));
+  }
+  return VMAS_OK;
+}
+
+int vmas_check(vmas_world *w, void *stream, int32_t *bits) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  return read_err(w, as_stream(stream), bits);
+}
+
+}  // extern "C"

@@ -45,3 +45,30 @@ def make_scene(bodies, *, substeps=1, dt=0.1, drag=0.0, g=(0.0, 0.0), c=100.0, k
     return scenes.Scene(name="custom", n_envs=n_envs, n_entities=N, n_actuated=A,
                         substeps=substeps, dt=dt, drag=drag, gx=g[0], gy=g[1], c=c, k=k,
                         max_speed=max_speed, shape=shape, flags=flags, init_state=st, **arr)
+
+
+def normwise_err(got, ref):
+    """Per state field (x, y, vx, vy, theta, omega): max |got - ref| divided
+    by max(max |ref|, 1e-6); returns the 6 errors."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    out = []
+    for f in range(6):
+        scale = max(np.abs(ref[..., f]).max(initial=0.0), 1e-6)
+        out.append(np.abs(got[..., f] - ref[..., f]).max(initial=0.0) / scale)
+    return np.array(out)
+
+
+@pytest.fixture(scope="session")
+def vmas_lib():
+    """The built CUDA library; GPU tests skip when no GPU is present."""
+    import torch
+
+    from paper_2207_03530_b300 import build
+
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_03530_b300 import _lib
+
+    return _lib.load()
