@@ -137,7 +137,8 @@ class ClockSampler:
 
     def summary(self):
         if not self.ok:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "error": getattr(self, "err", "unavailable")}
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
                 "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
                 "samples": len(self.samples)}
@@ -299,25 +300,39 @@ def run_native(args):
     torch.cuda.synchronize()
     warm = E * args.steps / (w0.elapsed_time(w1) / 1e3)
 
+    if args.stats:
+        world.enable_stats(True)
+        for k in range(args.steps):
+            world.step(actions[args.warmup + k])
+        st = world.stats(reset=True)
+        world.enable_stats(False)
+        n = max(1, st["env_steps"])
+        print("[stats per env-step] " + " ".join("%s=%.3f" % (k, v / n) for k, v in st.items()),
+              file=sys.stderr, flush=True)
+
     # end to end through the C ABI with host buffers: pinned actions up,
     # kernel, full state back to pinned host memory, every step
-    K2 = min(args.steps, 50)
-    h_act = torch.empty((K2, E, A, 3), dtype=torch.float32).pin_memory()
-    h_act.copy_(actions[args.warmup:args.warmup + K2].cpu())
-    h_state = torch.empty((E, sc.n_entities, 6), dtype=torch.float32).pin_memory()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(K2):
-        world.step_host(h_act[k])
-        world.state(out=h_state)  # waits for the copy
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = E * K2 * ws / e2e_s
+    e2e = None
+    if not args.no_e2e:
+        K2 = min(args.steps, 50)
+        h_act = torch.empty((K2, E, A, 3), dtype=torch.float32).pin_memory()
+        h_act.copy_(actions[args.warmup:args.warmup + K2].cpu())
+        h_state = torch.empty((E, sc.n_entities, 6), dtype=torch.float32).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K2):
+            world.step_host(h_act[k])
+            world.state(out=h_state)  # waits for the copy
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": E * K2 * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_act[0].numel() * 4),
+               "d2h_bytes_per_step": int(h_state.numel() * 4)}
 
     peak, peak_kind = _peaks()
     avg_ms = statistics.mean(kern_ms)
@@ -335,9 +350,7 @@ def run_native(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
                          "bytes_per_env_step": B_ALG_PER_ENV, "kernel": "world_step_kernel"},
-            "e2e": {"value": e2e, "unit": UNIT,
-                    "h2d_bytes_per_step": int(h_act[0].numel() * 4),
-                    "d2h_bytes_per_step": int(h_state.numel() * 4)},
+            "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "warm_l2_value": warm,
@@ -362,6 +375,9 @@ def main(argv=None):
     ap.add_argument("--substeps", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
+    ap.add_argument("--stats", action="store_true",
+                    help="print step counters per env-step to stderr (extra pass)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.steps > 2:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -110,6 +110,26 @@ int vmas_world_destroy(vmas_world *world);
 int vmas_world_info(const vmas_world *world, int32_t *n_envs, int32_t *n_entities,
                     int32_t *n_actuated, int32_t *substeps, int32_t *n_pairs);
 
+/* Margin of the per-step contact-candidate list (world units, >= 0).  The
+ * step keeps, for each environment, the pairs whose bounding circles are
+ * within `skin` of touching and rebuilds the list whenever a body has moved
+ * more than skin / 2 since; pairs left out cannot touch, so results do not
+ * depend on the value, only speed does.  Default at create: half the median
+ * bounding radius of the movable entities. */
+int vmas_world_set_skin(vmas_world *world, float skin);
+int vmas_world_get_skin(const vmas_world *world, float *skin);
+
+/* Optional step counters, for tuning (they cost a few atomics per env per
+ * substep while enabled).  vmas_world_get_stats waits for `stream` and
+ * copies VMAS_STATS_COUNT counters into `out`, zeroing them if `reset`:
+ *   [0] env-steps  [1] candidate-list builds  [2] candidates listed
+ *   [3..8] narrow-phase evaluations of sphere-sphere, sphere-box,
+ *          sphere-line, box-box, box-line, line-line candidates
+ *   [9..14] contacts found, same order   [15] env-substeps in full scan */
+#define VMAS_STATS_COUNT 16
+int vmas_world_set_stats(vmas_world *world, int32_t enable);
+int vmas_world_get_stats(vmas_world *world, uint64_t *out, int32_t reset, void *stream);
+
 /* One world step of every environment (section 3, Eqs. 1-3, substeps fused
  * on chip).  d_actions: device [n_envs][n_actuated][3] (fx, fy, torque); the
  * torque is applied to rotatable actuated entities only.  May be NULL when
@@ -154,6 +174,11 @@ int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
  * has raised the device error word since the last check; *bits (may be NULL)
  * receives the VMAS_DEVERR_* bits seen. */
 int vmas_check(vmas_world *world, void *stream, int32_t *bits);
+
+/* Diagnostic: the cosine and sine the step uses for a body angle, for n
+ * device angles d_theta into device d_cos_sin [n][2] (cos, sin); the
+ * library's own range reduction and series, absolute error about 1e-7. */
+int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void *stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *vmas_last_error(void);

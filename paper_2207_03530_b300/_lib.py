@@ -18,7 +18,13 @@ SYMBOLS = (
     "vmas_world_create", "vmas_world_destroy", "vmas_world_info", "vmas_step",
     "vmas_step_host", "vmas_rollout", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
+    "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
+    "vmas_debug_body_axes",
 )
+STATS_COUNT = 16
+STATS_NAMES = ("env_steps", "rebuilds", "candidates",
+               "eval_ss", "eval_sb", "eval_sl", "eval_bb", "eval_bl", "eval_ll",
+               "hits_ss", "hits_sb", "hits_sl", "hits_bb", "hits_bl", "hits_ll", "full_scan")
 
 
 class WorldDesc(ctypes.Structure):
@@ -67,6 +73,11 @@ def load():
         "vmas_check": ([vp, vp, P(i32)], ctypes.c_int),
         "vmas_last_error": ([], ctypes.c_char_p),
         "vmas_abi_version": ([], ctypes.c_int),
+        "vmas_world_set_skin": ([vp, ctypes.c_float], ctypes.c_int),
+        "vmas_world_get_skin": ([vp, P(ctypes.c_float)], ctypes.c_int),
+        "vmas_world_set_stats": ([vp, i32], ctypes.c_int),
+        "vmas_world_get_stats": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_debug_body_axes": ([vp, vp, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -1,23 +1,12 @@
-// Fused VMAS world step kernel (sm_103a, FP32 CUDA cores).
+// Shared pieces of the world step (sm_103a, FP32 CUDA cores): parameters,
+// the pair activity rule, the Eq. 2 magnitude, the exact narrow-phase
+// dispatch, and the first-substep contact-mask kernel (debug path).
 //
-// One warp steps one environment through all S substeps of one world step
-// (VMAS section 3, Eqs. 1-3); state stays in registers and shared memory
-// between substeps and touches HBM once on the way in and once on the way
-// out.
-//
-//   lanes own entities   : entity i lives in lane i % 32, slot i / 32
-//   lanes own pairs      : pair q (canonical i < j, row-major) in lane q % 32
-//   contact sums         : hits are appended, in pair order, to a per-warp
-//                          shared buffer (ballot + popc), then every lane
-//                          adds the records that touch its entities in that
-//                          order -- the same summation order as a serial loop
-//                          over pairs, with no atomics.
-//
-// Broad phase: a pair is skipped when the bounding circles (inflated by a
-// rounding allowance) are apart, or when a line's infinite carrier is
-// farther from the other body's centre than that body's bounding radius.
-// Both tests only skip pairs the narrow phase would reject, so results do
-// not depend on them.
+// Exact rejection inside pair_hit: a pair is skipped when the bounding
+// circles (radii inflated by a rounding allowance of 1e-5 (R + |x| + |y|))
+// are apart, or when a line's infinite carrier is farther from the other
+// body's centre than that body's inflated radius.  Both tests only skip
+// pairs the narrow phase would reject, so results do not depend on them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,8 +16,7 @@
 
 namespace vmas {
 
-constexpr int kWarpsPerCta = 8;  // environments per CTA
-constexpr int kCap = 64;         // buffered contact records per warp
+constexpr int kWarpsPerCta = 8;  // environments per CTA of the mask kernel
 
 // kind byte = shape | flags << 2
 enum : uint32_t {
@@ -46,26 +34,67 @@ struct StepParams {
   float ck;     // c * k
   float inv_k;  // 1 / k
   float vmax;   // 0 = no cap
+  float skin;   // broad-phase margin of the per-step candidate list
   float *px, *py, *vx, *vy, *th, *om;  // state planes [E * N]
-  const float4 *phys;                  // {m, 1/m (0 if fixed), 1/I (0 if not rotatable), 0}
-  const float4 *geom;                  // {ha, hb, bounding radius, 0}
+  const float4 *param;                 // {1/m (0 if fixed), 1/I (0 if not rotatable), ha, hb}
   const uint8_t *kind;                 // [E * N]
   const uint16_t *pairs;               // [P] i | j << 8
   const float *actions;                // [E][A][3]
   uint8_t *mask;                       // [E][P], mask kernel only
   int *err;                            // device error word
+  unsigned long long *stats;           // optional counters, nullptr = off
 };
 
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ inline int warp_smem_bytes(int N) {
-  return 2 * N * 16 + kCap * 16 + kCap * 4;
+
+// Self-checking build (compiled with -DVMAS_CHECKED only): every shared and
+// global index goes through VIDX, which records the first index outside
+// [0, lim) in the error words (bit 2 of word 0; word 1 = code << 20 | index,
+// word 2 = lim) and clamps it to 0 so the access stays inside the buffer.
+#ifdef VMAS_CHECKED
+__device__ __forceinline__ int vmas_checked_index(int idx, int lim, int code, int *err) {
+  if ((unsigned)idx < (unsigned)lim) return idx;
+  atomicOr(err, 2);
+  atomicCAS(err + 1, 0, (code << 20) | (idx & 0xfffff));
+  atomicCAS(err + 2, 0, lim);
+  return 0;
 }
-__host__ __device__ inline int cta_smem_bytes(int N, int P) {
-  return align16(2 * P) + kWarpsPerCta * warp_smem_bytes(N);
-}
+#define VIDX(idx, lim, code) vmas_checked_index((int)(idx), (int)(lim), (code), p.err)
+#else
+#define VIDX(idx, lim, code) (idx)
+#endif
 
 __device__ __forceinline__ bool pair_active(uint32_t ki, uint32_t kj) {
   return (ki & kCollidable) && (kj & kCollidable) && ((ki | kj) & (kMovable | kRotatable));
+}
+
+// cos and sin of a body angle, written out (no library call): Cody-Waite
+// reduction r = th - k pi/2 with pi/2 split in three floats (1.5703125 and
+// 4.8387050628662109e-4 have 8 and 12 significant bits, so k times them is
+// exact for |k| < 2^12), then the Taylor series of sin to r^9 and cos to r^10
+// on |r| <= pi/4 (truncation below 2e-9) and the quadrant k mod 4.  Absolute
+// error about 1e-7.  Shared by every kernel that needs a body frame.
+__device__ __forceinline__ void body_axes(float th, float &c, float &s) {
+  const float k = rintf(th * 0.63661977236758134f);  // 2 / pi
+  float r = fmaf(-k, 1.5703125f, th);
+  r = fmaf(-k, 4.8387050628662109e-4f, r);
+  r = fmaf(-k, -4.3711388286737929e-8f, r);
+  const float z = r * r;
+  const float ps = fmaf(fmaf(fmaf(2.7557319223985891e-6f, z, -1.9841269841269841e-4f), z,
+                             8.3333333333333333e-3f), z, -1.6666666666666667e-1f);
+  const float sr = fmaf(r * z, ps, r);
+  const float pc = fmaf(fmaf(fmaf(fmaf(-2.7557319223985891e-7f, z, 2.4801587301587302e-5f), z,
+                                  -1.3888888888888889e-3f), z, 4.1666666666666667e-2f), z, -0.5f);
+  const float cr = fmaf(z, pc, 1.0f);
+  const int q = ((int)k) & 3;
+  c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
+  s = q == 0 ? sr : (q == 1 ? cr : (q == 2 ? -sr : -cr));
+}
+
+// Diagnostic kernel: body_axes of n angles (for the accuracy test).
+__global__ void body_axes_kernel(const float *th, float *cs, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) body_axes(th[t], cs[2 * t], cs[2 * t + 1]);
 }
 
 // softplus(z) = log(1 + e^z) for z >= 0 without overflow.
@@ -111,181 +140,51 @@ __device__ __forceinline__ bool pair_hit(const float4 bi, const float4 bj, uint3
   return hit_poly_poly(A, B, h);
 }
 
-template <int SLOTS, bool MASK_ONLY>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-    world_step_kernel(const StepParams p) {
+// First-substep contact mask (debug path): one warp per environment, lanes
+// own pairs; writes 1 where the pair is active and its gap is <= 0 with a
+// defined normal, using the same narrow phase as the step kernel.
+template <int SLOTS>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) pair_mask_kernel(const StepParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = p.N, P = p.P;
   uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
   for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *wb = smem + align16(2 * P) + warp * warp_smem_bytes(N);
-  float4 *s_bp = reinterpret_cast<float4 *>(wb);  // {x, y, inflated R, kind}
-  float4 *s_ng = s_bp + N;                         // {cos, sin, ha, hb}
-  float4 *s_rec = s_ng + N;                        // {fx, fy, ti, tj}
-  uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kCap);
+  float4 *s_bp = reinterpret_cast<float4 *>(smem + align16(2 * P) + warp * 32 * N);
+  float4 *s_ng = s_bp + N;
   __syncthreads();
-
   const int e = blockIdx.x * kWarpsPerCta + warp;
   if (e >= p.E) return;
   const size_t eb = (size_t)e * N;
-  const unsigned lt = (1u << lane) - 1u;
-
-  float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
-  float fax[SLOTS], fay[SLOTS], tau[SLOTS], ms[SLOTS], im[SLOTS], iI[SLOTS], ha[SLOTS],
-      hb[SLOTS], rb[SLOTS];
-  uint32_t kd[SLOTS];
-  int act_base = 0;
-#pragma unroll
-  for (int s = 0; s < SLOTS; ++s) {
-    const int i = lane + 32 * s;
-    const bool ok = i < N;
-    kd[s] = ok ? p.kind[eb + i] : 0u;
-    x[s] = ok ? p.px[eb + i] : 0.f;
-    y[s] = ok ? p.py[eb + i] : 0.f;
-    vx[s] = ok ? p.vx[eb + i] : 0.f;
-    vy[s] = ok ? p.vy[eb + i] : 0.f;
-    th[s] = ok ? p.th[eb + i] : 0.f;
-    om[s] = ok ? p.om[eb + i] : 0.f;
-    const float4 ph = ok ? p.phys[eb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 ge = ok ? p.geom[eb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    ms[s] = ph.x;
-    im[s] = ph.y;
-    iI[s] = ph.z;
-    ha[s] = ge.x;
-    hb[s] = ge.y;
-    rb[s] = ge.z;
-    const bool actuated = ok && (kd[s] & kActuated);
-    const unsigned bal = __ballot_sync(0xffffffffu, actuated);
-    const int slot = act_base + __popc(bal & lt);
-    act_base += __popc(bal);
-    fax[s] = fay[s] = tau[s] = 0.f;
-    if (!MASK_ONLY && actuated && slot < p.A) {
-      const float *a = p.actions + ((size_t)e * p.A + slot) * 3;
-      fax[s] = a[0];
-      fay[s] = a[1];
-      tau[s] = (kd[s] & kRotatable) ? a[2] : 0.f;
-    }
-  }
-
-  const int n_sub = MASK_ONLY ? 1 : p.S;
-  for (int sub = 0; sub < n_sub; ++sub) {
-    // publish the substep-start pose
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const int i = lane + 32 * s;
-      if (i < N) {
-        const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
-        s_bp[i] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
-        float sn = 0.f, cs = 1.f;
-        if ((kd[s] & 3u) != kSphere) sincosf(th[s], &sn, &cs);
-        s_ng[i] = make_float4(cs, sn, ha[s], hb[s]);
-      }
-    }
-    __syncwarp();
-
-    // Eq. 1: action + gravity; Eq. 3: action torque
-    float Fx[SLOTS], Fy[SLOTS], T[SLOTS];
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      Fx[s] = fax[s] + ms[s] * p.gx;
-      Fy[s] = fay[s] + ms[s] * p.gy;
-      T[s] = tau[s];
-    }
-
-    int count = 0;
-    auto drain = [&](int n) {
-      for (int c = 0; c < n; ++c) {
-        const float4 r = s_rec[c];
-        const uint32_t ij = s_rij[c];
-        const int ci = (int)(ij & 0xffffu), cj = (int)(ij >> 16);
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const int me = lane + 32 * s;
-          if (me == ci) { Fx[s] += r.x; Fy[s] += r.y; T[s] += r.z; }
-          if (me == cj) { Fx[s] -= r.x; Fy[s] -= r.y; T[s] += r.w; }
-        }
-      }
-    };
-
-    for (int q0 = 0; q0 < P; q0 += 32) {
-      const int q = q0 + lane;
-      bool hit = false;
-      Hit hh;
-      int i = 0, j = 0;
-      if (q < P) {
-        const uint32_t ij = s_pairs[q];
-        i = (int)(ij & 0xffu);
-        j = (int)(ij >> 8);
-        const float4 bi = s_bp[i], bj = s_bp[j];
-        const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
-        if (pair_active(ki, kj)) hit = pair_hit(bi, bj, ki, kj, s_ng, i, j, hh);
-        if (MASK_ONLY) p.mask[(size_t)e * P + q] = hit ? 1 : 0;
-      }
-      if (!MASK_ONLY) {
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        const int nh = __popc(bal);
-        if (count + nh > kCap) {  // warp-uniform
-          __syncwarp();
-          drain(count);
-          __syncwarp();
-          count = 0;
-        }
-        if (hit) {
-          // Eq. 2 magnitude c k log(1 + exp(-g / k)), g <= 0
-          const float mag = p.ck * softplus_pos(-hh.g * p.inv_k);
-          const int slot = count + __popc(bal & lt);
-          s_rec[slot] = make_float4(mag * hh.nx, mag * hh.ny, mag * hh.ti, -mag * hh.tj);
-          s_rij[slot] = (uint32_t)i | ((uint32_t)j << 16);
-        }
-        count += nh;
-      }
-    }
-    if (MASK_ONLY) return;
-    __syncwarp();
-    drain(count);
-    __syncwarp();
-
-    // Eqs. 1 and 3: damped semi-implicit Euler
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      if (kd[s] & kMovable) {
-        vx[s] = p.damp * vx[s] + Fx[s] * im[s] * p.h;
-        vy[s] = p.damp * vy[s] + Fy[s] * im[s] * p.h;
-        if (p.vmax > 0.f) {
-          const float sp = sqrtf(vx[s] * vx[s] + vy[s] * vy[s]);
-          if (sp > p.vmax) {
-            const float sc = p.vmax / sp;
-            vx[s] *= sc;
-            vy[s] *= sc;
-          }
-        }
-        x[s] += vx[s] * p.h;
-        y[s] += vy[s] * p.h;
-      }
-      if (kd[s] & kRotatable) {
-        om[s] = p.damp * om[s] + T[s] * iI[s] * p.h;
-        th[s] += om[s] * p.h;
-      }
-    }
-  }
-
-  bool bad = false;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int i = lane + 32 * s;
     if (i < N) {
-      p.px[eb + i] = x[s];
-      p.py[eb + i] = y[s];
-      p.vx[eb + i] = vx[s];
-      p.vy[eb + i] = vy[s];
-      p.th[eb + i] = th[s];
-      p.om[eb + i] = om[s];
-      bad |= !(isfinite(x[s]) && isfinite(y[s]) && isfinite(vx[s]) && isfinite(vy[s]) &&
-               isfinite(th[s]) && isfinite(om[s]));
+      const uint32_t kd = p.kind[eb + i];
+      const float x = p.px[eb + i], y = p.py[eb + i], th = p.th[eb + i];
+      const float4 pr = p.param[eb + i];
+      const float R = (kd & 3u) == kBox ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
+      const float infl = R + 1e-5f * (R + fabsf(x) + fabsf(y));
+      s_bp[i] = make_float4(x, y, infl, __uint_as_float(kd));
+      float sn = 0.f, cs = 1.f;
+      if ((kd & 3u) != kSphere) body_axes(th, cs, sn);
+      s_ng[i] = make_float4(cs, sn, pr.z, pr.w);
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, 1);
+  __syncwarp();
+  for (int q = lane; q < P; q += 32) {
+    const uint32_t ij = s_pairs[q];
+    const int i = (int)(ij & 0xffu), j = (int)(ij >> 8);
+    const float4 bi = s_bp[i], bj = s_bp[j];
+    const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
+    Hit h;
+    const bool hit = pair_active(ki, kj) && pair_hit(bi, bj, ki, kj, s_ng, i, j, h);
+    p.mask[(size_t)e * P + q] = hit ? 1 : 0;
+  }
+}
+
+__host__ __device__ inline int mask_cta_smem_bytes(int N, int P) {
+  return align16(2 * P) + kWarpsPerCta * 32 * N;
 }
 
 }  // namespace vmas

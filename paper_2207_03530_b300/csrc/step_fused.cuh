@@ -1,0 +1,360 @@
+// Fused VMAS world step kernel (sm_103a, FP32 CUDA cores).
+//
+// One group of G lanes steps one environment through all S substeps of one
+// world step (VMAS section 3, Eqs. 1-3); state stays in registers and shared
+// memory between substeps and touches HBM once on the way in and once on the
+// way out.  32 / G environments share a warp.
+//
+//   entities   entity a lives in lane a % G of its group, slot a / G
+//   candidates once per step (and again only if some body has moved more
+//              than half the skin since) every lane tests the pairs
+//              {a, a + d mod N}, d = 1 .. N/2, of its entities -- each
+//              unordered pair exactly once, the same count for every lane --
+//              against bounding circles grown by the skin (and, for a line
+//              that cannot rotate, its carrier grown by the skin).  Survivors
+//              are compacted, in (lane, slot, d) order, into one list per
+//              environment.  A pair left out is farther apart than its
+//              bounding circles for the rest of the list's life, so the list
+//              never changes results, and the list order does not depend on
+//              the skin.
+//   contacts   per substep the group walks its list G pairs at a time through
+//              the exact narrow phase; hits are appended to a per-env buffer
+//              in list order (ballot + popc) and every lane adds the records
+//              touching its entities in that order: deterministic sums, no
+//              atomics.
+//   fallback   if a lane's list overflows, that environment scans all pairs
+//              in canonical order every substep until the next rebuild.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "step.cuh"
+
+namespace vmas {
+
+#ifndef VMAS_FUSED_WARPS
+#define VMAS_FUSED_WARPS 4
+#endif
+constexpr int kFusedWarps = VMAS_FUSED_WARPS;  // warps per CTA
+#ifndef VMAS_MIN_BLOCKS
+#define VMAS_MIN_BLOCKS 1          // resident CTAs per SM the register budget targets
+#endif
+constexpr int kLaneCand = 16;    // candidate slots per lane
+constexpr int kRecCap = 32;      // buffered contact records per environment
+constexpr int kTypes = 6;        // SS SB SL BB BL LL
+
+// Stats counters (only when StepParams::stats != nullptr).
+enum {
+  kStatEnvSteps = 0,
+  kStatRebuilds = 1,
+  kStatCandidates = 2,
+  kStatEval = 3,   // + type, narrow-phase evaluations
+  kStatHits = 9,   // + type, contacts
+  kStatFullScan = 15,
+  kStatCount = 16
+};
+
+__host__ __device__ inline int fused_env_bytes(int N, int G) {
+  return 32 * N + kRecCap * 20 + 2 * align16(2 * G * kLaneCand);
+}
+__host__ __device__ inline int fused_cta_smem_bytes(int N, int P, int G) {
+  return align16(2 * P) + kFusedWarps * (32 / G) * fused_env_bytes(N, G);
+}
+
+// Shape-pair class of two shape ids: SS 0, SB 1, SL 2, BB 3, BL 4, LL 5.
+__device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
+  const uint32_t lo = sa < sb ? sa : sb, hi = sa < sb ? sb : sa;
+  return lo == 0u ? (int)hi : (lo == 1u ? 2 + (int)hi : 5);
+}
+
+template <int G, int SLOTS>
+__global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
+    world_step_kernel(const StepParams p) {
+  constexpr int EPW = 32 / G;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = p.N, P = p.P;
+  uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
+  for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / G, lg = lane % G;
+  const int LC = G * kLaneCand;  // candidate capacity per env
+  (void)LC;
+  const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(N, G);
+  float4 *s_bp = reinterpret_cast<float4 *>(es);  // {x, y, inflated R, kind}
+  float4 *s_ng = s_bp + N;                         // {cos, sin, ha, hb}
+  float4 *s_rec = s_ng + N;                        // {fx, fy, ti, tj}
+  uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kRecCap);
+  uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rij + kRecCap);  // [G][kLaneCand]
+  uint16_t *s_cand = s_lc + align16(2 * G * kLaneCand) / 2;          // compact list
+  __syncthreads();
+
+  const int e = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+  const bool valid = e < p.E;
+  const size_t eb = (size_t)e * N;
+  unsigned long long *const stats = p.stats;
+
+  float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
+  float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
+  float xr[SLOTS], yr[SLOTS];
+  uint32_t kd[SLOTS];
+  int act_base = 0;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int a = lg + G * s;
+    const bool ok = valid && a < N;
+    const size_t ga_ = ok ? VIDX(eb + a, (size_t)p.E * N, 1) : 0;
+    kd[s] = ok ? p.kind[ga_] : 0u;
+    x[s] = ok ? p.px[ga_] : 0.f;
+    y[s] = ok ? p.py[ga_] : 0.f;
+    vx[s] = ok ? p.vx[ga_] : 0.f;
+    vy[s] = ok ? p.vy[ga_] : 0.f;
+    th[s] = ok ? p.th[ga_] : 0.f;
+    om[s] = ok ? p.om[ga_] : 0.f;
+    const float4 pr = ok ? p.param[ga_] : make_float4(0.f, 0.f, 0.f, 0.f);
+    im[s] = pr.x;
+    iI[s] = pr.y;
+    const uint32_t sh = kd[s] & 3u;
+    rb[s] = sh == kBox ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
+    if (ok) {
+      float c = 1.f, sn = 0.f;
+      if (sh != kSphere) body_axes(th[s], c, sn);
+      s_ng[VIDX(a, N, 2)] = make_float4(c, sn, pr.z, pr.w);  // {cos, sin, ha, hb}
+    }
+    // the k-th actuated entity of the env (entity order = slot-major) reads row k
+    const bool actuated = ok && (kd[s] & kActuated);
+    const unsigned gb = __ballot_sync(FULL, actuated) & gbits;
+    const int row = act_base + __popc(gb & lt);
+    act_base += __popc(gb);
+    float fax = 0.f, fay = 0.f;
+    tau[s] = 0.f;
+    if (actuated && row < p.A) {
+      const float *ap = p.actions + (size_t)VIDX((size_t)e * p.A + row, (size_t)p.E * p.A, 3) * 3;
+      fax = ap[0];
+      fay = ap[1];
+      tau[s] = (kd[s] & kRotatable) ? ap[2] : 0.f;
+    }
+    // Eq. 1: action + gravity, constant over the step (only movable bodies
+    // integrate, so only their mass matters)
+    const float m = im[s] > 0.f ? 1.f / im[s] : 0.f;
+    fbx[s] = fax + m * p.gx;
+    fby[s] = fay + m * p.gy;
+  }
+
+  const float half_skin = 0.5f * p.skin;
+  const float move2 = (0.499f * p.skin) * (0.499f * p.skin);
+  bool full = false;    // group scans all pairs (list overflow)
+  int ncand = 0;        // list length (group-uniform)
+  bool rebuild = true;  // warp-uniform
+
+  for (int sub = 0; sub < p.S; ++sub) {
+    // publish the substep-start pose
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int a = lg + G * s;
+      if (valid && a < N) {
+        if (sub > 0 && (kd[s] & kRotatable) && (kd[s] & 3u) != kSphere) {
+          float c, sn;
+          body_axes(th[s], c, sn);
+          *reinterpret_cast<float2 *>(&s_ng[VIDX(a, N, 4)]) = make_float2(c, sn);
+        }
+        const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
+        s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
+      }
+    }
+    __syncwarp();
+
+    if (rebuild) {
+      // candidate list: pairs {a, a + d mod N}, each unordered pair once
+      int n = 0;
+      bool over = false;
+      if (valid) {
+        const int dmax = (N - 1) / 2;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int a = lg + G * s;
+          if (a >= N) continue;
+          const float4 ba = s_bp[VIDX(a, N, 6)];
+          const float4 ga = s_ng[VIDX(a, N, 7)];
+          const uint32_t ka = kd[s];
+          const bool a_line = (ka & 3u) == kLine && !(ka & kRotatable);
+          const float ra = ba.z + half_skin;
+          const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
+#pragma unroll 2
+          for (int d = 1; d <= dlast; ++d) {
+            int b = a + d;
+            if (b >= N) b -= N;
+            const float4 bb = s_bp[VIDX(b, N, 8)];
+            const uint32_t kb = __float_as_uint(bb.w);
+            if (!pair_active(ka, kb)) continue;
+            const float dx = ba.x - bb.x, dy = ba.y - bb.y;
+            const float lim = ra + bb.z + half_skin;
+            if (dx * dx + dy * dy > lim * lim) continue;
+            if ((kb & 3u) == kLine && !(kb & kRotatable)) {
+              const float4 gb4 = s_ng[VIDX(b, N, 9)];
+              if (fabsf(dx * gb4.y - dy * gb4.x) >
+                  ba.z + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
+                continue;
+            }
+            if (a_line && fabsf(dx * ga.y - dy * ga.x) >
+                              bb.z + p.skin + 1e-5f * (fabsf(ba.x) + fabsf(ba.y)))
+              continue;
+            if (n < kLaneCand) {
+              const int lo = a < b ? a : b, hi = a < b ? b : a;
+              s_lc[VIDX(lg * kLaneCand + n, LC, 10)] = (uint16_t)(lo | (hi << 8));
+            } else {
+              over = true;
+            }
+            ++n;
+          }
+        }
+      }
+      // compact the lane lists in lane order
+      const int cnt = n < kLaneCand ? n : kLaneCand;
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o, G);
+        if (lg >= o) incl += v;
+      }
+      const int total = __shfl_sync(FULL, incl, G - 1, G);
+      for (int k = 0, off = incl - cnt; k < cnt; ++k)
+        s_cand[VIDX(off + k, LC, 15)] = s_lc[VIDX(lg * kLaneCand + k, LC, 12)];
+      // every lane votes (a warp-wide vote skipped by some lanes is undefined)
+      const unsigned over_bits = __ballot_sync(FULL, over);
+      full = valid && (over_bits & gbits) != 0u;
+      ncand = valid ? (full ? P : total) : 0;
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        xr[s] = x[s];
+        yr[s] = y[s];
+      }
+      if (stats && valid && lg == 0) {
+        atomicAdd(stats + kStatRebuilds, 1ull);
+        atomicAdd(stats + kStatCandidates, (unsigned long long)total);
+      }
+      __syncwarp();
+    }
+
+    // Eq. 1: action + gravity; Eq. 3: action torque
+    float Fx[SLOTS], Fy[SLOTS], T[SLOTS];
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      Fx[s] = fbx[s];
+      Fy[s] = fby[s];
+      T[s] = tau[s];
+    }
+    auto drain = [&](int n) {
+      const int nmax = (int)__reduce_max_sync(FULL, (unsigned)n);
+      for (int c = 0; c < nmax; ++c) {
+        if (c < n) {
+          const float4 r = s_rec[VIDX(c, kRecCap, 16)];
+          const uint32_t ij = s_rij[VIDX(c, kRecCap, 17)];
+          const int ci = (int)(ij & 0xffffu), cj = (int)(ij >> 16);
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) {
+            const int me = lg + G * s;
+            if (me == ci) { Fx[s] += r.x; Fy[s] += r.y; T[s] += r.z; }
+            if (me == cj) { Fx[s] -= r.x; Fy[s] -= r.y; T[s] += r.w; }
+          }
+        }
+      }
+    };
+
+    int count = 0;
+    const int iters = (int)__reduce_max_sync(FULL, (unsigned)((ncand + G - 1) / G));
+    if (stats && lg == 0 && full) atomicAdd(stats + kStatFullScan, 1ull);
+    for (int k = 0; k < iters; ++k) {
+      const int c = k * G + lg;
+      bool hit = false;
+      Hit hh;
+      int i = 0, j = 0;
+      if (c < ncand) {
+        const uint32_t ij = full ? s_pairs[VIDX(c, P, 21)] : s_cand[VIDX(c, LC, 20)];
+        i = VIDX((int)(ij & 0xffu), N, 22);
+        j = VIDX((int)(ij >> 8), N, 23);
+        const float4 bi = s_bp[i], bj = s_bp[j];
+        const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
+        if (pair_active(ki, kj)) {
+          hit = pair_hit(bi, bj, ki, kj, s_ng, i, j, hh);
+          if (stats) {
+            const int t = pair_type(ki & 3u, kj & 3u);
+            atomicAdd(stats + kStatEval + t, 1ull);
+            if (hit) atomicAdd(stats + kStatHits + t, 1ull);
+          }
+        }
+      }
+      const unsigned gb = __ballot_sync(FULL, hit) & gbits;
+      const int nh = __popc(gb);
+      if (__any_sync(FULL, count + nh > kRecCap)) {
+        __syncwarp();
+        drain(count);
+        __syncwarp();
+        count = 0;
+      }
+      if (hit) {
+        // Eq. 2 magnitude c k log(1 + exp(-g / k)), g <= 0
+        const float mag = p.ck * softplus_pos(-hh.g * p.inv_k);
+        const int slot = count + __popc(gb & lt);
+        s_rec[VIDX(slot, kRecCap, 24)] = make_float4(mag * hh.nx, mag * hh.ny, mag * hh.ti, -mag * hh.tj);
+        s_rij[VIDX(slot, kRecCap, 25)] = (uint32_t)i | ((uint32_t)j << 16);
+      }
+      count += nh;
+    }
+    __syncwarp();
+    drain(count);
+    __syncwarp();
+
+    // Eqs. 1 and 3: damped semi-implicit Euler
+    bool moved = false;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      if (kd[s] & kMovable) {
+        vx[s] = p.damp * vx[s] + Fx[s] * im[s] * p.h;
+        vy[s] = p.damp * vy[s] + Fy[s] * im[s] * p.h;
+        if (p.vmax > 0.f) {
+          const float sp = sqrtf(vx[s] * vx[s] + vy[s] * vy[s]);
+          if (sp > p.vmax) {
+            const float sc = p.vmax / sp;
+            vx[s] *= sc;
+            vy[s] *= sc;
+          }
+        }
+        x[s] += vx[s] * p.h;
+        y[s] += vy[s] * p.h;
+        const float ddx = x[s] - xr[s], ddy = y[s] - yr[s];
+        moved |= ddx * ddx + ddy * ddy > move2;
+      }
+      if (kd[s] & kRotatable) {
+        om[s] = p.damp * om[s] + T[s] * iI[s] * p.h;
+        th[s] += om[s] * p.h;
+      }
+    }
+    rebuild = __any_sync(FULL, moved);
+    __syncwarp();
+  }
+
+  bool bad = false;
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    const int a = lg + G * s;
+    if (valid && a < N) {
+      const size_t go_ = VIDX(eb + a, (size_t)p.E * N, 26);
+      p.px[go_] = x[s];
+      p.py[go_] = y[s];
+      p.vx[go_] = vx[s];
+      p.vy[go_] = vy[s];
+      p.th[go_] = th[s];
+      p.om[go_] = om[s];
+      bad |= !(isfinite(x[s]) && isfinite(y[s]) && isfinite(vx[s]) && isfinite(vy[s]) &&
+               isfinite(th[s]) && isfinite(om[s]));
+    }
+  }
+  if (stats && valid && lg == 0) atomicAdd(stats + kStatEnvSteps, 1ull);
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, 1);  // VMAS_DEVERR_NONFINITE
+}
+
+}  // namespace vmas

@@ -1,13 +1,13 @@
 // Host side of the VMAS C ABI (include/vmas.h): world creation, device
-// layout, launches and error handling.  The physics lives in step.cuh and
-// contact.cuh.
+// layout, launches and error handling.  The physics lives in step_fused.cuh,
+// step.cuh and contact.cuh.
 //
 // Device layout of a world (all library-owned, allocated once at create):
 //   state   6 FP32 planes px, py, vx, vy, th, om, each [E * N], env-major
 //           (entity i of env e at e * N + i), so a warp reads an env's plane
 //           as one contiguous run;
-//   phys    float4 [E * N] {m, 1/m or 0, 1/I or 0, 0};
-//   geom    float4 [E * N] {half size a, half size b, bounding radius, 0};
+//   param   float4 [E * N] {1/m or 0, 1/I or 0, half size a, half size b}
+//           (sphere: r, 0; box: w/2, h/2; line: L/2, 0);
 //   kind    uint8  [E * N] shape | flags << 2;
 //   pairs   uint16 [P] canonical pair list i | j << 8;
 //   err     int32 device error word;
@@ -15,6 +15,7 @@
 //   stage   FP32 [E * N * 6] staging for host state transfers (lazy).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -22,8 +23,10 @@
 #include <string>
 #include <vector>
 
-#include "step.cuh"
+#include "step_fused.cuh"
 #include "vmas.h"
+
+static_assert(vmas::kStatCount == VMAS_STATS_COUNT, "stats layout");
 
 using vmas::StepParams;
 
@@ -31,9 +34,10 @@ struct vmas_world {
   int device = 0;
   int E = 0, N = 0, A = 0, S = 0, P = 0;
   float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0;
+  float skin = 0;  // candidate-list margin
   float *planes = nullptr;  // 6 * E * N
-  float4 *phys = nullptr;
-  float4 *geom = nullptr;
+  float4 *param = nullptr;
+  unsigned long long *stats = nullptr;  // optional step counters
   uint8_t *kind = nullptr;
   uint16_t *pairs = nullptr;
   int *err = nullptr;
@@ -67,8 +71,8 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 void free_world(vmas_world *w) {
   if (!w) return;
   cudaFree(w->planes);
-  cudaFree(w->phys);
-  cudaFree(w->geom);
+  cudaFree(w->param);
+  cudaFree(w->stats);
   cudaFree(w->kind);
   cudaFree(w->pairs);
   cudaFree(w->err);
@@ -92,6 +96,7 @@ StepParams make_params(const vmas_world *w) {
   p.ck = (float)((double)w->c * (double)w->k);
   p.inv_k = (float)(1.0 / (double)w->k);
   p.vmax = w->vmax;
+  p.skin = w->skin;
   const size_t EN = (size_t)w->E * w->N;
   p.px = w->planes;
   p.py = w->planes + EN;
@@ -99,18 +104,58 @@ StepParams make_params(const vmas_world *w) {
   p.vy = w->planes + 3 * EN;
   p.th = w->planes + 4 * EN;
   p.om = w->planes + 5 * EN;
-  p.phys = w->phys;
-  p.geom = w->geom;
+  p.param = w->param;
+  p.stats = w->stats;
   p.kind = w->kind;
   p.pairs = w->pairs;
   p.err = w->err;
   return p;
 }
 
-template <int SLOTS, bool MASK_ONLY>
-int launch_slots(const StepParams &p, cudaStream_t st) {
-  const int smem = vmas::cta_smem_bytes(p.N, p.P);
-  auto kern = vmas::world_step_kernel<SLOTS, MASK_ONLY>;
+template <int G, int SLOTS>
+int launch_step_gs(const StepParams &p, cudaStream_t st) {
+  const int smem = vmas::fused_cta_smem_bytes(p.N, p.P, G);
+  auto kern = vmas::world_step_kernel<G, SLOTS>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  const int envs_per_cta = vmas::kFusedWarps * (32 / G);
+  const int grid = (p.E + envs_per_cta - 1) / envs_per_cta;
+  kern<<<grid, vmas::kFusedWarps * 32, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "world_step_kernel launch");
+  return VMAS_OK;
+}
+
+template <int G>
+int launch_step_g(const StepParams &p, cudaStream_t st) {
+  switch ((p.N + G - 1) / G) {
+    case 1: return launch_step_gs<G, 1>(p, st);
+    case 2: return launch_step_gs<G, 2>(p, st);
+    case 3: return launch_step_gs<G, 3>(p, st);
+    default: return launch_step_gs<G, 4>(p, st);
+  }
+}
+
+// Lanes per environment: the smallest group that holds every entity in at
+// most 4 slots (N <= 8: 4 lanes, <= 32: 8, <= 64: 16, else 32).
+int group_lanes(int N) { return N <= 8 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : 32; }
+
+int launch_step(const StepParams &p, cudaStream_t st) {
+  if (p.E == 0) return VMAS_OK;
+  switch (group_lanes(p.N)) {
+    case 4: return launch_step_g<4>(p, st);
+    case 8: return launch_step_g<8>(p, st);
+    case 16: return launch_step_g<16>(p, st);
+    default: return launch_step_g<32>(p, st);
+  }
+}
+
+template <int SLOTS>
+int launch_mask_s(const StepParams &p, cudaStream_t st) {
+  const int smem = vmas::mask_cta_smem_bytes(p.N, p.P);
+  auto kern = vmas::pair_mask_kernel<SLOTS>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -118,19 +163,17 @@ int launch_slots(const StepParams &p, cudaStream_t st) {
   const int grid = (p.E + vmas::kWarpsPerCta - 1) / vmas::kWarpsPerCta;
   kern<<<grid, vmas::kWarpsPerCta * 32, smem, st>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "world_step_kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, "pair_mask_kernel launch");
   return VMAS_OK;
 }
 
-template <bool MASK_ONLY>
-int launch(const StepParams &p, cudaStream_t st) {
+int launch_mask(const StepParams &p, cudaStream_t st) {
   if (p.E == 0) return VMAS_OK;
-  const int slots = (p.N + 31) / 32;
-  switch (slots) {
-    case 1: return launch_slots<1, MASK_ONLY>(p, st);
-    case 2: return launch_slots<2, MASK_ONLY>(p, st);
-    case 3: return launch_slots<3, MASK_ONLY>(p, st);
-    default: return launch_slots<4, MASK_ONLY>(p, st);
+  switch ((p.N + 31) / 32) {
+    case 1: return launch_mask_s<1>(p, st);
+    case 2: return launch_mask_s<2>(p, st);
+    case 3: return launch_mask_s<3>(p, st);
+    default: return launch_mask_s<4>(p, st);
   }
 }
 
@@ -201,7 +244,8 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
                  !d->inertia || !d->init_state))
     return fail(VMAS_EINVAL, "a per-entity array is NULL");
 
-  std::vector<float4> phys(EN), geom(EN);
+  std::vector<float4> param(EN);
+  std::vector<float> bound_r(EN);
   std::vector<uint8_t> kind(EN);
   for (int e = 0; e < E; ++e) {
     int n_act = 0;
@@ -227,16 +271,13 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
       if ((fl & VMAS_ROTATABLE) && (!(I > 0) || !std::isfinite(I)))
         return fail(VMAS_EINVAL, "rotatable entity needs inertia > 0 at " + std::to_string(t));
       if (fl & VMAS_ACTUATED) ++n_act;
-      phys[t] = make_float4((float)m, (fl & VMAS_MOVABLE) ? (float)(1.0 / m) : 0.f,
-                            (fl & VMAS_ROTATABLE) ? (float)(1.0 / I) : 0.f, 0.f);
-      double ha, hb, R;
-      if (sh == VMAS_SPHERE) { ha = a; hb = 0; R = a; }
-      else if (sh == VMAS_BOX) { ha = 0.5 * a; hb = 0.5 * b; R = std::sqrt(ha * ha + hb * hb); }
-      else { ha = 0.5 * a; hb = 0; R = ha; }
-      // round the bounding radius up so it never undercuts the shape
-      float Rf = (float)R;
-      if ((double)Rf < R) Rf = std::nextafter(Rf, INFINITY);
-      geom[t] = make_float4((float)ha, (float)hb, Rf, 0.f);
+      double ha, hb;
+      if (sh == VMAS_SPHERE) { ha = a; hb = 0; }
+      else if (sh == VMAS_BOX) { ha = 0.5 * a; hb = 0.5 * b; }
+      else { ha = 0.5 * a; hb = 0; }
+      param[t] = make_float4((fl & VMAS_MOVABLE) ? (float)(1.0 / m) : 0.f,
+                             (fl & VMAS_ROTATABLE) ? (float)(1.0 / I) : 0.f, (float)ha, (float)hb);
+      bound_r[t] = (float)std::sqrt(ha * ha + hb * hb);
       kind[t] = (uint8_t)(sh | (fl << 2));
     }
     if (n_act > d->n_actuated)
@@ -260,6 +301,20 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
   w->c = d->contact_force;
   w->k = d->contact_margin;
   w->vmax = d->max_speed;
+  {
+    // candidate-list margin: half the median bounding radius of the movable
+    // entities (any value >= 0 gives the same results; this one balances
+    // list length against rebuilds)
+    std::vector<float> r;
+    for (size_t t = 0; t < EN; ++t)
+      if (d->flags[t] & VMAS_MOVABLE) r.push_back(bound_r[t]);
+    float med = 0.05f;
+    if (!r.empty()) {
+      std::nth_element(r.begin(), r.begin() + r.size() / 2, r.end());
+      med = r[r.size() / 2];
+    }
+    w->skin = 0.5f * med;
+  }
   std::vector<uint16_t> pairs(w->P > 0 ? w->P : 1);
   w->pi.resize(w->P);
   w->pj.resize(w->P);
@@ -280,11 +335,10 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
     return cudaMalloc(ptr, bytes > 0 ? bytes : 16) == cudaSuccess;
   };
   bool ok = alloc((void **)&w->planes, EN * 6 * sizeof(float)) &&
-            alloc((void **)&w->phys, EN * sizeof(float4)) &&
-            alloc((void **)&w->geom, EN * sizeof(float4)) &&
+            alloc((void **)&w->param, EN * sizeof(float4)) &&
             alloc((void **)&w->kind, EN) &&
             alloc((void **)&w->pairs, pairs.size() * sizeof(uint16_t)) &&
-            alloc((void **)&w->err, sizeof(int)) &&
+            alloc((void **)&w->err, 4 * sizeof(int)) &&
             alloc((void **)&w->act, (size_t)E * w->A * 3 * sizeof(float)) &&
             alloc((void **)&w->env_mask, (size_t)E);
   if (!ok) {
@@ -295,13 +349,12 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
   cudaError_t e = cudaSuccess;
   if (EN) {
     if (e == cudaSuccess) e = cudaMemcpy(w->planes, planes.data(), EN * 6 * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(w->phys, phys.data(), EN * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(w->geom, geom.data(), EN * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w->param, param.data(), EN * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(w->kind, kind.data(), EN, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess)
     e = cudaMemcpy(w->pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(w->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(w->err, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
     free_world(w);
     return cuda_fail(e, "world upload");
@@ -314,6 +367,45 @@ int vmas_world_destroy(vmas_world *w) {
   if (!w) return VMAS_OK;
   cudaDeviceSynchronize();
   free_world(w);
+  return VMAS_OK;
+}
+
+int vmas_world_set_skin(vmas_world *w, float skin) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (!(skin >= 0) || !std::isfinite(skin)) return fail(VMAS_EINVAL, "skin must be >= 0");
+  w->skin = skin;
+  return VMAS_OK;
+}
+
+int vmas_world_get_skin(const vmas_world *w, float *skin) {
+  if (!w || !skin) return fail(VMAS_EINVAL, "NULL argument");
+  *skin = w->skin;
+  return VMAS_OK;
+}
+
+int vmas_world_set_stats(vmas_world *w, int32_t enable) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (!enable) {
+    cudaFree(w->stats);
+    w->stats = nullptr;
+    return VMAS_OK;
+  }
+  if (!w->stats) {
+    VMAS_CUDA(cudaMalloc(&w->stats, VMAS_STATS_COUNT * sizeof(unsigned long long)));
+    VMAS_CUDA(cudaMemset(w->stats, 0, VMAS_STATS_COUNT * sizeof(unsigned long long)));
+  }
+  return VMAS_OK;
+}
+
+int vmas_world_get_stats(vmas_world *w, uint64_t *out, int32_t reset, void *stream) {
+  if (!w || !out) return fail(VMAS_EINVAL, "NULL argument");
+  if (!w->stats) return fail(VMAS_EINVAL, "stats are not enabled");
+  cudaStream_t st = as_stream(stream);
+  VMAS_CUDA(cudaMemcpyAsync(out, w->stats, VMAS_STATS_COUNT * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st));
+  if (reset)
+    VMAS_CUDA(cudaMemsetAsync(w->stats, 0, VMAS_STATS_COUNT * sizeof(unsigned long long), st));
+  VMAS_CUDA(cudaStreamSynchronize(st));
   return VMAS_OK;
 }
 
@@ -333,7 +425,7 @@ int vmas_step(vmas_world *w, const float *d_actions, void *stream) {
   if (w->A > 0 && w->E > 0 && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
   StepParams p = make_params(w);
   p.actions = d_actions;
-  return launch<false>(p, as_stream(stream));
+  return launch_step(p, as_stream(stream));
 }
 
 int vmas_step_host(vmas_world *w, const float *h_actions, void *stream) {
@@ -410,7 +502,7 @@ int vmas_debug_pairs(vmas_world *w, uint8_t *d_mask, void *stream) {
   if (w->P == 0) return VMAS_OK;
   StepParams p = make_params(w);
   p.mask = d_mask;
-  return launch<true>(p, as_stream(stream));
+  return launch_mask(p, as_stream(stream));
 }
 
 int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
@@ -420,6 +512,23 @@ int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
     std::memcpy(pair_i, w->pi.data(), w->P * sizeof(int32_t));
     std::memcpy(pair_j, w->pj.data(), w->P * sizeof(int32_t));
   }
+  return VMAS_OK;
+}
+
+#ifdef VMAS_CHECKED
+// Self-checking build only: the error words {bits, first bad index, limit}.
+int vmas_debug_err_words(vmas_world *w, int32_t *out) {
+  if (!w || !out) return VMAS_EINVAL;
+  cudaDeviceSynchronize();
+  return cudaMemcpy(out, w->err, 3 * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : VMAS_ECUDA;
+}
+#endif
+
+int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void *stream) {
+  if (n < 0 || (n > 0 && (!d_theta || !d_cos_sin))) return fail(VMAS_EINVAL, "bad arguments");
+  if (n == 0) return VMAS_OK;
+  vmas::body_axes_kernel<<<(n + 255) / 256, 256, 0, as_stream(stream)>>>(d_theta, d_cos_sin, n);
+  VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
 }
 

@@ -146,6 +146,28 @@ class World:
         _lib.check(self._L.vmas_pair_table(self._handle(), pi.ctypes.data, pj.ctypes.data))
         return pi[: self.n_pairs], pj[: self.n_pairs]
 
+    @property
+    def skin(self) -> float:
+        """Margin of the per-step contact-candidate list (speed only)."""
+        v = ctypes.c_float()
+        _lib.check(self._L.vmas_world_get_skin(self._handle(), ctypes.byref(v)))
+        return v.value
+
+    @skin.setter
+    def skin(self, value: float) -> None:
+        _lib.check(self._L.vmas_world_set_skin(self._handle(), float(value)))
+
+    def enable_stats(self, on: bool = True) -> None:
+        """Turn the step counters on or off (tuning aid; costs atomics)."""
+        _lib.check(self._L.vmas_world_set_stats(self._handle(), 1 if on else 0))
+
+    def stats(self, reset: bool = False, stream=None) -> dict:
+        """The step counters as a dict (see include/vmas.h)."""
+        out = np.zeros(_lib.STATS_COUNT, np.uint64)
+        _lib.check(self._L.vmas_world_get_stats(self._handle(), out.ctypes.data, 1 if reset else 0,
+                                                _stream_handle(stream)))
+        return dict(zip(_lib.STATS_NAMES, (int(v) for v in out)))
+
     def check(self, stream=None) -> int:
         """Wait for the stream; raise if a kernel set the device error word."""
         bits = ctypes.c_int32(0)

@@ -119,3 +119,18 @@ def test_binding_refuses_to_run_without_library(monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/libvmas.so")
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_no_conditionally_skipped_warp_votes():
+    """A full-warp vote or shuffle that some lanes skip (because it sits on
+    the right of && / || or in a ?: branch) is undefined behaviour and can
+    hang or corrupt a warp; the sources must not contain that pattern."""
+    import glob
+
+    pat = re.compile(r"(&&|\|\||\?|:)\s*\(*\s*__(ballot|any|all|shfl|reduce|match)\w*_sync")
+    bad = []
+    for f in glob.glob(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", "*")):
+        for n, line in enumerate(open(f), 1):
+            if pat.search(line.split("//")[0]):
+                bad.append("%s:%d: %s" % (os.path.basename(f), n, line.strip()))
+    assert not bad, bad

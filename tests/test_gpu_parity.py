@@ -69,6 +69,14 @@ def test_small_config_one_step(vmas_lib, orc, dense, seed):
         assert omask.sum() > 0
 
 
+@pytest.mark.parametrize("n_envs", [1, 5, 33, 100])
+def test_small_config_partial_ctas(vmas_lib, orc, n_envs):
+    """Env counts that leave empty env groups in the last warp / CTA."""
+    sc = scenes.small_scene(n_envs, 11, dense=True)
+    got, ref = _one_step(vmas_lib, orc, sc, 2, steps=2)
+    assert normwise_err(got, ref).max() <= TOL
+
+
 @pytest.mark.parametrize("dense", [False, True])
 @pytest.mark.parametrize("n_envs", [1, 7, 603])
 def test_paper_config_one_step(vmas_lib, orc, dense, n_envs):
@@ -148,7 +156,7 @@ def test_gravity_max_speed_and_inert_padding(vmas_lib, orc):
     sc = scenes.paper_scene(40, 2, dense=True)
     sc.gx, sc.gy, sc.max_speed = 0.3, -2.0, 0.05
     sc.flags[:, 3] = 0   # an inert padding entity
-    sc.flags[:, 5] &= ~ACT  # one fewer actuated entity than rows
+    sc.flags[:, 5] &= np.uint8(0xFF ^ ACT)  # one fewer actuated entity than rows
     got, ref = _one_step(vmas_lib, orc, sc, 1, steps=3)
     assert normwise_err(got, ref).max() <= TOL
     assert np.array_equal(got[:, 3], sc.init_state[:, 3])
@@ -230,3 +238,52 @@ def test_trajectory_error_reported(vmas_lib, orc, capsys):
             print("\n[trajectory] %s %d steps: normwise err per field %s, max |dx| %.3g"
                   % (sc.name, T, np.array2string(err, precision=2), pos))
         assert np.isfinite(got).all()
+
+
+def test_candidate_skin_does_not_change_results(vmas_lib):
+    """The per-step candidate list only skips pairs that cannot touch, and
+    its order is fixed by (lane, slot, offset), so any skin gives bitwise the
+    same state; an overflowing list (full pair scan) agrees to rounding."""
+    sc = scenes.paper_scene(200, 6, dense=True)
+    act = torch.from_numpy(scenes.make_actions(sc, 4, 2)).cuda()
+    out = []
+    for skin in (None, 0.0, 0.004, 0.06, 10.0):
+        w = _world(sc)
+        if skin is not None:
+            w.skin = skin
+        w.rollout(act)
+        out.append(w.state().cpu().numpy())
+        w.check()
+        w.close()
+    for o in out[1:4]:
+        assert np.array_equal(o, out[0])
+    assert normwise_err(out[4], out[0]).max() <= 1e-6
+
+
+def test_fast_bodies_force_list_rebuilds(vmas_lib, orc):
+    """Bodies moving several radii per step: the candidate list must be
+    rebuilt inside the step; the result still matches the oracle."""
+    sc = scenes.paper_scene(64, 8, dense=True)
+    rng = np.random.default_rng(0)
+    sc.init_state[:, :20, 2:4] = rng.uniform(-3, 3, (64, 20, 2)).astype(np.float32)
+    got, ref = _one_step(vmas_lib, orc, sc, 4, steps=2)
+    assert normwise_err(got, ref).max() <= TOL
+
+
+def test_body_axes_accuracy(vmas_lib):
+    """The step's own cos/sin of body angles (range reduction + series)
+    against float64 math on the same float32 angles."""
+    from paper_2207_03530_b300 import _lib
+
+    rng = np.random.default_rng(0)
+    th = np.concatenate([rng.uniform(-7, 7, 50000), rng.uniform(-2000, 2000, 50000),
+                         np.array([0, 1e-30, np.pi / 4, -np.pi / 4, np.pi / 2, np.pi, 4000.0])])
+    th = th.astype(np.float32)
+    d_th = torch.from_numpy(th).cuda()
+    out = torch.empty((len(th), 2), device="cuda")
+    _lib.check(vmas_lib.vmas_debug_body_axes(d_th.data_ptr(), out.data_ptr(), len(th),
+                                             torch.cuda.current_stream().cuda_stream))
+    cs = out.cpu().numpy().astype(np.float64)
+    t64 = th.astype(np.float64)
+    err = max(np.abs(cs[:, 0] - np.cos(t64)).max(), np.abs(cs[:, 1] - np.sin(t64)).max())
+    assert err <= 1.5e-7, err
