@@ -75,7 +75,7 @@ def _recorded_traffic():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel sources sha256[:16]") != _kernel_digest():
+    if fields.get("kernel sources sha256 prefix") != _kernel_digest():
         return None
     try:
         return float(fields["dram bytes per launch (read+write)"])
@@ -84,44 +84,60 @@ def _recorded_traffic():
 
 
 class ClockSampler:
-    """Polls NVML for SM clock and throttle reasons on a background thread."""
+    """Polls NVML (through ctypes, libnvidia-ml.so.1) for the SM clock and
+    the clock-event (throttle) reasons on a background thread."""
 
-    def __init__(self, index, period=0.002):
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, torch_device, period=0.002):
+        import ctypes
+
         self.samples, self.reasons = [], set()
         self.max_mhz = None
         self._stop = threading.Event()
         self._t = None
         self.ok = False
+        self.period = period
         try:
-            import pynvml
+            import torch
 
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.period = period
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            pr = torch.cuda.get_device_properties(torch_device)
+            bus = getattr(pr, "pci_bus_id", None)
+            rc = -1
+            if bus is not None:
+                busid = "%04x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), bus,
+                                             getattr(pr, "pci_device_id", 0))
+                rc = L.nvmlDeviceGetHandleByPciBusId_v2(busid.encode(), ctypes.byref(h))
+            if rc != 0:
+                rc = L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_device.index or 0),
+                                                     ctypes.byref(h))
+            if rc != 0:
+                raise RuntimeError("no NVML handle")
+            self.L, self.h, self.ct = L, h, ctypes
+            v = ctypes.c_uint()
+            if L.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(v)) == 0:  # NVML_CLOCK_SM
+                self.max_mhz = v.value
+            self._reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(L, "nvmlDeviceGetCurrentClocksThrottleReasons")
             self.ok = True
-        except Exception as e:  # pragma: no cover - no NVML here
+        except Exception as e:  # no NVML on this host
             self.err = str(e)
 
     def _run(self):
-        nv = self.nv
-        names = {
-            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
-            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
-            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
-            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
-            "hw_power_brake_slowdown": getattr(nv, "nvmlClocksEventReasonHwPowerBrakeSlowdown", 0x80),
-        }
+        ct, L, h = self.ct, self.L, self.h
+        v, bits = ct.c_uint(), ct.c_ulonglong()
         while not self._stop.is_set():
-            try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                bits = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                for n, b in names.items():
-                    if bits & b:
+            if L.nvmlDeviceGetClockInfo(h, 1, ct.byref(v)) == 0:
+                self.samples.append(v.value)
+            if self._reasons_fn(h, ct.byref(bits)) == 0:
+                for n, b in self.REASONS.items():
+                    if bits.value & b:
                         self.reasons.add(n)
-            except Exception:
-                pass
             time.sleep(self.period)
 
     def __enter__(self):
@@ -261,12 +277,13 @@ def run_native(args):
         flush.sum()
 
     for t in range(args.warmup):
+        flush_l2()
         world.step(actions[t])
     world.check()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sampler = ClockSampler(dev.index)
+    sampler = ClockSampler(dev)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()

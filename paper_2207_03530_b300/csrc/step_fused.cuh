@@ -6,8 +6,10 @@
 // way out.  32 / G environments share a warp.
 //
 //   entities   entity a lives in lane a % G of its group, slot a / G
-//   candidates once per step (and again only if some body has moved more
-//              than half the skin since) every lane tests the pairs
+//   candidates once per step (and again only if some body may have moved
+//              more than half the skin since: a per-lane bound adds
+//              (|vx| + |vy|) h of its fastest body every substep) every lane
+//              tests the pairs
 //              {a, a + d mod N}, d = 1 .. N/2, of its entities -- each
 //              unordered pair exactly once, the same count for every lane --
 //              against bounding circles grown by the skin (and, for a line
@@ -37,8 +39,15 @@ namespace vmas {
 #define VMAS_FUSED_WARPS 4
 #endif
 constexpr int kFusedWarps = VMAS_FUSED_WARPS;  // warps per CTA
-#ifndef VMAS_MIN_BLOCKS
-#define VMAS_MIN_BLOCKS 1          // resident CTAs per SM the register budget targets
+// Resident CTAs per SM the register budget targets: 5 (96 registers) for up
+// to 3 entities per lane measured fastest on B300 at 24 entities per env; 4
+// slots need more registers.  A build may override it for tuning sweeps.
+#ifdef VMAS_MIN_BLOCKS
+template <int SLOTS>
+constexpr int min_blocks() { return VMAS_MIN_BLOCKS; }
+#else
+template <int SLOTS>
+constexpr int min_blocks() { return SLOTS <= 3 ? 5 : 3; }
 #endif
 constexpr int kLaneCand = 16;    // candidate slots per lane
 constexpr int kRecCap = 32;      // buffered contact records per environment
@@ -55,8 +64,11 @@ enum {
   kStatCount = 16
 };
 
+// Per-environment shared memory: poses twice (the second copy lets the list
+// build read entity a + d without wrapping), body frames, contact records,
+// per-lane and compacted candidate lists.
 __host__ __device__ inline int fused_env_bytes(int N, int G) {
-  return 32 * N + kRecCap * 20 + 2 * align16(2 * G * kLaneCand);
+  return 48 * N + kRecCap * 20 + 2 * align16(2 * G * kLaneCand);
 }
 __host__ __device__ inline int fused_cta_smem_bytes(int N, int P, int G) {
   return align16(2 * P) + kFusedWarps * (32 / G) * fused_env_bytes(N, G);
@@ -68,13 +80,17 @@ __device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
   return lo == 0u ? (int)hi : (lo == 1u ? 2 + (int)hi : 5);
 }
 
-template <int G, int SLOTS>
-__global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
+// G lanes per environment, SLOTS = ceil(N / G) entities per lane; NC > 0
+// compiles the kernel for exactly NC entities (fully unrolled pair loops),
+// NC == 0 takes N from the parameters.
+template <int G, int SLOTS, int NC>
+__global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     world_step_kernel(const StepParams p) {
   constexpr int EPW = 32 / G;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int N = p.N, P = p.P;
+  const int N = NC > 0 ? NC : p.N;
+  const int P = NC > 0 ? NC * (NC - 1) / 2 : p.P;
   uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
   for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -84,8 +100,8 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
   const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   const unsigned lt = (1u << lane) - 1u;
   unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(N, G);
-  float4 *s_bp = reinterpret_cast<float4 *>(es);  // {x, y, inflated R, kind}
-  float4 *s_ng = s_bp + N;                         // {cos, sin, ha, hb}
+  float4 *s_bp = reinterpret_cast<float4 *>(es);  // [2N] {x, y, inflated R, kind}
+  float4 *s_ng = s_bp + 2 * N;                     // [N] {cos, sin, ha, hb}
   float4 *s_rec = s_ng + N;                        // {fx, fy, ti, tj}
   uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kRecCap);
   uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rij + kRecCap);  // [G][kLaneCand]
@@ -99,7 +115,6 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
 
   float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
   float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
-  float xr[SLOTS], yr[SLOTS];
   uint32_t kd[SLOTS];
   int act_base = 0;
 #pragma unroll
@@ -123,6 +138,9 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
       float c = 1.f, sn = 0.f;
       if (sh != kSphere) body_axes(th[s], c, sn);
       s_ng[VIDX(a, N, 2)] = make_float4(c, sn, pr.z, pr.w);  // {cos, sin, ha, hb}
+      // immovable bodies are published once here
+      const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
+      s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
     }
     // the k-th actuated entity of the env (entity order = slot-major) reads row k
     const bool actuated = ok && (kd[s] & kActuated);
@@ -144,30 +162,40 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
     fby[s] = fay + m * p.gy;
   }
 
-  const float half_skin = 0.5f * p.skin;
-  const float move2 = (0.499f * p.skin) * (0.499f * p.skin);
+  const float move_limit = 0.499f * p.skin;
   bool full = false;    // group scans all pairs (list overflow)
   int ncand = 0;        // list length (group-uniform)
   bool rebuild = true;  // warp-uniform
+  float moved = 0.f;    // bound on how far this lane's bodies moved since the build
 
   for (int sub = 0; sub < p.S; ++sub) {
-    // publish the substep-start pose
+    // publish the substep-start pose of bodies that move or turn
+    if (sub > 0) {
 #pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      const int a = lg + G * s;
-      if (valid && a < N) {
-        if (sub > 0 && (kd[s] & kRotatable) && (kd[s] & 3u) != kSphere) {
-          float c, sn;
-          body_axes(th[s], c, sn);
-          *reinterpret_cast<float2 *>(&s_ng[VIDX(a, N, 4)]) = make_float2(c, sn);
+      for (int s = 0; s < SLOTS; ++s) {
+        const int a = lg + G * s;
+        if (valid && a < N) {
+          if ((kd[s] & kRotatable) && (kd[s] & 3u) != kSphere) {
+            float c, sn;
+            body_axes(th[s], c, sn);
+            *reinterpret_cast<float2 *>(&s_ng[VIDX(a, N, 4)]) = make_float2(c, sn);
+          }
+          if (kd[s] & kMovable) {
+            const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
+            s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
+          }
         }
-        const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
-        s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
       }
     }
-    __syncwarp();
 
     if (rebuild) {
+      // second copy of the poses, so partner a + d needs no wrap
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int a = lg + G * s;
+        if (valid && a < N) s_bp[VIDX(a + N, 2 * N, 30)] = s_bp[VIDX(a, N, 31)];
+      }
+      __syncwarp();
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
       int n = 0;
       bool over = false;
@@ -177,31 +205,32 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
         for (int s = 0; s < SLOTS; ++s) {
           const int a = lg + G * s;
           if (a >= N) continue;
-          const float4 ba = s_bp[VIDX(a, N, 6)];
-          const float4 ga = s_ng[VIDX(a, N, 7)];
           const uint32_t ka = kd[s];
+          if (!(ka & kCollidable)) continue;
+          const float ax_ = x[s], ay_ = y[s];
+          const float infl_a = rb[s] + 1e-5f * (rb[s] + fabsf(ax_) + fabsf(ay_));
+          const float ra = infl_a + p.skin;  // grown by the skin on both sides
           const bool a_line = (ka & 3u) == kLine && !(ka & kRotatable);
-          const float ra = ba.z + half_skin;
+          const float4 ga = s_ng[VIDX(a, N, 7)];
+          const bool a_moves = (ka & (kMovable | kRotatable)) != 0u;
           const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
-#pragma unroll 2
-          for (int d = 1; d <= dlast; ++d) {
-            int b = a + d;
-            if (b >= N) b -= N;
-            const float4 bb = s_bp[VIDX(b, N, 8)];
+          auto test_partner = [&](int d) {
+            const float4 bb = s_bp[VIDX(a + d, 2 * N, 8)];
             const uint32_t kb = __float_as_uint(bb.w);
-            if (!pair_active(ka, kb)) continue;
-            const float dx = ba.x - bb.x, dy = ba.y - bb.y;
-            const float lim = ra + bb.z + half_skin;
-            if (dx * dx + dy * dy > lim * lim) continue;
+            if (!(kb & kCollidable) || !(a_moves || (kb & (kMovable | kRotatable)))) return;
+            const float dx = ax_ - bb.x, dy = ay_ - bb.y;
+            const float lim = ra + bb.z;
+            if (dx * dx + dy * dy > lim * lim) return;
+            const int b = a + d >= N ? a + d - N : a + d;
             if ((kb & 3u) == kLine && !(kb & kRotatable)) {
               const float4 gb4 = s_ng[VIDX(b, N, 9)];
               if (fabsf(dx * gb4.y - dy * gb4.x) >
-                  ba.z + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
-                continue;
+                  infl_a + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
+                return;
             }
             if (a_line && fabsf(dx * ga.y - dy * ga.x) >
-                              bb.z + p.skin + 1e-5f * (fabsf(ba.x) + fabsf(ba.y)))
-              continue;
+                              bb.z + p.skin + 1e-5f * (fabsf(ax_) + fabsf(ay_)))
+              return;
             if (n < kLaneCand) {
               const int lo = a < b ? a : b, hi = a < b ? b : a;
               s_lc[VIDX(lg * kLaneCand + n, LC, 10)] = (uint16_t)(lo | (hi << 8));
@@ -209,6 +238,13 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
               over = true;
             }
             ++n;
+          };
+          if (NC > 0) {
+#pragma unroll
+            for (int d = 1; d <= (NC > 0 ? NC / 2 : 1); ++d)
+              if (d <= dlast) test_partner(d);
+          } else {
+            for (int d = 1; d <= dlast; ++d) test_partner(d);
           }
         }
       }
@@ -227,17 +263,13 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
       const unsigned over_bits = __ballot_sync(FULL, over);
       full = valid && (over_bits & gbits) != 0u;
       ncand = valid ? (full ? P : total) : 0;
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        xr[s] = x[s];
-        yr[s] = y[s];
-      }
+      moved = 0.f;
       if (stats && valid && lg == 0) {
         atomicAdd(stats + kStatRebuilds, 1ull);
         atomicAdd(stats + kStatCandidates, (unsigned long long)total);
       }
-      __syncwarp();
     }
+    __syncwarp();
 
     // Eq. 1: action + gravity; Eq. 3: action torque
     float Fx[SLOTS], Fy[SLOTS], T[SLOTS];
@@ -309,7 +341,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
     __syncwarp();
 
     // Eqs. 1 and 3: damped semi-implicit Euler
-    bool moved = false;
+    float fastest = 0.f;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       if (kd[s] & kMovable) {
@@ -325,15 +357,16 @@ __global__ void __launch_bounds__(kFusedWarps * 32, VMAS_MIN_BLOCKS)
         }
         x[s] += vx[s] * p.h;
         y[s] += vy[s] * p.h;
-        const float ddx = x[s] - xr[s], ddy = y[s] - yr[s];
-        moved |= ddx * ddx + ddy * ddy > move2;
+        fastest = fmaxf(fastest, fabsf(vx[s]) + fabsf(vy[s]));
       }
       if (kd[s] & kRotatable) {
         om[s] = p.damp * om[s] + T[s] * iI[s] * p.h;
         th[s] += om[s] * p.h;
       }
     }
-    rebuild = __any_sync(FULL, moved);
+    // |displacement| <= (|vx| + |vy|) h per substep
+    moved = fmaf(fastest, p.h, moved);
+    rebuild = __any_sync(FULL, moved > move_limit);
     __syncwarp();
   }
 

@@ -112,10 +112,10 @@ StepParams make_params(const vmas_world *w) {
   return p;
 }
 
-template <int G, int SLOTS>
+template <int G, int SLOTS, int NC>
 int launch_step_gs(const StepParams &p, cudaStream_t st) {
   const int smem = vmas::fused_cta_smem_bytes(p.N, p.P, G);
-  auto kern = vmas::world_step_kernel<G, SLOTS>;
+  auto kern = vmas::world_step_kernel<G, SLOTS, NC>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -128,19 +128,35 @@ int launch_step_gs(const StepParams &p, cudaStream_t st) {
   return VMAS_OK;
 }
 
+// Entity counts with a kernel compiled for exactly that count (fully
+// unrolled pair loops); any other count runs the generic kernel.
 template <int G>
 int launch_step_g(const StepParams &p, cudaStream_t st) {
+#ifndef VMAS_NO_SPECIALIZE
+  if constexpr (G == 8) {
+    if (p.N == 24) return launch_step_gs<8, 3, 24>(p, st);
+  }
+  if constexpr (G == 4) {
+    if (p.N == 6) return launch_step_gs<4, 2, 6>(p, st);
+  }
+#endif
   switch ((p.N + G - 1) / G) {
-    case 1: return launch_step_gs<G, 1>(p, st);
-    case 2: return launch_step_gs<G, 2>(p, st);
-    case 3: return launch_step_gs<G, 3>(p, st);
-    default: return launch_step_gs<G, 4>(p, st);
+    case 1: return launch_step_gs<G, 1, 0>(p, st);
+    case 2: return launch_step_gs<G, 2, 0>(p, st);
+    case 3: return launch_step_gs<G, 3, 0>(p, st);
+    default: return launch_step_gs<G, 4, 0>(p, st);
   }
 }
 
 // Lanes per environment: the smallest group that holds every entity in at
 // most 4 slots (N <= 8: 4 lanes, <= 32: 8, <= 64: 16, else 32).
-int group_lanes(int N) { return N <= 8 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : 32; }
+int group_lanes(int N) {
+#ifdef VMAS_GROUP_LANES
+  const int g = VMAS_GROUP_LANES;  // build-time override for tuning sweeps
+  if ((N + g - 1) / g <= 4) return g;
+#endif
+  return N <= 8 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : 32;
+}
 
 int launch_step(const StepParams &p, cudaStream_t st) {
   if (p.E == 0) return VMAS_OK;
