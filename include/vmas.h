@@ -63,7 +63,8 @@ enum {
 
 /* Bits of the device error word reported through VMAS_EDEVICE. */
 enum {
-  VMAS_DEVERR_NONFINITE = 1 /* a state value became NaN or Inf */
+  VMAS_DEVERR_NONFINITE = 1, /* a state value became NaN or Inf */
+  VMAS_DEVERR_BAD_ENTITY = 4 /* vmas_step_noalloc met an invalid entity and left it inert */
 };
 
 /* Largest supported entity count per environment. */
@@ -179,6 +180,44 @@ int vmas_check(vmas_world *world, void *stream, int32_t *bits);
  * device angles d_theta into device d_cos_sin [n][2] (cos, sin); the
  * library's own range reduction and series, absolute error about 1e-7. */
 int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void *stream);
+
+/* ---- Allocation-free step --------------------------------------------
+ * Not part of the method: the paper has no counterpart.  Some callers cannot
+ * let a library call cudaMalloc: code that owns all device memory through
+ * its own allocator (a framework's memory pool, an arena reserved up front),
+ * loops that must not stall on the device synchronisation that cudaMalloc and
+ * cudaFree can cause, and code running under stream capture, where those
+ * calls are not allowed.  vmas_step_noalloc is one world step (the same
+ * kernel as vmas_step) over buffers the caller owns; it allocates nothing.
+ *
+ * Its only scratch is a fixed 16 KiB array in the library's device memory
+ * (the pair table for up to VMAS_NOALLOC_MAX_ENTITIES entities plus a status
+ * word), present on every device that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and rewrites it, so calls that can overlap on
+ * the GPU (on different streams) race: serialise them.
+ *
+ * Arguments: every pointer is device memory, entity arrays [n_envs *
+ * n_entities] as in vmas_world_desc, state [n_envs][n_entities][6] read and
+ * overwritten in place, actions [n_envs][n_actuated][3] (NULL when
+ * n_actuated == 0).  skin >= 0 is the candidate-list margin (see
+ * vmas_world_set_skin; 0 rebuilds the list every substep, always valid).
+ * status (optional, device int32): the call ORs VMAS_DEVERR_* bits into it;
+ * the caller clears it.  Entities are checked on the device: an invalid one
+ * is left inert and raises VMAS_DEVERR_BAD_ENTITY.  Returns VMAS_EINVAL
+ * (before enqueuing anything) when n_entities > VMAS_NOALLOC_MAX_ENTITIES. */
+#define VMAS_NOALLOC_MAX_ENTITIES 128
+typedef struct {
+  int32_t n_envs, n_entities, n_actuated, substeps;
+  float dt, drag, gx, gy, contact_force, contact_margin, max_speed, skin;
+  const uint8_t *shape, *flags;
+  const float *size_a, *size_b, *mass, *inertia;
+  float *state;
+  const float *actions;
+  int32_t *status;
+} vmas_step_noalloc_args;
+int vmas_step_noalloc(const vmas_step_noalloc_args *args, void *stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *vmas_last_error(void);

@@ -19,7 +19,7 @@ SYMBOLS = (
     "vmas_step_host", "vmas_rollout", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
     "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
-    "vmas_debug_body_axes",
+    "vmas_debug_body_axes", "vmas_step_noalloc",
 )
 STATS_COUNT = 16
 STATS_NAMES = ("env_steps", "rebuilds", "candidates",
@@ -37,6 +37,22 @@ class WorldDesc(ctypes.Structure):
         ("shape", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("size_a", ctypes.c_void_p),
         ("size_b", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("inertia", ctypes.c_void_p),
         ("init_state", ctypes.c_void_p),
+    ]
+
+
+class StepNoallocArgs(ctypes.Structure):
+    """vmas_step_noalloc_args: sizes, parameters and caller-owned device buffers."""
+
+    _fields_ = [
+        ("n_envs", ctypes.c_int32), ("n_entities", ctypes.c_int32),
+        ("n_actuated", ctypes.c_int32), ("substeps", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("drag", ctypes.c_float), ("gx", ctypes.c_float),
+        ("gy", ctypes.c_float), ("contact_force", ctypes.c_float),
+        ("contact_margin", ctypes.c_float), ("max_speed", ctypes.c_float),
+        ("skin", ctypes.c_float),
+        ("shape", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("size_a", ctypes.c_void_p),
+        ("size_b", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("inertia", ctypes.c_void_p),
+        ("state", ctypes.c_void_p), ("actions", ctypes.c_void_p), ("status", ctypes.c_void_p),
     ]
 
 
@@ -78,6 +94,7 @@ def load():
         "vmas_world_set_stats": ([vp, i32], ctypes.c_int),
         "vmas_world_get_stats": ([vp, vp, i32, vp], ctypes.c_int),
         "vmas_debug_body_axes": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_step_noalloc": ([P(StepNoallocArgs), vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

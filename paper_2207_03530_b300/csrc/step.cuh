@@ -43,6 +43,10 @@ struct StepParams {
   uint8_t *mask;                       // [E][P], mask kernel only
   int *err;                            // device error word
   unsigned long long *stats;           // optional counters, nullptr = off
+  // caller-owned buffers of the allocation-free entry point (RAW kernels):
+  float *aos_state;                    // [E][N][6] x y vx vy th om, read and written
+  const uint8_t *r_shape, *r_flags;    // [E * N]
+  const float *r_size_a, *r_size_b, *r_mass, *r_inertia;  // [E * N]
 };
 
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }

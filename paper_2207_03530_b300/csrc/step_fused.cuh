@@ -83,7 +83,10 @@ __device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
 // G lanes per environment, SLOTS = ceil(N / G) entities per lane; NC > 0
 // compiles the kernel for exactly NC entities (fully unrolled pair loops),
 // NC == 0 takes N from the parameters.
-template <int G, int SLOTS, int NC>
+// RAW = true is the allocation-free variant: it reads the caller's raw
+// entity arrays and [E][N][6] state and packs the per-entity parameters on
+// the fly instead of reading the library's packed planes.
+template <int G, int SLOTS, int NC, bool RAW = false>
 __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     world_step_kernel(const StepParams p) {
   constexpr int EPW = 32 / G;
@@ -122,14 +125,40 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     const int a = lg + G * s;
     const bool ok = valid && a < N;
     const size_t ga_ = ok ? VIDX(eb + a, (size_t)p.E * N, 1) : 0;
-    kd[s] = ok ? p.kind[ga_] : 0u;
-    x[s] = ok ? p.px[ga_] : 0.f;
-    y[s] = ok ? p.py[ga_] : 0.f;
-    vx[s] = ok ? p.vx[ga_] : 0.f;
-    vy[s] = ok ? p.vy[ga_] : 0.f;
-    th[s] = ok ? p.th[ga_] : 0.f;
-    om[s] = ok ? p.om[ga_] : 0.f;
-    const float4 pr = ok ? p.param[ga_] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pr;
+    if constexpr (RAW) {
+      pr = make_float4(0.f, 0.f, 0.f, 0.f);
+      kd[s] = 0u;
+      x[s] = y[s] = vx[s] = vy[s] = th[s] = om[s] = 0.f;
+      if (ok) {
+        const float *st = p.aos_state + ga_ * 6;
+        x[s] = st[0]; y[s] = st[1]; vx[s] = st[2]; vy[s] = st[3]; th[s] = st[4]; om[s] = st[5];
+        const uint32_t sh = p.r_shape[ga_], fl = p.r_flags[ga_];
+        const float sa = p.r_size_a[ga_], sb = p.r_size_b[ga_], m = p.r_mass[ga_];
+        float I = p.r_inertia[ga_];
+        if (I == 0.f)
+          I = sh == kBox ? m * (sa * sa + sb * sb) / 12.f
+                         : (sh == kLine ? m * sa * sa / 12.f : 0.5f * m * sa * sa);
+        const bool bad = sh > 2u || (fl & ~15u) || !(sa > 0.f) || (sh == kBox && !(sb > 0.f)) ||
+                         ((fl & 1u) && !(m > 0.f)) || ((fl & 2u) && !(I > 0.f));
+        if (bad) {
+          atomicOr(p.err, 4);  // VMAS_DEVERR_BAD_ENTITY: the entity is left inert
+        } else {
+          kd[s] = sh | (fl << 2);
+          pr = make_float4((fl & 1u) ? 1.f / m : 0.f, (fl & 2u) ? 1.f / I : 0.f,
+                           sh == kSphere ? sa : 0.5f * sa, sh == kBox ? 0.5f * sb : 0.f);
+        }
+      }
+    } else {
+      kd[s] = ok ? p.kind[ga_] : 0u;
+      x[s] = ok ? p.px[ga_] : 0.f;
+      y[s] = ok ? p.py[ga_] : 0.f;
+      vx[s] = ok ? p.vx[ga_] : 0.f;
+      vy[s] = ok ? p.vy[ga_] : 0.f;
+      th[s] = ok ? p.th[ga_] : 0.f;
+      om[s] = ok ? p.om[ga_] : 0.f;
+      pr = ok ? p.param[ga_] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     im[s] = pr.x;
     iI[s] = pr.y;
     const uint32_t sh = kd[s] & 3u;
@@ -376,12 +405,17 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     const int a = lg + G * s;
     if (valid && a < N) {
       const size_t go_ = VIDX(eb + a, (size_t)p.E * N, 26);
-      p.px[go_] = x[s];
-      p.py[go_] = y[s];
-      p.vx[go_] = vx[s];
-      p.vy[go_] = vy[s];
-      p.th[go_] = th[s];
-      p.om[go_] = om[s];
+      if constexpr (RAW) {
+        float *st = p.aos_state + go_ * 6;
+        st[0] = x[s]; st[1] = y[s]; st[2] = vx[s]; st[3] = vy[s]; st[4] = th[s]; st[5] = om[s];
+      } else {
+        p.px[go_] = x[s];
+        p.py[go_] = y[s];
+        p.vx[go_] = vx[s];
+        p.vy[go_] = vy[s];
+        p.th[go_] = th[s];
+        p.om[go_] = om[s];
+      }
       bad |= !(isfinite(x[s]) && isfinite(y[s]) && isfinite(vx[s]) && isfinite(vy[s]) &&
                isfinite(th[s]) && isfinite(om[s]));
     }

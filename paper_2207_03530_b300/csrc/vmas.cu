@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -229,9 +230,139 @@ int read_err(vmas_world *w, cudaStream_t st, int32_t *bits) {
   return VMAS_OK;
 }
 
+// ---- allocation-free step (vmas_step_noalloc) -----------------------------
+// Its only scratch is this array: the canonical pair table for up to
+// VMAS_NOALLOC_MAX_ENTITIES entities (uint16 i | j << 8) followed by a status
+// word.  Every device that loads the library holds it until exit; every call
+// shares it.
+constexpr int kNoallocPairs = VMAS_NOALLOC_MAX_ENTITIES * (VMAS_NOALLOC_MAX_ENTITIES - 1) / 2;
+constexpr int kNoallocStatusOffset = ((kNoallocPairs * 2 + 255) / 256) * 256;
+constexpr int kNoallocBytes = kNoallocStatusOffset + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
+
+// Set-up on first use per device (with that device current): the device
+// address of the scratch array.  A host-side reference to the array is only a
+// stand-in and must never be handed to a kernel.
+int noalloc_scratch(unsigned char **out) {
+  int dev = 0;
+  VMAS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(VMAS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    VMAS_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return VMAS_OK;
+}
+
+// Canonical pair list (i < j, row-major) for N entities.
+__global__ void fill_pairs_kernel(uint16_t *pairs, int N) {
+  for (int i = blockIdx.x; i < N - 1; i += gridDim.x) {
+    const int row = i * N - i * (i + 1) / 2;
+    for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x)
+      pairs[row + (j - i - 1)] = (uint16_t)(i | (j << 8));
+  }
+}
+
+template <int G, int SLOTS>
+int launch_raw_gs(const StepParams &p, cudaStream_t st) {
+  const int smem = vmas::fused_cta_smem_bytes(p.N, p.P, G);
+  auto kern = vmas::world_step_kernel<G, SLOTS, 0, true>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  const int envs_per_cta = vmas::kFusedWarps * (32 / G);
+  const int grid = (p.E + envs_per_cta - 1) / envs_per_cta;
+  kern<<<grid, vmas::kFusedWarps * 32, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "world_step_kernel (no-alloc) launch");
+  return VMAS_OK;
+}
+
+template <int G>
+int launch_raw_g(const StepParams &p, cudaStream_t st) {
+  switch ((p.N + G - 1) / G) {
+    case 1: return launch_raw_gs<G, 1>(p, st);
+    case 2: return launch_raw_gs<G, 2>(p, st);
+    case 3: return launch_raw_gs<G, 3>(p, st);
+    default: return launch_raw_gs<G, 4>(p, st);
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+int vmas_step_noalloc(const vmas_step_noalloc_args *a, void *stream) {
+  if (!a) return fail(VMAS_EINVAL, "args is NULL");
+  if (a->n_envs < 0 || a->n_actuated < 0 || a->substeps < 1)
+    return fail(VMAS_EINVAL, "n_envs, n_actuated must be >= 0 and substeps >= 1");
+  if (a->n_entities < 1 || a->n_entities > VMAS_NOALLOC_MAX_ENTITIES)
+    return fail(VMAS_EINVAL, "n_entities must be 1.." + std::to_string(VMAS_NOALLOC_MAX_ENTITIES) +
+                                 ": the allocation-free step keeps its pair table in a fixed "
+                                 "scratch array of that size");
+  if (!(a->dt > 0) || !std::isfinite(a->dt) || !(a->contact_margin > 0) ||
+      !(a->contact_force >= 0) || !(a->max_speed >= 0) || !(a->skin >= 0) ||
+      !std::isfinite(a->skin))
+    return fail(VMAS_EINVAL, "dt, contact_margin must be > 0; contact_force, max_speed, skin >= 0");
+  const size_t EN = (size_t)a->n_envs * a->n_entities;
+  if (EN && (!a->state || !a->shape || !a->flags || !a->size_a || !a->size_b || !a->mass ||
+             !a->inertia))
+    return fail(VMAS_EINVAL, "a device array is NULL");
+  if (EN && a->n_actuated && !a->actions) return fail(VMAS_EINVAL, "actions is NULL");
+  unsigned char *scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  const int N = a->n_entities;
+  uint16_t *pairs = reinterpret_cast<uint16_t *>(scratch);
+  int *status = reinterpret_cast<int *>(scratch + kNoallocStatusOffset);
+  // the status word must start each call at zero; the pair table is rewritten
+  VMAS_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  if (N > 1) {
+    fill_pairs_kernel<<<N - 1, 64, 0, st>>>(pairs, N);
+    VMAS_CUDA(cudaGetLastError());
+  }
+  if (!EN) return VMAS_OK;
+  StepParams p{};
+  p.E = a->n_envs;
+  p.N = N;
+  p.A = a->n_actuated;
+  p.S = a->substeps;
+  p.P = N * (N - 1) / 2;
+  p.h = (float)((double)a->dt / (double)a->substeps);
+  p.damp = (float)(1.0 - (double)a->drag);
+  p.gx = a->gx;
+  p.gy = a->gy;
+  p.ck = (float)((double)a->contact_force * (double)a->contact_margin);
+  p.inv_k = (float)(1.0 / (double)a->contact_margin);
+  p.vmax = a->max_speed;
+  p.skin = a->skin;
+  p.pairs = pairs;
+  p.actions = a->actions;
+  p.err = a->status ? a->status : status;
+  p.aos_state = a->state;
+  p.r_shape = a->shape;
+  p.r_flags = a->flags;
+  p.r_size_a = a->size_a;
+  p.r_size_b = a->size_b;
+  p.r_mass = a->mass;
+  p.r_inertia = a->inertia;
+  switch (group_lanes(N)) {
+    case 4: return launch_raw_g<4>(p, st);
+    case 8: return launch_raw_g<8>(p, st);
+    case 16: return launch_raw_g<16>(p, st);
+    default: return launch_raw_g<32>(p, st);
+  }
+}
+
 
 const char *vmas_last_error(void) { return g_last_error.c_str(); }
 
