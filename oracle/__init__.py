@@ -70,6 +70,10 @@ def _lib():
         h.ow_inertia.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
         h.ow_inertia.restype = ctypes.c_double
         h.ow_max_threads.restype = ctypes.c_int
+        h.ow_rollout_grad.argtypes = [ctypes.POINTER(_World), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+        h.ow_rollout_grad.restype = ctypes.c_int
         _handle = h
     return _handle
 
@@ -153,3 +157,27 @@ def inertia(shape: int, m: float, a: float, b: float, given: float = 0.0) -> flo
 
 def max_threads() -> int:
     return _lib().ow_max_threads()
+
+
+def rollout_grad(scene, state, actions, goals, with_grad=True):
+    """Differentiable rollout of a sphere world (FP64): per-env loss
+    sum_k |x_k(T) - goal_k|^2 over the actuated entities after len(actions)
+    steps, and its gradient with respect to the actions (reverse mode).
+
+    actions [T, E, A, 3], goals [E, A, 2].  Returns (loss [E], grad [T, E, A, 3]
+    or None)."""
+    pk = _Packed(scene)
+    E, N, A = int(scene.n_envs), int(scene.n_entities), int(scene.n_actuated)
+    st = np.ascontiguousarray(np.asarray(state, np.float64).reshape(E, N, 6))
+    act = np.ascontiguousarray(np.asarray(actions, np.float64))
+    T = act.shape[0]
+    act = act.reshape(T, E, A, 3)
+    gl = np.ascontiguousarray(np.asarray(goals, np.float64).reshape(E, A, 2))
+    loss = np.zeros(E, np.float64)
+    grad = np.zeros((T, E, A, 3), np.float64) if with_grad else None
+    rc = _lib().ow_rollout_grad(ctypes.byref(pk.w), st.ctypes.data, act.ctypes.data, T,
+                                gl.ctypes.data, loss.ctypes.data,
+                                grad.ctypes.data if with_grad else None)
+    if rc != 0:
+        raise ValueError("rollout_grad needs a sphere world without a speed cap")
+    return loss, grad

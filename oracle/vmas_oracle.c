@@ -693,3 +693,195 @@ int ow_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------- adjoint
+ * Gradient of a differentiable rollout (sphere worlds), FP64.
+ *
+ * Forward: T world steps of Eqs. 1-3 from `state` with actions
+ * [T][E][A][3]; loss per env = sum over actuated entities k of
+ * |x_k(T) - goal_k|^2.  Backward: reverse-mode through every substep.  With
+ * a = 1 - zeta and h = dt / S, one substep of a movable sphere is
+ *   F_i = f^a_i + m_i g + sum_j f_ij,   v_i' = a v_i + (h / m_i) F_i,
+ *   x_i' = x_i + h v_i',
+ * and the pair force f_ij = M(g) u, u = d / |d|, d = x_i - x_j,
+ * g = |d| - (r_i + r_j), M(g) = c k softplus(-g / k) (g <= 0, Eq. 2), whose
+ * Jacobian is J = dM/dg u u^T + M / |d| (I - u u^T), dM/dg = -c sigmoid(-g/k).
+ * The contact mask is treated as piecewise constant (Reading R2: no term
+ * from the jump at g = 0).  Adjoints, given lx', lv' of a substep's outputs:
+ *   lv'' = lv' + h lx',  lx = lx' + sum over pairs of J (lF_i - lF_j) terms,
+ *   lv = a lv'',  lF_i = (h / m_i) lv''_i,  d loss / d f^a_i += lF_i.
+ * Forces on immovable entities are dropped (Reading R6), so their lF is 0. */
+
+static void sphere_pair_force(const double *xi, const double *xj, double ri, double rj,
+                              double c, double k, int *hit, double f[2], double J[4]) {
+  double dx = xi[0] - xj[0], dy = xi[1] - xj[1];
+  double s = sqrt(dx * dx + dy * dy);
+  double g = s - (ri + rj);
+  *hit = (g <= 0 && s > 0);
+  if (!*hit) return;
+  double ux = dx / s, uy = dy / s;
+  double M = contact_magnitude(c, k, g);
+  double sig = 1.0 / (1.0 + exp(g / k)); /* sigmoid(-g/k) */
+  double dM = -c * sig;
+  f[0] = M * ux;
+  f[1] = M * uy;
+  double t = M / s;
+  J[0] = dM * ux * ux + t * (1 - ux * ux);
+  J[1] = dM * ux * uy - t * ux * uy;
+  J[2] = J[1];
+  J[3] = dM * uy * uy + t * (1 - uy * uy);
+}
+
+/* Forward of one env through T steps, recording (x, y, vx, vy) at every
+ * substep start into traj [(T*S + 1)][N][4]; returns the final loss. */
+static double rollout_env(const ow_world *w, int e, const double *st0, const double *act_all,
+                          int T, const double *goals, double *traj) {
+  int N = w->n_entities, A = w->n_actuated, S = w->substeps, E = w->n_envs;
+  size_t base = (size_t)e * N;
+  double h = w->dt / S;
+  double *F = (double *)malloc(sizeof(double) * 2 * N);
+  double *cur = (double *)malloc(sizeof(double) * 4 * N);
+  for (int i = 0; i < N; ++i) {
+    cur[4 * i + 0] = st0[6 * i + 0];
+    cur[4 * i + 1] = st0[6 * i + 1];
+    cur[4 * i + 2] = st0[6 * i + 2];
+    cur[4 * i + 3] = st0[6 * i + 3];
+  }
+  int q = 0;
+  memcpy(traj, cur, sizeof(double) * 4 * N);
+  for (int t = 0; t < T; ++t) {
+    const double *act = act_all + ((size_t)t * E + e) * A * 3;
+    for (int s = 0; s < S; ++s) {
+      int a = 0;
+      for (int i = 0; i < N; ++i) {
+        uint8_t fl = w->flags[base + i];
+        double m = w->mass[base + i];
+        F[2 * i] = m * w->gx;
+        F[2 * i + 1] = m * w->gy;
+        if (fl & OW_ACTUATED) {
+          F[2 * i] += act[3 * a];
+          F[2 * i + 1] += act[3 * a + 1];
+          ++a;
+        }
+      }
+      for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+          if (!pair_active(w->flags[base + i], w->flags[base + j])) continue;
+          int hit;
+          double f[2], J[4];
+          sphere_pair_force(cur + 4 * i, cur + 4 * j, w->size_a[base + i], w->size_a[base + j],
+                            w->c, w->k, &hit, f, J);
+          if (!hit) continue;
+          F[2 * i] += f[0];
+          F[2 * i + 1] += f[1];
+          F[2 * j] -= f[0];
+          F[2 * j + 1] -= f[1];
+        }
+      for (int i = 0; i < N; ++i) {
+        if (!(w->flags[base + i] & OW_MOVABLE)) continue;
+        double m = w->mass[base + i];
+        cur[4 * i + 2] = (1.0 - w->drag) * cur[4 * i + 2] + F[2 * i] / m * h;
+        cur[4 * i + 3] = (1.0 - w->drag) * cur[4 * i + 3] + F[2 * i + 1] / m * h;
+        cur[4 * i + 0] += cur[4 * i + 2] * h;
+        cur[4 * i + 1] += cur[4 * i + 3] * h;
+      }
+      ++q;
+      memcpy(traj + (size_t)q * 4 * N, cur, sizeof(double) * 4 * N);
+    }
+  }
+  double loss = 0;
+  int a = 0;
+  for (int i = 0; i < N; ++i)
+    if (w->flags[base + i] & OW_ACTUATED) {
+      double dx = cur[4 * i] - goals[((size_t)e * A + a) * 2];
+      double dy = cur[4 * i + 1] - goals[((size_t)e * A + a) * 2 + 1];
+      loss += dx * dx + dy * dy;
+      ++a;
+    }
+  free(F);
+  free(cur);
+  return loss;
+}
+
+/* Differentiable rollout of sphere worlds.  state [E][N][6] (only x, y, vx,
+ * vy are used), actions [T][E][A][3], goals [E][A][2].  loss [E] receives
+ * each env's loss; grad (if not NULL) [T][E][A][3] receives d loss_e /
+ * d action (torque component 0).  Returns -1 if a non-sphere entity or a
+ * speed cap is present. */
+int ow_rollout_grad(const ow_world *w, const double *state, const double *actions, int T,
+                    const double *goals, double *loss, double *grad) {
+  int E = w->n_envs, N = w->n_entities, A = w->n_actuated, S = w->substeps;
+  if (w->max_speed > 0) return -1;
+  for (size_t t = 0; t < (size_t)E * N; ++t)
+    if (w->shape[t] != OW_SPHERE) return -1;
+  double h = w->dt / S, a_drag = 1.0 - w->drag;
+  size_t Q = (size_t)T * S + 1;
+  double *traj = (double *)malloc(sizeof(double) * Q * 4 * N);
+  double *lx = (double *)malloc(sizeof(double) * 2 * N);
+  double *lv = (double *)malloc(sizeof(double) * 2 * N);
+  double *lF = (double *)malloc(sizeof(double) * 2 * N);
+  for (int e = 0; e < E; ++e) {
+    size_t base = (size_t)e * N;
+    loss[e] = rollout_env(w, e, state + base * 6, actions, T, goals, traj);
+    if (!grad) continue;
+    /* d loss / d x(T) = 2 (x - goal); d loss / d v(T) = 0 */
+    const double *fin = traj + (Q - 1) * 4 * N;
+    int a = 0;
+    for (int i = 0; i < N; ++i) {
+      lx[2 * i] = lx[2 * i + 1] = 0;
+      lv[2 * i] = lv[2 * i + 1] = 0;
+      if (w->flags[base + i] & OW_ACTUATED) {
+        lx[2 * i] = 2 * (fin[4 * i] - goals[((size_t)e * A + a) * 2]);
+        lx[2 * i + 1] = 2 * (fin[4 * i + 1] - goals[((size_t)e * A + a) * 2 + 1]);
+        ++a;
+      }
+    }
+    for (int t = T - 1; t >= 0; --t) {
+      double *gact = grad + ((size_t)t * E + e) * A * 3;
+      for (int q = 0; q < A * 3; ++q) gact[q] = 0;
+      for (int s = S - 1; s >= 0; --s) {
+        const double *cur = traj + ((size_t)t * S + s) * 4 * N; /* substep start */
+        /* through x' = x + h v' and v' = a v + (h/m) F */
+        for (int i = 0; i < N; ++i) {
+          lF[2 * i] = lF[2 * i + 1] = 0;
+          if (!(w->flags[base + i] & OW_MOVABLE)) continue;
+          double m = w->mass[base + i];
+          double lvx = lv[2 * i] + h * lx[2 * i], lvy = lv[2 * i + 1] + h * lx[2 * i + 1];
+          lF[2 * i] = h / m * lvx;
+          lF[2 * i + 1] = h / m * lvy;
+          lv[2 * i] = a_drag * lvx;
+          lv[2 * i + 1] = a_drag * lvy;
+        }
+        /* actions feed F directly */
+        int k = 0;
+        for (int i = 0; i < N; ++i)
+          if (w->flags[base + i] & OW_ACTUATED) {
+            gact[3 * k] += lF[2 * i];
+            gact[3 * k + 1] += lF[2 * i + 1];
+            ++k;
+          }
+        /* contact forces depend on positions at the substep start */
+        for (int i = 0; i < N; ++i)
+          for (int j = i + 1; j < N; ++j) {
+            if (!pair_active(w->flags[base + i], w->flags[base + j])) continue;
+            int hit;
+            double f[2], J[4];
+            sphere_pair_force(cur + 4 * i, cur + 4 * j, w->size_a[base + i],
+                              w->size_a[base + j], w->c, w->k, &hit, f, J);
+            if (!hit) continue;
+            double dx = lF[2 * i] - lF[2 * j], dy = lF[2 * i + 1] - lF[2 * j + 1];
+            double gx = J[0] * dx + J[1] * dy, gy = J[2] * dx + J[3] * dy;
+            lx[2 * i] += gx;
+            lx[2 * i + 1] += gy;
+            lx[2 * j] -= gx;
+            lx[2 * j + 1] -= gy;
+          }
+      }
+    }
+  }
+  free(traj);
+  free(lx);
+  free(lv);
+  free(lF);
+  return 0;
+}

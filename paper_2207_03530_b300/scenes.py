@@ -387,6 +387,34 @@ def mixed_scene(n_envs: int = 64, seed: int = 0, spread: float = 0.35,
     return sc
 
 
+def diff_scene(n_envs: int = 4096, seed: int = 0, dense: bool = False) -> Scene:
+    """Differentiable-rollout workload: per env 8 agent spheres (r=0.05,
+    mass 1, movable, actuated) then 2 static landmark spheres (r=0.1); centres
+    uniform in [-1,1]^2 with bounding circles apart (or, dense, 30% placed
+    against an earlier body); dt=0.1, drag 0.25, 3 substeps."""
+    E, N = n_envs, 10
+    sc = _empty("diff" + ("-dense" if dense else ""), E, N, 8, 3, 0.1, 0.25)
+    rng = np.random.default_rng(seed)
+    radii = np.array([0.05] * 8 + [0.1] * 2)
+    sc.shape[:] = SPHERE
+    sc.flags[:, :8] = MOVABLE | COLLIDABLE | ACTUATED
+    sc.flags[:, 8:] = COLLIDABLE
+    sc.size_a[:] = _f32(radii)
+    P = _Placer(rng, E, N)
+    order = [8, 9] + list(range(8))
+    for slot, ent in enumerate(order):
+        x, y = _place_sphere(P, rng, radii[ent], dense and slot > 0)
+        sc.init_state[:, ent, 0] = x
+        sc.init_state[:, ent, 1] = y
+    return sc
+
+
+def make_goals(scene: Scene, seed: int = 0) -> np.ndarray:
+    """Goal positions [n_envs, n_actuated, 2], uniform in [-1, 1]^2, FP32."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x60A1]))
+    return rng.uniform(-1.0, 1.0, size=(scene.n_envs, scene.n_actuated, 2)).astype(np.float32)
+
+
 def make_actions(scene: Scene, n_steps: int, seed: int = 0) -> np.ndarray:
     """Per-step actions [n_steps, n_envs, n_actuated, 3] (fx, fy, torque),
     uniform in [-1, 1], FP32."""
@@ -399,4 +427,5 @@ CONFIGS = {
     "small": small_scene,
     "paper": paper_scene,
     "mixed": mixed_scene,
+    "diff": diff_scene,
 }
