@@ -382,12 +382,78 @@ def run_native(args):
     return 0
 
 
+def run_adjoint(args):
+    """Differentiable rollout (BASELINE config 4): 4,096 envs x (8 agents + 2
+    landmarks), 3 substeps, 50 steps, checkpoint every 10.  Times forward +
+    backward (hand-written adjoint) and the plain step on the same scene,
+    and checks 4 sampled envs' gradients against the FP64 oracle."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    build.build()
+    torch.cuda.set_device(0)
+    E, T, K = args.envs if args.envs != 30000 else 4096, 50, 10
+    sc = scenes.diff_scene(E, args.seed)
+    w = World(sc)
+    act = torch.from_numpy(scenes.make_actions(sc, T, args.seed + 1)).cuda()
+    goals = torch.from_numpy(scenes.make_goals(sc, args.seed + 2)).cuda()
+
+    def fwd_bwd():
+        a = act.clone().requires_grad_(True)
+        rollout_loss(w, a, goals, ckpt_every=K).sum().backward()
+        return a.grad
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        grad = fwd_bwd()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    # plain fused step on the same scene, same actions
+    for t in range(3):
+        w.step(act[t])
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    w.rollout(act)
+    p1.record()
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    # accuracy on 4 sampled envs
+    import oracle
+
+    pick = np.array([0, E // 3, 2 * E // 3, E - 1])
+    sub = sc.subset(pick)
+    a_np, g_np = act.cpu().numpy(), goals.cpu().numpy()
+    _, ref = oracle.rollout_grad(sub, sub.init_state, a_np[:, pick], g_np[pick])
+    got = grad.cpu().numpy()[:, pick]
+    err = float(np.abs(got - ref).max() / np.abs(ref).max())
+    w.close()
+    print(json.dumps({
+        "form": "adjoint", "metric": "env-steps/s, differentiable rollout forward + backward",
+        "value": E * T / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+        "plain_step_value": E * T / (plain_ms / 1e3), "rollout_steps": T, "ckpt_every": K,
+        "grad_rel_err_vs_fp64_oracle": err, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%d envs x (8 agent spheres + 2 landmarks), 3 substeps, %d steps"
+                               % (E, T)}}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--form", choices=["plain", "adjoint"], default="plain",
+                    help="plain: the fused world step (the headline); adjoint: "
+                         "differentiable rollout forward + backward")
     ap.add_argument("--envs", type=int, default=30000)
     ap.add_argument("--substeps", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
@@ -400,6 +466,8 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "adjoint":
+        return run_adjoint(args)
     return run_native(args)
 
 

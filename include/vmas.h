@@ -176,6 +176,30 @@ int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
  * receives the VMAS_DEVERR_* bits seen. */
 int vmas_check(vmas_world *world, void *stream, int32_t *bits);
 
+/* ---- Differentiable rollout (sphere worlds) -----------------------------
+ * Loss per env = sum over its actuated entities k of |x_k(T) - goal_k|^2
+ * after n_steps world steps from the world's current state (which is left
+ * unchanged), and its gradient with respect to every action by a
+ * hand-written adjoint of the contact force (Eq. 2), drag and damped
+ * semi-implicit Euler (Eq. 1) over all substeps; the contact mask is held
+ * piecewise constant (no term from the force jump at gap 0).  Requires every
+ * entity to be a sphere, n_entities <= 32 and no speed cap (VMAS_EINVAL
+ * otherwise).
+ *   d_actions [n_steps][n_envs][n_actuated][3], d_goals [n_envs][n_actuated][2];
+ *   d_ckpt    [ceil(n_steps / ckpt_every)][n_envs][n_entities][4] (x y vx vy at
+ *             steps 0, ckpt_every, ...), written by vmas_diff_rollout and read
+ *             by vmas_diff_backward, which replays each segment on chip;
+ *   d_loss    [n_envs] (written);  d_dloss [n_envs] = d L / d loss_e;
+ *   d_grad    [n_steps][n_envs][n_actuated][3] (written; torque entries 0).
+ * All device memory, enqueued on `stream`.  ckpt_every * substeps is limited by
+ * shared memory (VMAS_EINVAL beyond about 200 substeps per segment). */
+int vmas_diff_rollout(vmas_world *world, const float *d_actions, int32_t n_steps,
+                      const float *d_goals, int32_t ckpt_every, float *d_ckpt, float *d_loss,
+                      void *stream);
+int vmas_diff_backward(vmas_world *world, const float *d_actions, int32_t n_steps,
+                       const float *d_goals, int32_t ckpt_every, const float *d_ckpt,
+                       const float *d_dloss, float *d_grad, void *stream);
+
 /* Diagnostic: the cosine and sine the step uses for a body angle, for n
  * device angles d_theta into device d_cos_sin [n][2] (cos, sin); the
  * library's own range reduction and series, absolute error about 1e-7. */

@@ -1,0 +1,267 @@
+// Differentiable rollout of sphere worlds (FP32, sm_103a): a forward pass
+// that writes state checkpoints, and a hand-written adjoint (reverse mode) of
+// the contact force, drag and damped semi-implicit Euler of VMAS section 3,
+// Eqs. 1-2, over every substep.
+//
+// Loss per env = sum over actuated entities k of |x_k(T) - goal_k|^2.  With
+// h = dt / S and a = 1 - zeta, one substep of a movable sphere is
+//   F_i = f^a_i + m_i g + sum_j f_ij,   v_i' = a v_i + (h / m_i) F_i,
+//   x_i' = x_i + h v_i',
+// f_ij = M(g) u, u = d / |d|, d = x_i - x_j, g = |d| - (r_i + r_j),
+// M = c k softplus(-g / k) when g <= 0.  Its Jacobian with respect to d is
+// J = M'(g) u u^T + M / |d| (I - u u^T), M'(g) = -c sigmoid(-g / k); J is
+// symmetric and the same for (i, j) and (j, i).  Given the adjoints lx', lv'
+// of a substep's outputs:
+//   w = lv' + h lx',  lF_i = (h / m_i) w,  lv = a w,
+//   lx_i = lx'_i + sum_j J_ij (lF_i - lF_j),   d loss / d f^a_i += lF_i.
+// The contact mask is piecewise constant (no term from the jump at g = 0);
+// forces on immovable entities are dropped, so their lF is 0.
+//
+// Layout: one warp per environment, entity i in lane i (N <= 32); the pair
+// sums of lane i run over j = 0 .. N-1 in order, the same order as a serial
+// loop over canonical pairs.  Checkpoints every K steps hold (x, y, vx, vy)
+// of every entity; the backward pass re-runs each K-step segment forward from
+// its checkpoint into shared memory (positions at every substep start) and
+// sweeps it backward, segments last to first.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "step.cuh"
+
+namespace vmas {
+
+constexpr int kDiffWarps = 4;  // environments per CTA
+
+struct DiffParams {
+  int E, N, A, S, T, K;
+  float h, damp, gx, gy, ck, inv_k, c;
+  const float *px, *py, *vx, *vy;  // initial state planes [E * N]
+  const float4 *param;             // {1/m, 1/I, r, 0}
+  const uint8_t *kind;
+  const float *actions;  // [T][E][A][3]
+  const float *goals;    // [E][A][2]
+  float *ckpt;           // [ceil(T / K)][E][N][4]
+  float *loss;           // [E]
+  const float *dloss;    // [E] upstream gradient
+  float *grad;           // [T][E][A][3]
+};
+
+// Pair force on i from j and (optionally) its Jacobian; false when apart.
+__device__ __forceinline__ bool sphere_force(float xi, float yi, float xj, float yj, float rsum,
+                                             const DiffParams &p, float &fx, float &fy,
+                                             float *J) {
+  const float dx = xi - xj, dy = yi - yj;
+  const float s = sqrtf(dx * dx + dy * dy);
+  const float g = s - rsum;
+  if (!(g <= 0.f) || !(s > 0.f)) return false;
+  const float inv = 1.f / s;
+  const float ux = dx * inv, uy = dy * inv;
+  const float M = p.ck * softplus_pos(-g * p.inv_k);
+  fx = M * ux;
+  fy = M * uy;
+  if (J) {
+    const float sig = 1.f / (1.f + expf(g * p.inv_k));  // sigmoid(-g / k)
+    const float dM = -p.c * sig;
+    const float t = M * inv;
+    J[0] = dM * ux * ux + t * (1.f - ux * ux);
+    J[1] = (dM - t) * ux * uy;
+    J[2] = dM * uy * uy + t * (1.f - uy * uy);
+  }
+  return true;
+}
+
+struct DiffLane {
+  bool ok, mov, act;
+  uint32_t kd;
+  float im, m, r;
+  int row;
+};
+
+__device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, int lane) {
+  DiffLane L{};
+  L.ok = lane < p.N;
+  const size_t t = (size_t)e * p.N + lane;
+  L.kd = L.ok ? p.kind[t] : 0u;
+  const float4 pr = L.ok ? p.param[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+  L.im = pr.x;
+  L.m = pr.x > 0.f ? 1.f / pr.x : 0.f;
+  L.r = pr.z;
+  L.mov = (L.kd & kMovable) != 0u;
+  L.act = (L.kd & kActuated) != 0u;
+  const unsigned bal = __ballot_sync(0xffffffffu, L.ok && L.act);
+  L.row = __popc(bal & ((1u << lane) - 1u));
+  if (L.row >= p.A) L.act = false;
+  return L;
+}
+
+// One forward substep for lane i; s_pos holds every entity's (x, y).
+__device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane &L, int lane,
+                                             const float2 *s_pos, const uint8_t *s_kind,
+                                             const float *s_r, float fax, float fay, float &x,
+                                             float &y, float &vx, float &vy) {
+  float Fx = fax + L.m * p.gx, Fy = fay + L.m * p.gy;
+  if (L.ok && (L.kd & kCollidable)) {
+    for (int j = 0; j < p.N; ++j) {
+      if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+      const float2 q = s_pos[j];
+      float fx, fy;
+      if (sphere_force(x, y, q.x, q.y, L.r + s_r[j], p, fx, fy, nullptr)) {
+        Fx += fx;
+        Fy += fy;
+      }
+    }
+  }
+  if (L.mov) {
+    vx = p.damp * vx + Fx * L.im * p.h;
+    vy = p.damp * vy + Fy * L.im * p.h;
+    x += vx * p.h;
+    y += vy * p.h;
+  }
+}
+
+__global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const DiffParams p) {
+  __shared__ float2 s_pos_all[kDiffWarps][32];
+  __shared__ uint8_t s_kind_all[kDiffWarps][32];
+  __shared__ float s_r_all[kDiffWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kDiffWarps + warp;
+  if (e >= p.E) return;  // whole warp leaves together
+  float2 *s_pos = s_pos_all[warp];
+  uint8_t *s_kind = s_kind_all[warp];
+  float *s_r = s_r_all[warp];
+  const DiffLane L = diff_lane(p, e, lane);
+  const size_t t0 = (size_t)e * p.N + lane;
+  float x = L.ok ? p.px[t0] : 0.f, y = L.ok ? p.py[t0] : 0.f;
+  float vx = L.ok ? p.vx[t0] : 0.f, vy = L.ok ? p.vy[t0] : 0.f;
+  s_kind[lane] = (uint8_t)L.kd;
+  s_r[lane] = L.r;
+  for (int t = 0; t < p.T; ++t) {
+    if (t % p.K == 0 && L.ok) {
+      float4 *c = reinterpret_cast<float4 *>(p.ckpt) + ((size_t)(t / p.K) * p.E + e) * p.N + lane;
+      *c = make_float4(x, y, vx, vy);
+    }
+    float fax = 0.f, fay = 0.f;
+    if (L.act) {
+      const float *a = p.actions + (((size_t)t * p.E + e) * p.A + L.row) * 3;
+      fax = a[0];
+      fay = a[1];
+    }
+    for (int s = 0; s < p.S; ++s) {
+      s_pos[lane] = make_float2(x, y);
+      __syncwarp();
+      diff_substep(p, L, lane, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
+      __syncwarp();
+    }
+  }
+  float l = 0.f;
+  if (L.act) {
+    const float *gl = p.goals + ((size_t)e * p.A + L.row) * 2;
+    const float dx = x - gl[0], dy = y - gl[1];
+    l = dx * dx + dy * dy;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (lane == 0) p.loss[e] = l;
+}
+
+// Dynamic shared memory per warp: positions at the K * S + 1 substep starts
+// of one segment.
+__host__ __device__ inline size_t diff_traj_bytes(int K, int S) {
+  return (size_t)(K * S + 1) * 32 * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const DiffParams p) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ float2 s_lf_all[kDiffWarps][32];
+  __shared__ uint8_t s_kind_all[kDiffWarps][32];
+  __shared__ float s_r_all[kDiffWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kDiffWarps + warp;
+  if (e >= p.E) return;
+  float2 *traj = reinterpret_cast<float2 *>(dsm + warp * diff_traj_bytes(p.K, p.S));
+  float2 *s_lf = s_lf_all[warp];
+  uint8_t *s_kind = s_kind_all[warp];
+  float *s_r = s_r_all[warp];
+  const DiffLane L = diff_lane(p, e, lane);
+  s_kind[lane] = (uint8_t)L.kd;
+  s_r[lane] = L.r;
+  float lx = 0.f, ly = 0.f, lvx = 0.f, lvy = 0.f;
+  const int nseg = (p.T + p.K - 1) / p.K;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int ta = seg * p.K, tb = min(p.T, ta + p.K);
+    // re-run the segment forward, keeping every substep-start position
+    const float4 c = L.ok ? reinterpret_cast<const float4 *>(p.ckpt)[((size_t)seg * p.E + e) * p.N + lane]
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    float x = c.x, y = c.y, vx = c.z, vy = c.w;
+    int q = 0;
+    for (int t = ta; t < tb; ++t) {
+      float fax = 0.f, fay = 0.f;
+      if (L.act) {
+        const float *a = p.actions + (((size_t)t * p.E + e) * p.A + L.row) * 3;
+        fax = a[0];
+        fay = a[1];
+      }
+      for (int s = 0; s < p.S; ++s, ++q) {
+        traj[q * 32 + lane] = make_float2(x, y);
+        __syncwarp();
+        diff_substep(p, L, lane, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
+        __syncwarp();
+      }
+    }
+    if (seg == nseg - 1 && L.act) {  // d loss / d x(T) = 2 (x - goal), scaled by the upstream
+      const float *gl = p.goals + ((size_t)e * p.A + L.row) * 2;
+      const float w = 2.f * p.dloss[e];
+      lx = w * (x - gl[0]);
+      ly = w * (y - gl[1]);
+    }
+    // sweep the segment backward
+    for (int t = tb - 1; t >= ta; --t) {
+      float gax = 0.f, gay = 0.f;
+      for (int s = p.S - 1; s >= 0; --s) {
+        --q;
+        float lfx = 0.f, lfy = 0.f;
+        if (L.mov) {
+          const float wx = lvx + p.h * lx, wy = lvy + p.h * ly;
+          lfx = p.h * L.im * wx;
+          lfy = p.h * L.im * wy;
+          lvx = p.damp * wx;
+          lvy = p.damp * wy;
+        }
+        gax += lfx;
+        gay += lfy;
+        s_lf[lane] = make_float2(lfx, lfy);
+        __syncwarp();
+        if (L.ok && (L.kd & kCollidable)) {
+          const float2 me = traj[q * 32 + lane];
+          for (int j = 0; j < p.N; ++j) {
+            if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+            const float2 o = traj[q * 32 + j];
+            float fx, fy, J[3];
+            if (sphere_force(me.x, me.y, o.x, o.y, L.r + s_r[j], p, fx, fy, J)) {
+              const float2 lj = s_lf[j];
+              const float dx = lfx - lj.x, dy = lfy - lj.y;
+              lx += J[0] * dx + J[1] * dy;
+              ly += J[1] * dx + J[2] * dy;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (L.act) {
+        float *g = p.grad + (((size_t)t * p.E + e) * p.A + L.row) * 3;
+        g[0] = gax;
+        g[1] = gay;
+        g[2] = 0.f;
+      }
+    }
+  }
+}
+
+// Zero the gradient rows of actuated slots no entity uses.
+__global__ void diff_zero_grad_kernel(float *grad, size_t n) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) grad[t] = 0.f;
+}
+
+}  // namespace vmas

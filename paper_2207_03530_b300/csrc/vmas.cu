@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "diff.cuh"
 #include "step_fused.cuh"
 #include "vmas.h"
 
@@ -36,6 +37,7 @@ struct vmas_world {
   int E = 0, N = 0, A = 0, S = 0, P = 0;
   float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0;
   float skin = 0;  // candidate-list margin
+  bool diff_ok = false;  // every entity a sphere, N <= 32 (differentiable rollout)
   float *planes = nullptr;  // 6 * E * N
   float4 *param = nullptr;
   unsigned long long *stats = nullptr;  // optional step counters
@@ -449,6 +451,11 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
   w->k = d->contact_margin;
   w->vmax = d->max_speed;
   {
+    bool spheres = N <= 32;
+    for (size_t t = 0; t < EN && spheres; ++t) spheres = d->shape[t] == VMAS_SPHERE;
+    w->diff_ok = spheres;
+  }
+  {
     // candidate-list margin: half the median bounding radius of the movable
     // entities (any value >= 0 gives the same results; this one balances
     // list length against rebuilds)
@@ -670,6 +677,89 @@ int vmas_debug_err_words(vmas_world *w, int32_t *out) {
   return cudaMemcpy(out, w->err, 3 * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : VMAS_ECUDA;
 }
 #endif
+
+static int diff_setup(vmas_world *w, int32_t T, int32_t K, vmas::DiffParams *p) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (!w->diff_ok)
+    return fail(VMAS_EINVAL, "the differentiable rollout needs a world of spheres with at most 32 entities");
+  if (w->vmax > 0) return fail(VMAS_EINVAL, "the differentiable rollout does not support a speed cap");
+  if (T < 0 || K < 1) return fail(VMAS_EINVAL, "n_steps must be >= 0 and ckpt_every >= 1");
+  *p = vmas::DiffParams{};
+  p->E = w->E;
+  p->N = w->N;
+  p->A = w->A;
+  p->S = w->S;
+  p->T = T;
+  p->K = K;
+  p->h = (float)((double)w->dt / (double)w->S);
+  p->damp = (float)(1.0 - (double)w->drag);
+  p->gx = w->gx;
+  p->gy = w->gy;
+  p->ck = (float)((double)w->c * (double)w->k);
+  p->inv_k = (float)(1.0 / (double)w->k);
+  p->c = w->c;
+  const size_t EN = (size_t)w->E * w->N;
+  p->px = w->planes;
+  p->py = w->planes + EN;
+  p->vx = w->planes + 2 * EN;
+  p->vy = w->planes + 3 * EN;
+  p->param = w->param;
+  p->kind = w->kind;
+  return VMAS_OK;
+}
+
+int vmas_diff_rollout(vmas_world *w, const float *d_actions, int32_t n_steps,
+                      const float *d_goals, int32_t ckpt_every, float *d_ckpt, float *d_loss,
+                      void *stream) {
+  vmas::DiffParams p;
+  int rc = diff_setup(w, n_steps, ckpt_every, &p);
+  if (rc) return rc;
+  if (w->E == 0) return VMAS_OK;
+  if (!d_loss || (w->A && (!d_goals || (n_steps && !d_actions))) || (n_steps && !d_ckpt))
+    return fail(VMAS_EINVAL, "NULL buffer");
+  p.actions = d_actions;
+  p.goals = d_goals;
+  p.ckpt = d_ckpt;
+  p.loss = d_loss;
+  const int grid = (w->E + vmas::kDiffWarps - 1) / vmas::kDiffWarps;
+  vmas::diff_forward_kernel<<<grid, vmas::kDiffWarps * 32, 0, as_stream(stream)>>>(p);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
+                       const float *d_goals, int32_t ckpt_every, const float *d_ckpt,
+                       const float *d_dloss, float *d_grad, void *stream) {
+  vmas::DiffParams p;
+  int rc = diff_setup(w, n_steps, ckpt_every, &p);
+  if (rc) return rc;
+  const size_t ng = (size_t)n_steps * w->E * w->A * 3;
+  if (ng == 0) return VMAS_OK;
+  if (!d_actions || !d_goals || !d_ckpt || !d_dloss || !d_grad)
+    return fail(VMAS_EINVAL, "NULL buffer");
+  const size_t per_warp = vmas::diff_traj_bytes(ckpt_every, w->S);
+  const size_t smem = per_warp * vmas::kDiffWarps;
+  if (smem > 220 * 1024)
+    return fail(VMAS_EINVAL, "ckpt_every * substeps too large for on-chip segment replay; "
+                             "use a shorter checkpoint interval");
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(vmas::diff_backward_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  cudaStream_t st = as_stream(stream);
+  vmas::diff_zero_grad_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(d_grad, ng);
+  VMAS_CUDA(cudaGetLastError());
+  p.actions = d_actions;
+  p.goals = d_goals;
+  p.ckpt = const_cast<float *>(d_ckpt);
+  p.dloss = d_dloss;
+  p.grad = d_grad;
+  const int grid = (w->E + vmas::kDiffWarps - 1) / vmas::kDiffWarps;
+  vmas::diff_backward_kernel<<<grid, vmas::kDiffWarps * 32, smem, st>>>(p);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
 
 int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void *stream) {
   if (n < 0 || (n > 0 && (!d_theta || !d_cos_sin))) return fail(VMAS_EINVAL, "bad arguments");

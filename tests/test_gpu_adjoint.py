@@ -1,0 +1,106 @@
+"""Differentiable rollout on the GPU (hand-written adjoint) against the FP64
+oracle's loss and reverse-mode gradient (itself pinned to central
+differences), through the C ABI and torch.autograd."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2207_03530_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n_envs, seed, dense=True, T=50):
+    from paper_2207_03530_b300 import World
+
+    sc = scenes.diff_scene(n_envs, seed, dense=dense)
+    act = scenes.make_actions(sc, T, seed + 1)
+    goals = scenes.make_goals(sc, seed + 2)
+    return sc, World(sc), act, goals
+
+
+def _relerr(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-12)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense):
+    """64 envs x 50 steps x 3 substeps: loss to 1e-4 and gradient to 2e-3 of
+    the oracle's (normwise, per tensor); FP32 through 150 substeps of stiff
+    contacts."""
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc, w, act, goals = _setup(64, 3, dense)
+    a = torch.from_numpy(act).cuda().requires_grad_(True)
+    g = torch.from_numpy(goals).cuda()
+    loss = rollout_loss(w, a, g, ckpt_every=10)
+    loss.sum().backward()
+    ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
+    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= 1e-4
+    err = _relerr(a.grad.cpu().numpy(), ref_grad)
+    assert err <= 2e-3, err
+    # the world's own state is untouched by the differentiable rollout
+    assert np.array_equal(w.state().cpu().numpy(), sc.init_state)
+    w.close()
+
+
+def test_full_config_gradient_on_sampled_envs(vmas_lib, orc):
+    """4,096 envs x (8 agents + 2 landmarks), 50 steps, checkpoint every 10:
+    4 sampled envs checked against the oracle's gradient."""
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc, w, act, goals = _setup(4096, 0, dense=False)
+    a = torch.from_numpy(act).cuda().requires_grad_(True)
+    loss = rollout_loss(w, a, torch.from_numpy(goals).cuda())
+    loss.sum().backward()
+    pick = np.array([0, 1234, 2047, 4095])
+    sub = sc.subset(pick)
+    ref_loss, ref_grad = orc.rollout_grad(sub, sub.init_state, act[:, pick], goals[pick])
+    assert _relerr(loss.detach().cpu().numpy()[pick], ref_loss) <= 1e-4
+    assert _relerr(a.grad.cpu().numpy()[:, pick], ref_grad) <= 2e-3
+    w.close()
+
+
+def test_checkpoint_interval_does_not_change_gradient(vmas_lib):
+    """Segments are replayed bit for bit, so the gradient is the same for any
+    checkpoint interval."""
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc, w, act, goals = _setup(48, 9, T=23)
+    g = torch.from_numpy(goals).cuda()
+    grads = []
+    for k in (1, 4, 10, 23, 40):
+        a = torch.from_numpy(act).cuda().requires_grad_(True)
+        rollout_loss(w, a, g, ckpt_every=k).sum().backward()
+        grads.append(a.grad.cpu().numpy())
+    for gr in grads[1:]:
+        assert np.array_equal(gr, grads[0])
+    w.close()
+
+
+def test_upstream_weights_scale_env_gradients(vmas_lib):
+    """d(sum_e w_e loss_e)/d a = w_e d loss_e / d a, env by env."""
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc, w, act, goals = _setup(16, 4, T=12)
+    g = torch.from_numpy(goals).cuda()
+    a1 = torch.from_numpy(act).cuda().requires_grad_(True)
+    rollout_loss(w, a1, g).sum().backward()
+    wts = torch.linspace(-2, 3, 16, device="cuda")
+    a2 = torch.from_numpy(act).cuda().requires_grad_(True)
+    (rollout_loss(w, a2, g) * wts).sum().backward()
+    expect = a1.grad * wts[None, :, None, None]
+    torch.testing.assert_close(a2.grad, expect, rtol=1e-6, atol=1e-7)
+    w.close()
+
+
+def test_rejects_non_sphere_worlds(vmas_lib):
+    from paper_2207_03530_b300 import World, _lib
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc = scenes.paper_scene(4, 0)
+    w = World(sc)
+    a = torch.zeros((2, 4, sc.n_actuated, 3), device="cuda", requires_grad=True)
+    with pytest.raises(_lib.VmasError):
+        rollout_loss(w, a, torch.zeros((4, sc.n_actuated, 2), device="cuda"))
+    w.close()
