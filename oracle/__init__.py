@@ -74,6 +74,9 @@ def _lib():
                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]
         h.ow_rollout_grad.restype = ctypes.c_int
+        h.ow_lidar.argtypes = [ctypes.POINTER(_World), ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_void_p]
+        h.ow_lidar.restype = ctypes.c_int
         _handle = h
     return _handle
 
@@ -181,3 +184,14 @@ def rollout_grad(scene, state, actions, goals, with_grad=True):
     if rc != 0:
         raise ValueError("rollout_grad needs a sphere world without a speed cap")
     return loss, grad
+
+
+def lidar(scene, state, n_rays: int, max_range: float) -> np.ndarray:
+    """Ray-cast distances [E, n_actuated, n_rays] from every actuated entity
+    (angles theta + 2 pi k / n_rays), FP64."""
+    pk = _Packed(scene)
+    E, N, A = int(scene.n_envs), int(scene.n_entities), int(scene.n_actuated)
+    st = np.ascontiguousarray(np.asarray(state, np.float64).reshape(E, N, 6))
+    out = np.zeros((E, A, n_rays), np.float64)
+    _lib().ow_lidar(ctypes.byref(pk.w), st.ctypes.data, n_rays, float(max_range), out.ctypes.data)
+    return out

@@ -885,3 +885,88 @@ int ow_rollout_grad(const ow_world *w, const double *state, const double *action
   free(lF);
   return 0;
 }
+
+/* ------------------------------------------------------------------ LIDAR
+ * Ray casts (section 3: agents can carry LIDAR sensors).  Every actuated
+ * entity casts n_rays rays from its centre at angles th + 2 pi k / n_rays
+ * (k = 0 .. n_rays-1); a ray reports the smallest distance t in [0, range]
+ * at which it meets another collidable entity (0 when its origin is inside
+ * one), or `range` when it meets none.  The caster itself is excluded.
+ * Shapes: sphere = disc of radius r, box = filled rectangle, line = segment
+ * (a ray exactly parallel to a segment does not meet it). */
+
+/* Smallest t >= 0 at which o + t d enters the shape, or INFINITY. */
+static double ray_shape(double ox, double oy, double dx, double dy, const ow_body *b) {
+  if (b->shape == OW_SPHERE) {
+    double px = ox - b->x, py = oy - b->y;
+    double c = px * px + py * py - b->a * b->a;
+    if (c <= 0) return 0.0; /* origin inside */
+    double bq = px * dx + py * dy;
+    double disc = bq * bq - c;
+    if (disc < 0) return INFINITY;
+    double t = -bq - sqrt(disc);
+    return t >= 0 ? t : INFINITY;
+  }
+  double cs = cos(b->th), sn = sin(b->th);
+  /* ray in the body frame */
+  double lx = cs * (ox - b->x) + sn * (oy - b->y), ly = -sn * (ox - b->x) + cs * (oy - b->y);
+  double ldx = cs * dx + sn * dy, ldy = -sn * dx + cs * dy;
+  if (b->shape == OW_BOX) {
+    double hw = 0.5 * b->a, hh = 0.5 * b->b;
+    if (fabs(lx) <= hw && fabs(ly) <= hh) return 0.0;
+    /* slabs */
+    double tmin = -INFINITY, tmax = INFINITY;
+    double o[2] = {lx, ly}, d[2] = {ldx, ldy}, h[2] = {hw, hh};
+    for (int q = 0; q < 2; ++q) {
+      if (d[q] == 0) {
+        if (fabs(o[q]) > h[q]) return INFINITY;
+      } else {
+        double t1 = (-h[q] - o[q]) / d[q], t2 = (h[q] - o[q]) / d[q];
+        if (t1 > t2) { double tt = t1; t1 = t2; t2 = tt; }
+        if (t1 > tmin) tmin = t1;
+        if (t2 < tmax) tmax = t2;
+      }
+    }
+    if (tmin > tmax || tmax < 0) return INFINITY;
+    return tmin >= 0 ? tmin : 0.0;
+  }
+  /* line: segment from (-L/2, 0) to (L/2, 0) in the body frame */
+  if (ldy == 0) return INFINITY;
+  double t = -ly / ldy;
+  if (t < 0) return INFINITY;
+  double xh = lx + t * ldx;
+  if (fabs(xh) > 0.5 * b->a) return INFINITY;
+  return t;
+}
+
+/* out [E][A][n_rays]; rows of actuated slots an env does not use stay at
+ * `range`. */
+int ow_lidar(const ow_world *w, const double *state, int n_rays, double range, double *out) {
+  int E = w->n_envs, N = w->n_entities, A = w->n_actuated;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (size_t q = 0; q < (size_t)E * A * n_rays; ++q) out[q] = range;
+  for (int e = 0; e < E; ++e) {
+    size_t base = (size_t)e * N;
+    const double *st = state + base * 6;
+    int a = 0;
+    for (int i = 0; i < N; ++i) {
+      if (!(w->flags[base + i] & OW_ACTUATED)) continue;
+      if (a >= A) break;
+      for (int k = 0; k < n_rays; ++k) {
+        double ang = st[6 * i + 4] + two_pi * k / n_rays;
+        double dx = cos(ang), dy = sin(ang);
+        double best = range;
+        for (int j = 0; j < N; ++j) {
+          if (j == i || !(w->flags[base + j] & OW_COLLIDABLE)) continue;
+          ow_body bj;
+          load_body(w, st, base, j, &bj);
+          double t = ray_shape(st[6 * i], st[6 * i + 1], dx, dy, &bj);
+          if (t < best) best = t;
+        }
+        out[((size_t)e * A + a) * n_rays + k] = best;
+      }
+      ++a;
+    }
+  }
+  return 0;
+}
