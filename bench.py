@@ -445,13 +445,42 @@ def run_adjoint(args):
     return 0
 
 
+def run_lidar(args):
+    """LIDAR on the paper-scale scene: 20 agents x 32 rays per env."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+
+    build.build()
+    torch.cuda.set_device(0)
+    sc = scenes.paper_scene(args.envs, args.seed)
+    w = World(sc)
+    for _ in range(max(3, args.warmup)):
+        w.lidar(32, 1.0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        w.lidar(32, 1.0)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    rays = args.envs * sc.n_actuated * 32
+    w.close()
+    print(json.dumps({"form": "lidar", "metric": "rays/s", "value": rays / (ms / 1e3),
+                      "unit": "rays/s", "ms_per_call": ms, "env_scans_per_s": args.envs / (ms / 1e3),
+                      "config": {"workload": "%d envs x 20 agents x 32 rays vs 24 bodies"
+                                             % args.envs}}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--form", choices=["plain", "adjoint"], default="plain",
+    ap.add_argument("--form", choices=["plain", "adjoint", "lidar"], default="plain",
                     help="plain: the fused world step (the headline); adjoint: "
                          "differentiable rollout forward + backward")
     ap.add_argument("--envs", type=int, default=30000)
@@ -468,6 +497,8 @@ def main(argv=None):
         return run_reference(args)
     if args.form == "adjoint":
         return run_adjoint(args)
+    if args.form == "lidar":
+        return run_lidar(args)
     return run_native(args)
 
 

@@ -176,6 +176,16 @@ int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
  * receives the VMAS_DEVERR_* bits seen. */
 int vmas_check(vmas_world *world, void *stream, int32_t *bits);
 
+/* LIDAR (section 3: agents can carry LIDAR sensors).  Every actuated
+ * entity of every env casts n_rays rays from its centre at angles
+ * theta + 2 pi k / n_rays (k = 0 .. n_rays-1) against the other collidable
+ * entities of its env, from the current state; d_out [n_envs][n_actuated]
+ * [n_rays] (device) receives the distance to the first entry into a sphere,
+ * box or line segment, 0 when the ray starts inside one, max_range when it
+ * meets none (also for action rows an env does not use).  A ray exactly
+ * parallel to a segment misses it.  Enqueues one kernel on `stream`. */
+int vmas_lidar(vmas_world *world, int32_t n_rays, float max_range, float *d_out, void *stream);
+
 /* ---- Differentiable rollout (sphere worlds) -----------------------------
  * Loss per env = sum over its actuated entities k of |x_k(T) - goal_k|^2
  * after n_steps world steps from the world's current state (which is left

@@ -20,6 +20,7 @@ SYMBOLS = (
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
     "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
     "vmas_debug_body_axes", "vmas_step_noalloc", "vmas_diff_rollout", "vmas_diff_backward",
+    "vmas_lidar",
 )
 STATS_COUNT = 16
 STATS_NAMES = ("env_steps", "rebuilds", "candidates",
@@ -97,6 +98,7 @@ def load():
         "vmas_step_noalloc": ([P(StepNoallocArgs), vp], ctypes.c_int),
         "vmas_diff_rollout": ([vp, vp, i32, vp, i32, vp, vp, vp], ctypes.c_int),
         "vmas_diff_backward": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], ctypes.c_int),
+        "vmas_lidar": ([vp, i32, ctypes.c_float, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -13,6 +13,9 @@
 #include <stdint.h>
 
 #include "contact.cuh"
+#include "vmas.h"
+
+#define VMAS_LIDAR_MAX_ENTITIES VMAS_MAX_ENTITIES
 
 namespace vmas {
 

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "diff.cuh"
+#include "lidar.cuh"
 #include "step_fused.cuh"
 #include "vmas.h"
 
@@ -757,6 +758,31 @@ int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
   p.grad = d_grad;
   const int grid = (w->E + vmas::kDiffWarps - 1) / vmas::kDiffWarps;
   vmas::diff_backward_kernel<<<grid, vmas::kDiffWarps * 32, smem, st>>>(p);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (n_rays < 1 || !(max_range >= 0) || !std::isfinite(max_range))
+    return fail(VMAS_EINVAL, "n_rays must be >= 1 and max_range >= 0");
+  if ((size_t)w->E * w->A == 0) return VMAS_OK;
+  if (!d_out) return fail(VMAS_EINVAL, "d_out is NULL");
+  vmas::LidarParams p{};
+  p.E = w->E;
+  p.N = w->N;
+  p.A = w->A;
+  p.R = n_rays;
+  p.range = max_range;
+  const size_t EN = (size_t)w->E * w->N;
+  p.px = w->planes;
+  p.py = w->planes + EN;
+  p.th = w->planes + 4 * EN;
+  p.param = w->param;
+  p.kind = w->kind;
+  p.out = d_out;
+  const size_t smem = (size_t)w->N * (16 + 8 + 1) + 16;
+  vmas::lidar_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
 }

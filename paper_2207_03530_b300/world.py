@@ -140,6 +140,15 @@ class World:
                                             _stream_handle(stream)))
         return out
 
+    def lidar(self, n_rays: int, max_range: float, stream=None) -> torch.Tensor:
+        """LIDAR distances [E, n_actuated, n_rays] from the current state."""
+        out = torch.empty((self.n_envs, self.n_actuated, n_rays), dtype=torch.float32,
+                          device=self.device)
+        _lib.check(self._L.vmas_lidar(self._handle(), int(n_rays), float(max_range),
+                                      out.data_ptr() if out.numel() else None,
+                                      _stream_handle(stream)))
+        return out
+
     def pair_table(self):
         pi = np.zeros(max(self.n_pairs, 1), np.int32)
         pj = np.zeros(max(self.n_pairs, 1), np.int32)
