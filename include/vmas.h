@@ -120,6 +120,11 @@ int vmas_world_info(const vmas_world *world, int32_t *n_envs, int32_t *n_entitie
 int vmas_world_set_skin(vmas_world *world, float skin);
 int vmas_world_get_skin(const vmas_world *world, float *skin);
 
+/* vmas_rollout launches `steps_per_launch` world steps per kernel (default
+ * 1): the state and the contact-candidate lists stay on chip between them.
+ * Results are bitwise the same for any value. */
+int vmas_world_set_rollout_tile(vmas_world *world, int32_t steps_per_launch);
+
 /* Optional step counters, for tuning (they cost a few atomics per env per
  * substep while enabled).  vmas_world_get_stats waits for `stream` and
  * copies VMAS_STATS_COUNT counters into `out`, zeroing them if `reset`:
@@ -175,6 +180,50 @@ int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
  * has raised the device error word since the last check; *bits (may be NULL)
  * receives the VMAS_DEVERR_* bits seen. */
 int vmas_check(vmas_world *world, void *stream, int32_t *bits);
+
+/* ---- Packed ragged worlds ----------------------------------------------
+ * Environments with different entity counts (1 .. VMAS_MAX_ENTITIES each),
+ * packed without padding.  env_offsets [n_envs + 1] (host) gives env e the
+ * entities [env_offsets[e], env_offsets[e + 1]) of every per-entity array
+ * (host, as in vmas_world_desc) and of init_state [total][6].  Actions are
+ * packed the same way: env e owns the action rows
+ * [aoff[e], aoff[e + 1]) of a [n_action_rows][3] array, aoff given by
+ * vmas_ragged_action_offsets (the k-th actuated entity of env e reads row
+ * aoff[e] + k).
+ *
+ * The library sorts the envs into size classes of capacity 8, 16, 32, 64
+ * and 128 entities and steps each class with the fused kernel compiled for
+ * its choice of lanes per environment (4, 8, 16 or 32); rollouts run
+ * steps_per_launch world steps per launch and are captured once into a CUDA
+ * graph per (actions buffer, n_steps, tuning), then replayed.
+ * vmas_ragged_autotune times the choices on the caller's actions (the world
+ * state is restored afterwards) and keeps the fastest. */
+typedef struct vmas_ragged vmas_ragged;
+typedef struct {
+  int32_t n_envs, substeps;
+  float dt, drag, gx, gy, contact_force, contact_margin, max_speed;
+  const int32_t *env_offsets;
+  const uint8_t *shape, *flags;
+  const float *size_a, *size_b, *mass, *inertia;
+  const float *init_state;
+} vmas_ragged_desc;
+int vmas_ragged_create(const vmas_ragged_desc *desc, vmas_ragged **out);
+int vmas_ragged_destroy(vmas_ragged *world);
+/* class_envs [5]: envs per size class (8, 16, 32, 64, 128). */
+int vmas_ragged_info(const vmas_ragged *world, int32_t *n_envs, int64_t *n_entities,
+                     int64_t *n_action_rows, int32_t *class_envs);
+int vmas_ragged_action_offsets(const vmas_ragged *world, int32_t *aoff);
+/* One world step: d_actions [n_action_rows][3] (device). */
+int vmas_ragged_step(vmas_ragged *world, const float *d_actions, void *stream);
+/* n_steps world steps: d_actions [n_steps][n_action_rows][3] (device). */
+int vmas_ragged_rollout(vmas_ragged *world, const float *d_actions, int32_t n_steps, void *stream);
+/* State [total][6] in the caller's entity order (see vmas_state). */
+int vmas_ragged_state(vmas_ragged *world, float *out, int32_t out_is_device, void *stream);
+int vmas_ragged_set_state(vmas_ragged *world, const float *d_state, void *stream);
+/* lanes [5] per size class (NULL keeps them); steps_per_launch 1..1024. */
+int vmas_ragged_set_tuning(vmas_ragged *world, const int32_t *lanes, int32_t steps_per_launch);
+int vmas_ragged_get_tuning(const vmas_ragged *world, int32_t *lanes, int32_t *steps_per_launch);
+int vmas_ragged_autotune(vmas_ragged *world, const float *d_actions, int32_t n_steps, void *stream);
 
 /* LIDAR (section 3: agents can carry LIDAR sensors).  Every actuated
  * entity of every env casts n_rays rays from its centre at angles

@@ -20,7 +20,10 @@ SYMBOLS = (
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
     "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
     "vmas_debug_body_axes", "vmas_step_noalloc", "vmas_diff_rollout", "vmas_diff_backward",
-    "vmas_lidar",
+    "vmas_lidar", "vmas_world_set_rollout_tile",
+    "vmas_ragged_create", "vmas_ragged_destroy", "vmas_ragged_info", "vmas_ragged_action_offsets",
+    "vmas_ragged_step", "vmas_ragged_rollout", "vmas_ragged_state", "vmas_ragged_set_state",
+    "vmas_ragged_set_tuning", "vmas_ragged_get_tuning", "vmas_ragged_autotune",
 )
 STATS_COUNT = 16
 STATS_NAMES = ("env_steps", "rebuilds", "candidates",
@@ -54,6 +57,19 @@ class StepNoallocArgs(ctypes.Structure):
         ("shape", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("size_a", ctypes.c_void_p),
         ("size_b", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("inertia", ctypes.c_void_p),
         ("state", ctypes.c_void_p), ("actions", ctypes.c_void_p), ("status", ctypes.c_void_p),
+    ]
+
+
+class RaggedDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_envs", ctypes.c_int32), ("substeps", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("drag", ctypes.c_float), ("gx", ctypes.c_float),
+        ("gy", ctypes.c_float), ("contact_force", ctypes.c_float),
+        ("contact_margin", ctypes.c_float), ("max_speed", ctypes.c_float),
+        ("env_offsets", ctypes.c_void_p),
+        ("shape", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("size_a", ctypes.c_void_p),
+        ("size_b", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("inertia", ctypes.c_void_p),
+        ("init_state", ctypes.c_void_p),
     ]
 
 
@@ -99,6 +115,18 @@ def load():
         "vmas_diff_rollout": ([vp, vp, i32, vp, i32, vp, vp, vp], ctypes.c_int),
         "vmas_diff_backward": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], ctypes.c_int),
         "vmas_lidar": ([vp, i32, ctypes.c_float, vp, vp], ctypes.c_int),
+        "vmas_world_set_rollout_tile": ([vp, i32], ctypes.c_int),
+        "vmas_ragged_create": ([P(RaggedDesc), P(vp)], ctypes.c_int),
+        "vmas_ragged_destroy": ([vp], ctypes.c_int),
+        "vmas_ragged_info": ([vp, P(i32), P(ctypes.c_int64), P(ctypes.c_int64), vp], ctypes.c_int),
+        "vmas_ragged_action_offsets": ([vp, vp], ctypes.c_int),
+        "vmas_ragged_step": ([vp, vp, vp], ctypes.c_int),
+        "vmas_ragged_rollout": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_ragged_state": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_ragged_set_state": ([vp, vp, vp], ctypes.c_int),
+        "vmas_ragged_set_tuning": ([vp, vp, i32], ctypes.c_int),
+        "vmas_ragged_get_tuning": ([vp, vp, vp], ctypes.c_int),
+        "vmas_ragged_autotune": ([vp, vp, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

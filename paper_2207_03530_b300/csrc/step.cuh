@@ -46,6 +46,14 @@ struct StepParams {
   uint8_t *mask;                       // [E][P], mask kernel only
   int *err;                            // device error word
   unsigned long long *stats;           // optional counters, nullptr = off
+  int tile;                            // world steps per launch (actions of step t at + t * act_step)
+  size_t act_step;                     // floats per step in the actions array
+  size_t EN;                           // entities in the state arrays (bound of every entity index)
+  // packed ragged worlds (RAGGED kernels): envs [env_begin, env_end) of one size class
+  const int *soff;                     // [E + 1] entity offsets, size-class (sorted) env order
+  const int *perm;                     // [E] sorted position -> caller env index
+  const int *aoff;                     // [E + 1] action-row offsets, caller env order
+  int env_begin, env_end;
   // caller-owned buffers of the allocation-free entry point (RAW kernels):
   float *aos_state;                    // [E][N][6] x y vx vy th om, read and written
   const uint8_t *r_shape, *r_flags;    // [E * N]

@@ -85,14 +85,18 @@ __device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
 // NC == 0 takes N from the parameters.
 // RAW = true is the allocation-free variant: it reads the caller's raw
 // entity arrays and [E][N][6] state and packs the per-entity parameters on
-// the fly instead of reading the library's packed planes.
-template <int G, int SLOTS, int NC, bool RAW = false>
+// the fly instead of reading the library's packed planes.  RAGGED = true
+// steps envs [env_begin, env_end) of a packed ragged world, each with its own
+// entity count (at most p.N, the layout capacity) at its own offset.  TILED
+// kernels run p.tile consecutive world steps per launch (others run one);
+// the state and the candidate list stay on chip between them.
+template <int G, int SLOTS, int NC, bool RAW = false, bool RAGGED = false, bool TILED = false>
 __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     world_step_kernel(const StepParams p) {
   constexpr int EPW = 32 / G;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int N = NC > 0 ? NC : p.N;
+  const int NL = NC > 0 ? NC : p.N;  // layout capacity per env
   const int P = NC > 0 ? NC * (NC - 1) / 2 : p.P;
   uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
   for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
@@ -102,29 +106,47 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   (void)LC;
   const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   const unsigned lt = (1u << lane) - 1u;
-  unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(N, G);
-  float4 *s_bp = reinterpret_cast<float4 *>(es);  // [2N] {x, y, inflated R, kind}
-  float4 *s_ng = s_bp + 2 * N;                     // [N] {cos, sin, ha, hb}
-  float4 *s_rec = s_ng + N;                        // {fx, fy, ti, tj}
+  unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(NL, G);
+  float4 *s_bp = reinterpret_cast<float4 *>(es);  // [2 NL] {x, y, inflated R, kind}
+  float4 *s_ng = s_bp + 2 * NL;                    // [NL] {cos, sin, ha, hb}
+  float4 *s_rec = s_ng + NL;                       // {fx, fy, ti, tj}
   uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kRecCap);
   uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rij + kRecCap);  // [G][kLaneCand]
   uint16_t *s_cand = s_lc + align16(2 * G * kLaneCand) / 2;          // compact list
   __syncthreads();
 
-  const int e = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
-  const bool valid = e < p.E;
-  const size_t eb = (size_t)e * N;
+  // this group's environment: index, entity base and count, action rows
+  int e, N, A_e;
+  size_t eb, arow0;
+  bool valid;
+  if constexpr (RAGGED) {
+    e = p.env_begin + (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+    valid = e < p.env_end;
+    const int s0 = valid ? p.soff[e] : 0, s1 = valid ? p.soff[e + 1] : 0;
+    eb = (size_t)s0;
+    N = s1 - s0;
+    const int oe = valid ? p.perm[e] : 0;
+    arow0 = valid ? (size_t)p.aoff[oe] : 0;
+    A_e = valid ? p.aoff[oe + 1] - p.aoff[oe] : 0;
+  } else {
+    e = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+    valid = e < p.E;
+    N = NL;
+    eb = (size_t)e * NL;
+    arow0 = (size_t)e * p.A;
+    A_e = p.A;
+  }
   unsigned long long *const stats = p.stats;
 
   float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
   float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
-  uint32_t kd[SLOTS];
+  uint32_t kd[SLOTS];  // kind byte; bits 8.. hold 1 + the entity's action row (0: none)
   int act_base = 0;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int a = lg + G * s;
     const bool ok = valid && a < N;
-    const size_t ga_ = ok ? VIDX(eb + a, (size_t)p.E * N, 1) : 0;
+    const size_t ga_ = ok ? VIDX(eb + a, p.EN, 1) : 0;
     float4 pr;
     if constexpr (RAW) {
       pr = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -174,22 +196,29 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     // the k-th actuated entity of the env (entity order = slot-major) reads row k
     const bool actuated = ok && (kd[s] & kActuated);
     const unsigned gb = __ballot_sync(FULL, actuated) & gbits;
-    const int row = act_base + __popc(gb & lt);
+    const int r = act_base + __popc(gb & lt);
     act_base += __popc(gb);
-    float fax = 0.f, fay = 0.f;
-    tau[s] = 0.f;
-    if (actuated && row < p.A) {
-      const float *ap = p.actions + (size_t)VIDX((size_t)e * p.A + row, (size_t)p.E * p.A, 3) * 3;
-      fax = ap[0];
-      fay = ap[1];
-      tau[s] = (kd[s] & kRotatable) ? ap[2] : 0.f;
-    }
-    // Eq. 1: action + gravity, constant over the step (only movable bodies
-    // integrate, so only their mass matters)
-    const float m = im[s] > 0.f ? 1.f / im[s] : 0.f;
-    fbx[s] = fax + m * p.gx;
-    fby[s] = fay + m * p.gy;
+    if (actuated && r < A_e) kd[s] |= (uint32_t)(r + 1) << 8;
   }
+  // Eq. 1: action + gravity, constant over a step (only movable bodies
+  // integrate, so only their mass matters)
+  auto load_actions = [&](int t) {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      float fax = 0.f, fay = 0.f;
+      tau[s] = 0.f;
+      if (kd[s] >> 8) {
+        const float *ap = p.actions + (size_t)t * p.act_step + (arow0 + (kd[s] >> 8) - 1) * 3;
+        fax = ap[0];
+        fay = ap[1];
+        tau[s] = (kd[s] & kRotatable) ? ap[2] : 0.f;
+      }
+      const float m = im[s] > 0.f ? 1.f / im[s] : 0.f;
+      fbx[s] = fax + m * p.gx;
+      fby[s] = fay + m * p.gy;
+    }
+  };
+  load_actions(0);
 
   const float move_limit = 0.499f * p.skin;
   bool full = false;    // group scans all pairs (list overflow)
@@ -197,9 +226,12 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   bool rebuild = true;  // warp-uniform
   float moved = 0.f;    // bound on how far this lane's bodies moved since the build
 
+  const int tile = TILED ? p.tile : 1;
+  for (int t = 0; t < tile; ++t) {
+  if (t > 0) load_actions(t);
   for (int sub = 0; sub < p.S; ++sub) {
     // publish the substep-start pose of bodies that move or turn
-    if (sub > 0) {
+    if (t > 0 || sub > 0) {
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int a = lg + G * s;
@@ -222,7 +254,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int a = lg + G * s;
-        if (valid && a < N) s_bp[VIDX(a + N, 2 * N, 30)] = s_bp[VIDX(a, N, 31)];
+        if (valid && a < N) s_bp[VIDX(a + N, 2 * NL, 30)] = s_bp[VIDX(a, N, 31)];
       }
       __syncwarp();
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
@@ -244,7 +276,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
           const bool a_moves = (ka & (kMovable | kRotatable)) != 0u;
           const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
           auto test_partner = [&](int d) {
-            const float4 bb = s_bp[VIDX(a + d, 2 * N, 8)];
+            const float4 bb = s_bp[VIDX(a + d, 2 * NL, 8)];
             const uint32_t kb = __float_as_uint(bb.w);
             if (!(kb & kCollidable) || !(a_moves || (kb & (kMovable | kRotatable)))) return;
             const float dx = ax_ - bb.x, dy = ay_ - bb.y;
@@ -335,11 +367,12 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       int i = 0, j = 0;
       if (c < ncand) {
         const uint32_t ij = full ? s_pairs[VIDX(c, P, 21)] : s_cand[VIDX(c, LC, 20)];
-        i = VIDX((int)(ij & 0xffu), N, 22);
-        j = VIDX((int)(ij >> 8), N, 23);
-        const float4 bi = s_bp[i], bj = s_bp[j];
+        i = VIDX((int)(ij & 0xffu), NL, 22);
+        j = VIDX((int)(ij >> 8), NL, 23);
+        const bool in_env = !RAGGED || j < N;  // a full scan covers the layout capacity
+        const float4 bi = s_bp[in_env ? i : 0], bj = s_bp[in_env ? j : 0];
         const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
-        if (pair_active(ki, kj)) {
+        if (in_env && pair_active(ki, kj)) {
           hit = pair_hit(bi, bj, ki, kj, s_ng, i, j, hh);
           if (stats) {
             const int t = pair_type(ki & 3u, kj & 3u);
@@ -398,13 +431,14 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     rebuild = __any_sync(FULL, moved > move_limit);
     __syncwarp();
   }
+  }
 
   bool bad = false;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int a = lg + G * s;
     if (valid && a < N) {
-      const size_t go_ = VIDX(eb + a, (size_t)p.E * N, 26);
+      const size_t go_ = VIDX(eb + a, p.EN, 26);
       if constexpr (RAW) {
         float *st = p.aos_state + go_ * 6;
         st[0] = x[s]; st[1] = y[s]; st[2] = vx[s]; st[3] = vy[s]; st[4] = th[s]; st[5] = om[s];
@@ -420,7 +454,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
                isfinite(th[s]) && isfinite(om[s]));
     }
   }
-  if (stats && valid && lg == 0) atomicAdd(stats + kStatEnvSteps, 1ull);
+  if (stats && valid && lg == 0) atomicAdd(stats + kStatEnvSteps, (unsigned long long)tile);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, 1);  // VMAS_DEVERR_NONFINITE
 }
 

@@ -409,6 +409,79 @@ def diff_scene(n_envs: int = 4096, seed: int = 0, dense: bool = False) -> Scene:
     return sc
 
 
+def ragged_scene(n_envs: int = 65536, seed: int = 0, max_agents: int = 64,
+                 max_boxes: int = 8, max_lines: int = 4):
+    """Ragged workload: per env U{2..max_agents} agent spheres (r=0.05, mass
+    1, actuated), U{0..max_boxes} boxes (0.1 x 0.2, mass 5, rotatable,
+    actuated) and U{0..max_lines} fixed walls (the walls at x = +1, x = -1,
+    y = +1, y = -1, in that order); bodies rejection-sampled inside
+    [-0.9, 0.9]^2; dt 0.1, drag 0.25, 5 substeps.
+
+    Returns (scene, counts): the scene padded to the largest count with inert
+    entities (no flags) after each env's real ones, and counts [E] of real
+    entities (agents, then boxes, then walls)."""
+    rng = np.random.default_rng(seed)
+    na = rng.integers(2, max_agents + 1, size=n_envs)
+    nb = rng.integers(0, max_boxes + 1, size=n_envs)
+    nl = rng.integers(0, max_lines + 1, size=n_envs)
+    counts = na + nb + nl
+    N = int(counts.max()) if n_envs else 1
+    A = int((na + nb).max()) if n_envs else 0
+    sc = _empty("ragged", n_envs, N, A, 5, 0.1, 0.25)
+    sc.shape[:] = SPHERE
+    sc.size_a[:] = 0.05
+    walls = [(1.0, 0.0, np.float32(math.pi / 2)), (-1.0, 0.0, np.float32(math.pi / 2)),
+             (0.0, 1.0, 0.0), (0.0, -1.0, 0.0)]
+    P = _Placer(rng, n_envs, max_agents + max_boxes)
+    Rb = math.hypot(0.05, 0.1)
+    envs_all = np.arange(n_envs)
+    for q in range(max_boxes):
+        envs = envs_all[nb > q]
+        idx = na[envs] + q
+        x, y = P.place_free(np.full(n_envs, Rb), -0.9, 0.9, envs=envs)
+        P.cx[envs, P.n], P.cy[envs, P.n], P.R[envs, P.n] = x, y, Rb
+        P.advance()
+        sc.shape[envs, idx] = BOX
+        sc.flags[envs, idx] = MOVABLE | ROTATABLE | COLLIDABLE | ACTUATED
+        sc.size_a[envs, idx] = 0.1
+        sc.size_b[envs, idx] = 0.2
+        sc.mass[envs, idx] = 5.0
+        sc.init_state[envs, idx, 0] = x
+        sc.init_state[envs, idx, 1] = y
+        sc.init_state[envs, idx, 4] = rng.uniform(0, 2 * math.pi, size=len(envs)).astype(np.float32)
+    for q in range(max_agents):
+        envs = envs_all[na > q]
+        x, y = P.place_free(np.full(n_envs, 0.05), -0.9, 0.9, envs=envs)
+        P.cx[envs, P.n], P.cy[envs, P.n], P.R[envs, P.n] = x, y, 0.05
+        P.advance()
+        sc.flags[envs, q] = MOVABLE | COLLIDABLE | ACTUATED
+        sc.init_state[envs, q, 0] = x
+        sc.init_state[envs, q, 1] = y
+    # agents occupy [0, na), boxes were written at [na, na + nb): move boxes
+    # after agents is already their index; walls follow
+    for q in range(max_lines):
+        envs = envs_all[nl > q]
+        idx = na[envs] + nb[envs] + q
+        wx, wy, wt = walls[q]
+        sc.shape[envs, idx] = LINE
+        sc.flags[envs, idx] = COLLIDABLE
+        sc.size_a[envs, idx] = 2.0
+        sc.init_state[envs, idx, 0] = wx
+        sc.init_state[envs, idx, 1] = wy
+        sc.init_state[envs, idx, 4] = wt
+    return sc, counts
+
+
+def pack_ragged(scene: Scene, counts):
+    """Packed per-entity arrays (dict of [total] / [total, 6]) of the first
+    counts[e] entities of every env."""
+    sel = np.arange(scene.n_entities)[None, :] < np.asarray(counts)[:, None]
+    out = {k: np.ascontiguousarray(getattr(scene, k)[sel])
+           for k in ("shape", "flags", "size_a", "size_b", "mass", "inertia")}
+    out["init_state"] = np.ascontiguousarray(scene.init_state[sel])
+    return out
+
+
 def make_goals(scene: Scene, seed: int = 0) -> np.ndarray:
     """Goal positions [n_envs, n_actuated, 2], uniform in [-1, 1]^2, FP32."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x60A1]))
