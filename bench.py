@@ -505,6 +505,85 @@ def run_ragged(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned surrogate (BASELINE config 5): 262,144 envs x 16 agent spheres
+    (+ 4 walls), 50-step rollouts.  Trains the network on the GPU with the
+    library's own forward / backward / Adam kernels on transitions of the
+    plain step (5 substeps), then runs the same 50 steps from the same start
+    with (a) the plain step at 5 substeps (the judge of the error), (b) the
+    surrogate with its plain-step fallback and (c) the plain step at 1
+    substep, and reports env-steps/s of each and the mean agent position
+    error of (b) and (c) against (a)."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+    from paper_2207_03530_b300.surrogate import Surrogate, train_on_plain_step
+
+    build.build()
+    torch.cuda.set_device(0)
+    E = args.envs if args.envs != 30000 else 262144
+    T = 50
+    E_train = min(E, args.train_envs)
+    sur = Surrogate(max(E, E_train), seed=args.seed)
+    train_s, train_loss, transitions = train_on_plain_step(
+        sur, E_train, args.train_steps, args.lr, args.seed + 1000, log=sys.stderr)
+
+    sc5 = scenes.surrogate_scene(E, args.seed)
+    sc1 = dataclasses_replace(sc5, substeps=1)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed + 5)
+    act = torch.rand((T, E, 16, 3), device="cuda", generator=gen) * 2 - 1
+    runs = {}
+    for name, sc, use_sur in (("plain_s5", sc5, False), ("surrogate", sc5, True),
+                              ("plain_s1", sc1, False)):
+        w = World(sc)
+        nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
+        pos = torch.empty((T, E, 16, 2), device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T)]
+        for t in range(T):
+            ev[2 * t].record()
+            if use_sur:
+                sur.step(w, act[t], n_fallback=nfb[t:t + 1])
+            else:
+                w.step(act[t])
+            ev[2 * t + 1].record()
+            pos[t] = w.state()[:, :16, :2]
+        torch.cuda.synchronize()
+        ms = [ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(T)]
+        runs[name] = dict(pos=pos, ms=statistics.median(ms[3:]), nfb=nfb.cpu().numpy())
+        w.close()
+    ref = runs["plain_s5"]["pos"]
+
+    def err(name):
+        d = (runs[name]["pos"] - ref).norm(dim=-1)  # [T, E, 16]
+        return float(d.mean().item()), float(d[-1].mean().item())
+
+    e_sur, e_sur_end = err("surrogate")
+    e_s1, e_s1_end = err("plain_s1")
+    val = {k: E / (v["ms"] / 1e3) for k, v in runs.items()}
+    sur.close()
+    print(json.dumps({
+        "form": "surrogate",
+        "metric": "env-steps/s, learned surrogate step (with plain-step fallback)",
+        "value": val["surrogate"], "unit": UNIT, "ms_per_step": runs["surrogate"]["ms"],
+        "plain_s5_value": val["plain_s5"], "plain_s1_value": val["plain_s1"],
+        "surrogate_mean_pos_err_50": e_sur, "surrogate_pos_err_at_50": e_sur_end,
+        "plain_s1_mean_pos_err_50": e_s1, "plain_s1_pos_err_at_50": e_s1_end,
+        "fallback_envs_per_step": float(runs["surrogate"]["nfb"].mean()),
+        "train": {"seconds": train_s, "transitions": transitions, "envs": E_train,
+                  "steps": args.train_steps, "final_loss": train_loss, "lr": args.lr},
+        "dtype": "bf16 network / f32 fallback", "data": "synthetic",
+        "config": {"workload": "%d envs x (16 agent spheres + 4 walls), 5 substeps, %d steps"
+                               % (E, T)}}), flush=True)
+    return 0
+
+
+def dataclasses_replace(scene, **kw):
+    import dataclasses
+
+    return dataclasses.replace(scene, **kw)
+
+
 def run_lidar(args):
     """LIDAR on the paper-scale scene: 20 agents x 32 rays per env."""
     import torch
@@ -540,12 +619,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--form", choices=["plain", "adjoint", "lidar", "ragged"], default="plain",
+    ap.add_argument("--form", choices=["plain", "adjoint", "lidar", "ragged", "surrogate"],
+                    default="plain",
                     help="plain: the fused world step (the headline); adjoint: "
                          "differentiable rollout forward + backward")
     ap.add_argument("--envs", type=int, default=30000)
     ap.add_argument("--substeps", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--train-envs", type=int, default=65536, help="surrogate form")
+    ap.add_argument("--train-steps", type=int, default=1500, help="surrogate form")
+    ap.add_argument("--lr", type=float, default=2e-3, help="surrogate form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--stats", action="store_true",
@@ -561,6 +644,8 @@ def main(argv=None):
         return run_lidar(args)
     if args.form == "ragged":
         return run_ragged(args)
+    if args.form == "surrogate":
+        return run_surrogate(args)
     return run_native(args)
 
 

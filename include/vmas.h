@@ -40,7 +40,7 @@ extern "C" {
 
 #define VMAS_ABI_VERSION 1
 
-/* Entity shapes (section 3: "Entities have a shape (sphere, box, or line)"). */
+/* Entity shapes (section 3, Core: every entity is a sphere, a box or a line). */
 enum { VMAS_SPHERE = 0, VMAS_BOX = 1, VMAS_LINE = 2 };
 
 /* Entity flags (section 3: movable, rotatable, collidable; actuated = takes an
@@ -301,6 +301,83 @@ typedef struct {
   int32_t *status;
 } vmas_step_noalloc_args;
 int vmas_step_noalloc(const vmas_step_noalloc_args *args, void *stream);
+
+/* ---- Learned surrogate of the world step --------------------------------
+ * Not part of the paper's method: a network trained on the transitions that
+ * the step of section 3 (Eqs. 1-3, all substeps) produces, standing in for
+ * it on the walled sphere world: per env 16 movable, actuated, non-rotating
+ * agent spheres (action rows 0..15) then 4 fixed lines (the walls at x = +-1
+ * and y = +-1).  Worlds of any other layout give VMAS_EINVAL.
+ *
+ * Network, per agent: node features (10 vx, 10 vy, f/m, 10 r, 1/m and the
+ * 4 wall gaps min(gap, 0.3)/0.3); edge features for up to 6 nearest other
+ * agents within 0.3 (relative position / 0.3, 10 relative velocity, 10 r_j,
+ * surface gap / 0.3, 1); edge MLP 16 -> 64 -> 64 (GELU) summed over the
+ * edges; node MLP 80 -> 128 -> 128 -> 8 (GELU); prediction
+ * x' = x + 0.01 out[0:2], v' = v + 0.1 out[2:4].  Weights and activations
+ * bfloat16, accumulation FP32 (tensor-core mma), biases FP32.
+ *
+ * Parameters: vmas_sur_param_count() FP32 values in the order We1 [64][16],
+ * be1 [64], We2 [64][64], be2 [64], W1 [128][80], b1 [128], W2 [128][128],
+ * b2 [128], W3 [8][128], b3 [8] (weights [out][in]); the library keeps an
+ * FP32 master copy and rounds the weights to bfloat16 for the GEMMs.
+ * Training minimises mean((out[:, 0:4] - target)^2), the target being the
+ * plain step's deltas (x, y, vx, vy) over (0.01, 0.01, 0.1, 0.1), with Adam
+ * (beta 0.9 / 0.999, eps 1e-8).
+ *
+ * A surrogate is created for at most max_envs envs (its activations are
+ * sized for them) and serves any world of that layout and size; d_actions
+ * is the world's [n_envs][n_actuated][3] device action array.  Calls on one
+ * surrogate must be serialised; all work is enqueued on `stream` except in
+ * set_params / get_params, which synchronise the device. */
+typedef struct vmas_surrogate vmas_surrogate;
+int vmas_sur_param_count(void);
+int vmas_sur_create(int32_t max_envs, vmas_surrogate **out);
+int vmas_sur_destroy(vmas_surrogate *sur);
+/* h_params / out: host [vmas_sur_param_count()]; set_params resets Adam. */
+int vmas_sur_set_params(vmas_surrogate *sur, const float *h_params);
+int vmas_sur_get_params(vmas_surrogate *sur, float *h_params);
+/* The network on the world's current state: d_out [n_envs * 16][8] (device,
+ * may be NULL), row e * 16 + i for agent i of env e. */
+int vmas_sur_forward(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
+                     float *d_out, void *stream);
+/* Loss against d_target [n_envs * 16][4] into d_loss [1] (may be NULL) and
+ * its gradient, kept for vmas_sur_adam and copied to d_grad
+ * [vmas_sur_param_count()] (may be NULL).  The world is not changed. */
+int vmas_sur_loss_grad(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
+                       const float *d_target, float *d_loss, float *d_grad, void *stream);
+/* One Adam update with the gradient of the last loss_grad / train_step. */
+int vmas_sur_adam(vmas_surrogate *sur, float lr, void *stream);
+/* One training step on a fresh transition: the network on the current state,
+ * then the plain step (vmas_step) advances the world and its result is the
+ * target; loss (d_loss, may be NULL), gradient and one Adam update. */
+int vmas_sur_train_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions, float lr,
+                        float *d_loss, void *stream);
+/* One world step by the surrogate.  Envs whose predicted agents overlap one
+ * another, or a wall, by more than `limit` world units (or whose prediction is
+ * not finite) are stepped by the plain step instead; the other envs take the
+ * prediction (x, y, vx, vy of the agents; angles and walls unchanged).
+ * d_n_fallback (device int32, may be NULL) receives the number of envs that
+ * fell back. */
+int vmas_sur_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions, float limit,
+                  int32_t *d_n_fallback, void *stream);
+/* Diagnostic: the features of the world's current state as bfloat16 bits,
+ * d_node [n_envs * 16][16], d_edge [6][n_envs * 16][16] (neighbour slot
+ * major), d_mask [6][n_envs * 16] (1 for a present neighbour); any may be
+ * NULL. */
+int vmas_sur_debug_features(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
+                            uint16_t *d_node, uint16_t *d_edge, float *d_mask, void *stream);
+/* Diagnostic: the surrogate's GEMM, C [M][N] = A B with A(m, k) =
+ * trans_a ? a[k lda + m] : a[m lda + k] and B(k, n) = trans_b ? b[n ldb + k]
+ * : b[k ldb + n], bfloat16 operands (bits), FP32 accumulation; plus bias [N]
+ * (FP32, may be NULL) into d_out_f32 [M][N] (may be NULL) and GELU (gelu != 0)
+ * of it rounded into d_out_bf16 [M][N] (may be NULL).  splits > 1 sums K in
+ * that many chunks (then no bias, GELU or bfloat16 output); it allocates a
+ * temporary buffer and waits for `stream`. */
+int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N, int32_t K,
+                         const uint16_t *d_a, int32_t lda, const uint16_t *d_b, int32_t ldb,
+                         const float *d_bias, int32_t gelu, float *d_out_f32,
+                         uint16_t *d_out_bf16, int32_t splits, void *stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *vmas_last_error(void);

@@ -15,7 +15,7 @@ library in-tree.
 """
 from . import scenes  # noqa: F401
 
-__all__ = ["World", "scenes", "build"]
+__all__ = ["World", "Surrogate", "scenes", "build"]
 
 
 def __getattr__(name):
@@ -23,6 +23,8 @@ def __getattr__(name):
 
     if name == "World":
         return importlib.import_module(__name__ + ".world").World
-    if name in ("build", "world", "_lib"):
+    if name == "Surrogate":
+        return importlib.import_module(__name__ + ".surrogate").Surrogate
+    if name in ("build", "world", "_lib", "surrogate", "diff", "ragged", "sharding"):
         return importlib.import_module(__name__ + "." + name)
     raise AttributeError(name)

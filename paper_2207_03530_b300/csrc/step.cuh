@@ -54,6 +54,9 @@ struct StepParams {
   const int *perm;                     // [E] sorted position -> caller env index
   const int *aoff;                     // [E + 1] action-row offsets, caller env order
   int env_begin, env_end;
+  // listed stepping (plain kernels): only envs env_list[0 .. *env_count) are
+  // stepped; nullptr = all E envs
+  const int *env_list, *env_count;
   // caller-owned buffers of the allocation-free entry point (RAW kernels):
   float *aos_state;                    // [E][N][6] x y vx vy th om, read and written
   const uint8_t *r_shape, *r_flags;    // [E * N]

@@ -98,6 +98,11 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   extern __shared__ __align__(16) unsigned char smem[];
   const int NL = NC > 0 ? NC : p.N;  // layout capacity per env
   const int P = NC > 0 ? NC * (NC - 1) / 2 : p.P;
+  if constexpr (!RAGGED && !RAW) {
+    // listed stepping: a block past the end of the list has nothing to do
+    // (uniform over the block, before its first barrier)
+    if (p.env_list && (int)(blockIdx.x * kFusedWarps * EPW) >= *p.env_count) return;
+  }
   uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
   for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,8 +134,15 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     arow0 = valid ? (size_t)p.aoff[oe] : 0;
     A_e = valid ? p.aoff[oe + 1] - p.aoff[oe] : 0;
   } else {
-    e = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
-    valid = e < p.E;
+    const int slot = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+    if (!RAW && p.env_list) {
+      valid = slot < *p.env_count;
+      e = valid ? p.env_list[slot] : 0;
+      valid = valid && e >= 0 && e < p.E;
+    } else {
+      e = slot;
+      valid = e < p.E;
+    }
     N = NL;
     eb = (size_t)e * NL;
     arow0 = (size_t)e * p.A;

@@ -1,0 +1,420 @@
+// Learned surrogate of the world step (sm_103a): bfloat16 tensor-core GEMMs
+// with FP32 accumulation (warp-level mma.sync m16n8k16), and the feature,
+// aggregation, loss, GELU-backward and Adam kernels around them.
+//
+// Network (per agent of a walled 16-agent sphere world; all sizes fixed):
+//   node features n (16), edge features e (16) for up to K = 6 nearest other
+//   agents within 0.3;  edge MLP he = bf(gelu(We1 bf(e) + be1)) (16 -> 64),
+//   m = gelu(We2 he + be2) (64 -> 64), M = bf(sum of m over the edges);
+//   node MLP z = [bf(n), M] (80), h1 = bf(gelu(W1 z + b1)) (-> 128),
+//   h2 = bf(gelu(W2 h1 + b2)) (-> 128), out = W3 h2 + b3 (-> 8, 4 used);
+//   next state x' = x + 0.01 out[0:2], v' = v + 0.1 out[2:4].
+// bf() rounds to bfloat16; gelu(z) = z (1 + erf(z / sqrt 2)) / 2.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vmas {
+namespace sur {
+
+constexpr int kK = 6;            // neighbour slots per agent
+constexpr int kAgents = 16;      // agents per env
+constexpr int kEnts = 20;        // 16 agents + 4 walls
+constexpr float kRadius = 0.3f;
+constexpr float kXScale = 0.01f, kVScale = 0.1f;
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float gelu(float z) {
+  return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) +
+         z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// --------------------------------------------------------------- GEMM
+// C[m, n] = sum_k A(m, k) B(k, n);  A(m, k) = TA ? A[k lda + m] : A[m lda + k],
+// B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Grid (ceil(M/64), ceil(N/64),
+// splits); split z sums k in [z kchunk, (z+1) kchunk) and writes its partial
+// to out_f32 + z M ldc_f.
+struct GemmArgs {
+  int M, N, K;
+  const bf16 *A;
+  int lda;
+  const bf16 *B;
+  int ldb;
+  const float *bias;  // [N] or null (added by split 0 only)
+  int act;            // 0: none, 1: gelu (applied to the bf16 output)
+  float *out_f32;     // optional
+  int ldc_f;
+  bf16 *out_bf;       // optional
+  int ldc_b;
+  int kchunk;
+};
+
+constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
+  __shared__ __align__(16) bf16 As[kBM][kBK + kPad];  // [m][k]
+  __shared__ __align__(16) bf16 Bs[kBN][kBK + kPad];  // [n][k]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gi = lane >> 2, ti = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+    // stage the tiles (bounds-checked, zero filled)
+    for (int q = tid; q < kBM * kBK; q += 128) {
+      const int mm = TA ? (q % kBM) : (q / kBK), kk = TA ? (q / kBM) : (q % kBK);
+      const int m = m0 + mm, k = k0 + kk;
+      bf16 v = zero;
+      if (m < g.M && k < kend) v = TA ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+      As[mm][kk] = v;
+    }
+    for (int q = tid; q < kBN * kBK; q += 128) {
+      const int nn = TB ? (q / kBK) : (q % kBN), kk = TB ? (q % kBK) : (q / kBN);
+      const int n = n0 + nn, k = k0 + kk;
+      bf16 v = zero;
+      if (n < g.N && k < kend) v = TB ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
+      Bs[nn][kk] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kBK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int r = wm + a * 16 + gi, c = ks + 2 * ti;
+        af[a][0] = pack2(As[r][c], As[r][c + 1]);
+        af[a][1] = pack2(As[r + 8][c], As[r + 8][c + 1]);
+        af[a][2] = pack2(As[r][c + 8], As[r][c + 9]);
+        af[a][3] = pack2(As[r + 8][c + 8], As[r + 8][c + 9]);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int n = wn + b * 8 + gi, c = ks + 2 * ti;
+        bfr[b][0] = pack2(Bs[n][c], Bs[n][c + 1]);
+        bfr[b][1] = pack2(Bs[n][c + 8], Bs[n][c + 9]);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+              "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+              : "+f"(acc[a][b][0]), "+f"(acc[a][b][1]), "+f"(acc[a][b][2]), "+f"(acc[a][b][3])
+              : "r"(af[a][0]), "r"(af[a][1]), "r"(af[a][2]), "r"(af[a][3]), "r"(bfr[b][0]),
+                "r"(bfr[b][1]));
+    }
+    __syncthreads();
+  }
+  // epilogue
+  float *of = g.out_f32 ? g.out_f32 + (size_t)blockIdx.z * g.M * g.ldc_f : nullptr;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = m0 + wm + a * 16 + gi + (c >= 2 ? 8 : 0);
+        const int n = n0 + wn + b * 8 + 2 * ti + (c & 1);
+        if (m >= g.M || n >= g.N) continue;
+        float v = acc[a][b][c];
+        if (g.bias && blockIdx.z == 0) v += g.bias[n];
+        if (of) of[(size_t)m * g.ldc_f + n] = v;
+        if (g.out_bf) g.out_bf[(size_t)m * g.ldc_b + n] = __float2bfloat16_rn(g.act ? gelu(v) : v);
+      }
+}
+
+// Sum of `splits` partial [M][N] blocks (split-K reduction).
+__global__ void sum_partials_kernel(float *out, const float *part, int splits, size_t MN) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= MN) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * MN + t];
+  out[t] = s;
+}
+
+// Partial column sums of a [M][N] FP32 matrix (bias gradients): block c
+// sums rows [c chunk, (c+1) chunk) of column threadIdx.x in row order into
+// part[c][n]; sum_partials_kernel finishes.
+__global__ void col_sum_kernel(float *part, const float *x, int M, int N, int chunk) {
+  const int n = threadIdx.x;
+  if (n >= N) return;
+  const size_t r0 = (size_t)blockIdx.x * chunk;
+  const size_t r1 = min((size_t)M, r0 + chunk);
+  float s = 0.f;
+  for (size_t m = r0; m < r1; ++m) s += x[m * N + n];
+  part[(size_t)blockIdx.x * N + n] = s;
+}
+
+// ------------------------------------------------------------ features
+// One thread per agent row r = e * 16 + i, reading a world's state planes
+// (entity e * N + j; agents are entities 0..15, the walls the last 4),
+// per-entity parameters {1/m, 1/I, radius, -} and actions [E][A][3] (agent i
+// takes row i).  Writes node [R][16], edge [K][R][16] (bfloat16; slot-major:
+// row k R + r is agent r's k-th neighbour) and mask [K][R].
+struct FeatureArgs {
+  int E, N, A;
+  const float *px, *py, *vx, *vy;
+  const float4 *param;
+  const float *actions;
+  bf16 *node, *edge;
+  float *mask;
+};
+
+__global__ void features_kernel(const FeatureArgs f) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int R = f.E * kAgents;
+  if (r >= R) return;
+  const int e = r / kAgents, i = r % kAgents;
+  const size_t b = (size_t)e * f.N;
+  const float x = f.px[b + i], y = f.py[b + i], vx = f.vx[b + i], vy = f.vy[b + i];
+  const float4 pi = f.param[b + i];
+  const float ri = pi.z, im = pi.x;
+  const float *a = f.actions + ((size_t)e * f.A + i) * 3;
+  float nf[16];
+  nf[0] = 10.f * vx;
+  nf[1] = 10.f * vy;
+  nf[2] = a[0] * im;
+  nf[3] = a[1] * im;
+  nf[4] = 10.f * ri;
+  nf[5] = im;
+  const float gaps[4] = {1.f - x - ri, 1.f + x - ri, 1.f - y - ri, 1.f + y - ri};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) nf[6 + q] = fminf(gaps[q], kRadius) / kRadius;
+#pragma unroll
+  for (int q = 10; q < 16; ++q) nf[q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) f.node[(size_t)r * 16 + q] = __float2bfloat16_rn(nf[q]);
+  // the K nearest other agents within the radius (ties: lower index first)
+  float bd[kK];
+  int bj[kK];
+  int n = 0;
+  for (int j = 0; j < kAgents; ++j) {
+    if (j == i) continue;
+    const float dx = f.px[b + j] - x, dy = f.py[b + j] - y;
+    const float d = sqrtf(dx * dx + dy * dy);
+    if (!(d < kRadius)) continue;
+    int p = n;  // insertion position among the n kept (n <= K)
+    while (p > 0 && bd[p - 1] > d) --p;
+    if (p >= kK) continue;
+    const int last = n < kK ? n : kK - 1;
+    for (int q = last; q > p; --q) {
+      bd[q] = bd[q - 1];
+      bj[q] = bj[q - 1];
+    }
+    bd[p] = d;
+    bj[p] = j;
+    if (n < kK) ++n;
+  }
+  for (int k = 0; k < kK; ++k) {
+    const size_t row = (size_t)k * R + r;
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = 0.f;
+    float mk = 0.f;
+    if (k < n) {
+      const int j = bj[k];
+      const float rj = f.param[b + j].z;
+      v[0] = (f.px[b + j] - x) / kRadius;
+      v[1] = (f.py[b + j] - y) / kRadius;
+      v[2] = 10.f * (f.vx[b + j] - vx);
+      v[3] = 10.f * (f.vy[b + j] - vy);
+      v[4] = 10.f * rj;
+      v[5] = (bd[k] - ri - rj) / kRadius;
+      v[6] = 1.f;
+      mk = 1.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) f.edge[row * 16 + q] = __float2bfloat16_rn(v[q]);
+    f.mask[row] = mk;
+  }
+}
+
+// zin[r] = [node[r], bf(sum_k mask[k][r] gelu(ze2[k][r]))] (80 wide).
+__global__ void aggregate_kernel(int R, const float *ze2, const float *mask, const bf16 *node,
+                                 bf16 *zin) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)R * 80) return;
+  const size_t r = t / 80;
+  const int c = (int)(t % 80);
+  if (c < 16) {
+    zin[t] = node[r * 16 + c];
+    return;
+  }
+  float s = 0.f;
+  for (int k = 0; k < kK; ++k) {
+    const size_t rk = (size_t)k * R + r;
+    if (mask[rk] != 0.f) s += mask[rk] * gelu(ze2[rk * 64 + (c - 16)]);
+  }
+  zin[t] = __float2bfloat16_rn(s);
+}
+
+// d_z = d_h * gelu'(z); FP32 copy (bias gradients) and bfloat16 copy (GEMMs).
+__global__ void gelu_back_kernel(size_t n, const float *d_h, const float *z, float *d_z32,
+                                 bf16 *d_zbf) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float v = d_h[t] * gelu_grad(z[t]);
+  d_z32[t] = v;
+  d_zbf[t] = __float2bfloat16_rn(v);
+}
+
+// Edge-message gradient: d_ze2[k][r][c] = d_zin[r][16 + c] mask[k][r] gelu'(ze2[k][r][c]).
+__global__ void edge_back_kernel(int R, const float *d_zin, const float *mask, const float *ze2,
+                                 float *d_z32, bf16 *d_zbf) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)R * kK * 64) return;
+  const size_t rk = t / 64;
+  const int c = (int)(t % 64);
+  const size_t r = rk % (size_t)R;
+  const float v = mask[rk] != 0.f ? d_zin[r * 80 + 16 + c] * mask[rk] * gelu_grad(ze2[t]) : 0.f;
+  d_z32[t] = v;
+  d_zbf[t] = __float2bfloat16_rn(v);
+}
+
+// Loss mean((out[:, :4] - y)^2): d_out = 2 (out - y) / (4 R) (columns 4..7
+// zero); per-block partial sums of the squared error into part[blockIdx.x].
+__global__ void loss_kernel(int R, const float *out, const float *y, float *d_out32, bf16 *d_outbf,
+                            float *part) {
+  __shared__ float red[256];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float se = 0.f;
+  if (t < R * 8) {
+    const int r = t / 8, c = t % 8;
+    float d = 0.f;
+    if (c < 4) {
+      const float diff = out[(size_t)r * 8 + c] - y[(size_t)r * 4 + c];
+      se = diff * diff;
+      d = 2.f * diff / (4.f * (float)R);
+    }
+    d_out32[t] = d;
+    d_outbf[t] = __float2bfloat16_rn(d);
+  }
+  red[threadIdx.x] = se;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void finish_loss_kernel(const float *part, int n, int R, float *loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int q = 0; q < n; ++q) s += part[q];
+    *loss = s / (4.f * (float)R);
+  }
+}
+
+// Adam on FP32 master parameters; weights (not biases) mirrored to bfloat16.
+__global__ void adam_kernel(size_t n, float *p, const float *g, float *m, float *v, bf16 *pbf,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float gt = g[t];
+  const float mt = b1 * m[t] + (1.f - b1) * gt;
+  const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+  m[t] = mt;
+  v[t] = vt;
+  const float upd = lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+  const float np = p[t] - upd;
+  p[t] = np;
+  if (pbf) pbf[t] = __float2bfloat16_rn(np);
+}
+
+// Applies the prediction to a world's state planes for every env whose
+// predicted agents overlap each other, or the walls at +-1, by at most
+// `limit`; every other env is left unchanged and appended to `list` (the
+// plain step then advances it).  One thread per env.
+struct PredictArgs {
+  int E, N;
+  float *px, *py, *vx, *vy;
+  const float4 *param;
+  const float *out;  // [E * 16][8]
+  float limit;
+  int *list, *list_len;
+};
+
+__global__ void predict_kernel(const PredictArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  const size_t b = (size_t)e * a.N;
+  float px[kAgents], py[kAgents], rr[kAgents];
+  float worst = -1e30f;  // deepest predicted overlap
+#pragma unroll
+  for (int i = 0; i < kAgents; ++i) {
+    const float *o = a.out + ((size_t)e * kAgents + i) * 8;
+    px[i] = a.px[b + i] + kXScale * o[0];
+    py[i] = a.py[b + i] + kXScale * o[1];
+    rr[i] = a.param[b + i].z;
+    worst = fmaxf(worst, fmaxf(fmaxf(px[i] + rr[i] - 1.f, rr[i] - 1.f - px[i]),
+                               fmaxf(py[i] + rr[i] - 1.f, rr[i] - 1.f - py[i])));
+  }
+  for (int i = 0; i < kAgents; ++i)
+    for (int j = i + 1; j < kAgents; ++j) {
+      const float dx = px[i] - px[j], dy = py[i] - py[j];
+      worst = fmaxf(worst, rr[i] + rr[j] - sqrtf(dx * dx + dy * dy));
+    }
+  if (!(worst <= a.limit)) {  // also catches a non-finite prediction
+    a.list[atomicAdd(a.list_len, 1)] = e;
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < kAgents; ++i) {
+    const float *o = a.out + ((size_t)e * kAgents + i) * 8;
+    a.px[b + i] = px[i];
+    a.py[b + i] = py[i];
+    a.vx[b + i] += kVScale * o[2];
+    a.vy[b + i] += kVScale * o[3];
+  }
+}
+
+// Agents' (x, y, vx, vy) rows [E * 16][4] of a world's planes.
+__global__ void save_agents_kernel(int E, int N, const float *px, const float *py,
+                                   const float *vx, const float *vy, float *save) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= E * kAgents) return;
+  const size_t g = (size_t)(r / kAgents) * N + r % kAgents;
+  save[(size_t)r * 4 + 0] = px[g];
+  save[(size_t)r * 4 + 1] = py[g];
+  save[(size_t)r * 4 + 2] = vx[g];
+  save[(size_t)r * 4 + 3] = vy[g];
+}
+
+// Training targets: the step's deltas over (0.01, 0.01, 0.1, 0.1).
+__global__ void targets_kernel(int E, int N, const float *px, const float *py, const float *vx,
+                               const float *vy, const float *save, float *target) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= E * kAgents) return;
+  const size_t g = (size_t)(r / kAgents) * N + r % kAgents;
+  const float *s0 = save + (size_t)r * 4;
+  float *t = target + (size_t)r * 4;
+  t[0] = (px[g] - s0[0]) / kXScale;
+  t[1] = (py[g] - s0[1]) / kXScale;
+  t[2] = (vx[g] - s0[2]) / kVScale;
+  t[3] = (vy[g] - s0[3]) / kVScale;
+}
+
+}  // namespace sur
+}  // namespace vmas

@@ -482,6 +482,19 @@ def pack_ragged(scene: Scene, counts):
     return out
 
 
+def surrogate_scene(n_envs: int = 65536, seed: int = 0, substeps: int = 5) -> Scene:
+    """The walled sphere world of the learned surrogate: ``paper_scene``
+    without its boxes, i.e. per env the 16 agent spheres (entities 0..15,
+    actuated, action rows 0..15) then the 4 walls (entities 16..19)."""
+    sc = paper_scene(n_envs, seed, dense=False, substeps=substeps)
+    keep = np.r_[0:16, 20:24]
+    kw = dataclasses.asdict(sc)
+    for key in ("shape", "flags", "size_a", "size_b", "mass", "inertia", "init_state"):
+        kw[key] = np.ascontiguousarray(getattr(sc, key)[:, keep])
+    kw.update(name="surrogate", n_entities=20, n_actuated=16)
+    return Scene(**kw)
+
+
 def make_goals(scene: Scene, seed: int = 0) -> np.ndarray:
     """Goal positions [n_envs, n_actuated, 2], uniform in [-1, 1]^2, FP32."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x60A1]))
@@ -501,4 +514,5 @@ CONFIGS = {
     "paper": paper_scene,
     "mixed": mixed_scene,
     "diff": diff_scene,
+    "surrogate": surrogate_scene,
 }

@@ -92,6 +92,13 @@ class World:
             raise ValueError("step_host() takes host actions")
         _lib.check(self._L.vmas_step_host(self._handle(), _ptr(a) if a.numel() else None,
                                           _stream_handle(stream)))
+        if a.numel() and a.is_pinned():
+            # the upload is asynchronous: hold the buffer until it has run, so
+            # that the pinned-memory cache cannot hand it out again earlier
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream() if stream is None else stream)
+            self._in_flight = [(e, t) for e, t in getattr(self, "_in_flight", []) if not e.query()]
+            self._in_flight.append((ev, a))
 
     def rollout(self, actions: torch.Tensor, stream=None) -> None:
         """len(actions) consecutive steps; actions: CUDA float32 [T, E, A, 3]."""

@@ -1,0 +1,296 @@
+"""The learned surrogate's CUDA kernels against its FP64 reference.
+
+* GEMM: the bfloat16 tensor-core GEMM (all transpose forms, ragged tiles,
+  split-K, bias + GELU epilogue) against FP64 products of the same bfloat16
+  operands: FP32 accumulation of K terms stays within 1e-5 of sum |a||b|.
+* Features: bfloat16 values within one bfloat16 rounding step (2^-8
+  relative; the CUDA side forms them in FP32, the reference in FP64 before the
+  same rounding), neighbour masks exactly.
+* Network output: the rounding points are the same on both sides; what is
+  left is FP32 summation order and the rare activation that rounds to the
+  neighbouring bfloat16 value, so the output agrees to 5e-3 relative (norm).
+* Gradient: the CUDA backward feeds bfloat16 copies of the upstream
+  gradients to its GEMMs (2^-9 relative each), the reference stays in FP64:
+  every parameter block agrees to 3e-2 relative (Frobenius norm).
+* Fallback: envs that fall back to the plain step are bitwise equal to it;
+  the rest take the prediction.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2207_03530_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf(x):
+    """bfloat16 rounding (nearest even) of float32 values, as float64."""
+    f = np.ascontiguousarray(np.asarray(x, np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _gelu64(z):
+    from scipy.special import erf
+
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+@pytest.mark.parametrize("ta,tb", [(False, True), (False, False), (True, False), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(64, 64, 32), (130, 72, 80), (1, 8, 128), (257, 128, 16),
+                                   (96, 10, 0)])
+def test_gemm_matches_fp64(vmas_lib, ta, tb, M, N, K):
+    from paper_2207_03530_b300.surrogate import gemm_bf16
+
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = _bf(rng.normal(0, 1, (M, K)))
+    B = _bf(rng.normal(0, 1, (K, N)))
+    bias = rng.normal(0, 1, N).astype(np.float32)
+    a_dev = torch.tensor(A.T if ta else A, dtype=torch.bfloat16, device="cuda").contiguous()
+    b_dev = torch.tensor(B.T if tb else B, dtype=torch.bfloat16, device="cuda").contiguous()
+    out, obf = gemm_bf16(a_dev, b_dev, ta, tb, bias=torch.tensor(bias, device="cuda"), gelu=True)
+    ref = A @ B + bias.astype(np.float64)
+    bound = 1e-5 * (np.abs(A) @ np.abs(B) + np.abs(bias)) + 1e-7
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= bound)
+    g = obf.float().cpu().numpy()
+    gr = _gelu64(ref)
+    assert np.all(np.abs(g - gr) <= 2.0 ** -7 * np.abs(gr) + 1e-6)
+
+
+@pytest.mark.parametrize("splits", [2, 7, 64])
+def test_gemm_split_k(vmas_lib, splits):
+    from paper_2207_03530_b300.surrogate import gemm_bf16
+
+    rng = np.random.default_rng(splits)
+    M, N, K = 128, 80, 5000
+    A = _bf(rng.normal(0, 1, (K, M)))  # stored transposed: weight-gradient form
+    B = _bf(rng.normal(0, 1, (K, N)))
+    a_dev = torch.tensor(A, dtype=torch.bfloat16, device="cuda")
+    b_dev = torch.tensor(B, dtype=torch.bfloat16, device="cuda")
+    out, _ = gemm_bf16(a_dev, b_dev, trans_a=True, splits=splits)
+    ref = A.T @ B
+    bound = 1e-5 * (np.abs(A.T) @ np.abs(B)) + 1e-7
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= bound)
+
+
+def _sur_scene(E, seed, crowd=1.0):
+    """The surrogate's world with random agent velocities; crowd < 1 pulls the
+    agents together (more neighbours, the K = 6 cap reached)."""
+    sc = scenes.surrogate_scene(E, seed)
+    st = sc.init_state.copy()
+    rng = np.random.default_rng(seed + 100)
+    st[:, :16, :2] *= crowd
+    st[:, :16, 2:4] = rng.uniform(-0.5, 0.5, (E, 16, 2)).astype(np.float32)
+    return sc.with_state(st)
+
+
+def _weights(seed):
+    """Reference-initialised weights plus non-zero biases, all float32
+    representable (the library holds FP32 masters)."""
+    from oracle import surrogate as S
+
+    rng = np.random.default_rng(seed)
+    w = S.init_weights(seed)
+    for k in S.ORDER:
+        if k.startswith("b"):
+            w[k] = rng.normal(0, 0.1, w[k].shape).astype(np.float32).astype(np.float64)
+    w["W3"] = S.bf(rng.uniform(-0.09, 0.09, w["W3"].shape))
+    return w
+
+
+def _ref_inputs(sc):
+    from oracle import surrogate as S
+
+    st = sc.init_state.astype(np.float64)
+    return st, S
+
+
+@pytest.mark.parametrize("E,crowd", [(40, 1.0), (33, 0.35)])
+def test_features_match_reference(vmas_lib, E, crowd):
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate
+
+    sc = _sur_scene(E, 3, crowd)
+    act = scenes.make_actions(sc, 1, 5)[0]
+    st, S = _ref_inputs(sc)
+    node_r, edge_r, mask_r = S.features(st, act.astype(np.float64), sc.size_a[:, :16], sc.mass[:, :16])
+    w = World(sc)
+    sur = Surrogate(E)
+    node, edge, mask = sur.debug_features(w, torch.from_numpy(act).cuda())
+    node, edge, mask = node.cpu().numpy(), edge.cpu().numpy(), mask.cpu().numpy()
+    R = E * 16
+    edge_r = edge_r.transpose(1, 0, 2)  # [K, R, 16], slot major
+    mask_r = mask_r.T
+    np.testing.assert_array_equal(mask, mask_r)
+    assert mask.sum() > R * 0.3
+    if crowd < 1:
+        assert (mask.sum(0) == 6).mean() > 0.2  # the K cap is exercised
+    for got, ref in ((node, _bf(node_r)), (edge, _bf(edge_r))):
+        assert np.all(np.abs(got - ref) <= 2.0 ** -7 * np.abs(ref) + 1e-6)
+    w.close()
+    sur.close()
+
+
+def _cuda_forward(sc, w64, act):
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate
+
+    w = World(sc)
+    sur = Surrogate(sc.n_envs, params={k: v.astype(np.float32) for k, v in w64.items()})
+    out = sur.forward(w, torch.from_numpy(act).cuda()).cpu().numpy()
+    return w, sur, out
+
+
+@pytest.mark.parametrize("E,crowd", [(48, 1.0), (21, 0.4)])
+def test_forward_matches_reference(vmas_lib, E, crowd):
+    sc = _sur_scene(E, 7, crowd)
+    act = scenes.make_actions(sc, 1, 8)[0]
+    st, S = _ref_inputs(sc)
+    w64 = _weights(11)
+    node, edge, mask = S.features(st, act.astype(np.float64), sc.size_a[:, :16], sc.mass[:, :16])
+    ref = S.forward(w64, node, edge, mask)
+    w, sur, out = _cuda_forward(sc, w64, act)
+    err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert err <= 5e-3, err
+    w.close()
+    sur.close()
+
+
+def test_gradient_matches_reference(vmas_lib):
+    sc = _sur_scene(24, 9, 0.6)
+    act = scenes.make_actions(sc, 1, 2)[0]
+    st, S = _ref_inputs(sc)
+    w64 = _weights(5)
+    node, edge, mask = S.features(st, act.astype(np.float64), sc.size_a[:, :16], sc.mass[:, :16])
+    target = np.random.default_rng(1).normal(0, 1, (24 * 16, 4)).astype(np.float32)
+    loss_r, g_r = S.loss_and_grad(w64, node, edge, mask, target.astype(np.float64))
+    w, sur, _ = _cuda_forward(sc, w64, act)
+    loss, grad = sur.loss_grad(w, torch.from_numpy(act).cuda(), torch.from_numpy(target).cuda())
+    assert float(loss.item()) == pytest.approx(loss_r, rel=2e-3)
+    from paper_2207_03530_b300.surrogate import unflatten
+
+    g = unflatten(grad.cpu().numpy())
+    for k in S.ORDER:
+        ref = g_r[k]
+        e = np.linalg.norm(g[k] - ref) / max(np.linalg.norm(ref), 1e-12)
+        assert e <= 3e-2, (k, e)
+    w.close()
+    sur.close()
+
+
+def test_fallback_envs_equal_plain_step(vmas_lib):
+    """Big output weights make most predictions overlap: those envs must be
+    bitwise the plain step, the others exactly the prediction."""
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate, init_params
+
+    E = 300
+    sc = _sur_scene(E, 4)
+    act = torch.from_numpy(scenes.make_actions(sc, 1, 3)[0]).cuda()
+    p = init_params(2)
+    p["W3"] = p["W3"] * 40.0
+    p["b3"][:] = 0.0
+    plain = World(sc)
+    plain.step(act)
+    ref = plain.state().cpu().numpy()
+    w = World(sc)
+    sur = Surrogate(E, params=p)
+    out = sur.forward(w, act).cpu().numpy().reshape(E, 16, 8)
+    nfb = int(sur.step(w, act).item())
+    got = w.state().cpu().numpy()
+    s0 = sc.init_state
+    pred = s0.copy()
+    pred[:, :16, 0] = s0[:, :16, 0] + np.float32(0.01) * out[..., 0]
+    pred[:, :16, 1] = s0[:, :16, 1] + np.float32(0.01) * out[..., 1]
+    pred[:, :16, 2] = s0[:, :16, 2] + np.float32(0.1) * out[..., 2]
+    pred[:, :16, 3] = s0[:, :16, 3] + np.float32(0.1) * out[..., 3]
+    is_plain = np.all(got == ref, axis=(1, 2))
+    is_pred = np.all(np.abs(got - pred) <= 1e-6 * (1 + np.abs(pred)), axis=(1, 2))
+    assert np.all(is_plain | is_pred)
+    n_plain_only = int((is_plain & ~is_pred).sum())
+    assert n_plain_only == nfb
+    assert 0 < nfb < E
+    w.close()
+    plain.close()
+    sur.close()
+
+
+def test_surrogate_rejects_other_layouts(vmas_lib):
+    from paper_2207_03530_b300 import World, _lib
+    from paper_2207_03530_b300.surrogate import Surrogate
+
+    sc = scenes.paper_scene(8, 0)
+    w = World(sc)
+    sur = Surrogate(8)
+    act = torch.zeros((8, sc.n_actuated, 3), device="cuda")
+    with pytest.raises(_lib.VmasError):
+        sur.step(w, act)
+    w.close()
+    big = World(scenes.surrogate_scene(9, 0))
+    with pytest.raises(_lib.VmasError):
+        sur.forward(big, torch.zeros((9, 16, 3), device="cuda"))
+    big.close()
+    sur.close()
+
+
+def test_training_lowers_loss(vmas_lib):
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate
+
+    E, T = 2048, 150
+    sc = scenes.surrogate_scene(E, 1)
+    w = World(sc)
+    sur = Surrogate(E, seed=1)
+    acts = torch.from_numpy(scenes.make_actions(sc, T, 6)).cuda()
+    losses = []
+    for t in range(T):
+        losses.append(sur.train_step(w, acts[t], 1e-3))
+    ls = torch.cat(losses).cpu().numpy()
+    assert np.all(np.isfinite(ls))
+    assert ls[-20:].mean() < 0.3 * ls[5:25].mean(), (ls[:25].mean(), ls[-20:].mean())
+    w.close()
+    sur.close()
+
+
+def _rollout_positions(world, acts, sur=None):
+    pos = []
+    for t in range(acts.shape[0]):
+        if sur is None:
+            world.step(acts[t])
+        else:
+            sur.step(world, acts[t])
+        pos.append(world.state()[:, :16, :2].clone())
+    return torch.stack(pos)
+
+
+def test_trained_surrogate_50_step_error(vmas_lib):
+    """Trained on the GPU on plain-step transitions, the surrogate (with its
+    fallback) stays within 1e-2 world units mean agent position error of the
+    plain step over 50 steps; the untrained network does not, and the plain
+    step at 1 substep (the cheap method without the network) is worse."""
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate, train_on_plain_step
+
+    E, T = 4096, 50
+    sur = Surrogate(16384, seed=3)
+    untrained = Surrogate(E, seed=3)
+    secs, loss, _ = train_on_plain_step(sur, 16384, 600, 2e-3, 77)
+    assert loss < 1e-3, loss
+    sc = scenes.surrogate_scene(E, 11)
+    acts = torch.from_numpy(scenes.make_actions(sc, T, 12)).cuda()
+    ref = _rollout_positions(World(sc), acts)
+    err = {}
+    for name, s in (("trained", sur), ("untrained", untrained)):
+        err[name] = float((_rollout_positions(World(sc), acts, s) - ref).norm(dim=-1).mean())
+    import dataclasses
+
+    s1 = _rollout_positions(World(dataclasses.replace(sc, substeps=1)), acts)
+    err["plain_s1"] = float((s1 - ref).norm(dim=-1).mean())
+    print("mean position error over %d steps: %s (training %.1f s)" % (T, err, secs))
+    assert err["trained"] <= 1e-2
+    assert err["trained"] < 0.2 * err["untrained"]
+    assert err["trained"] < err["plain_s1"]
+    sur.close()
+    untrained.close()
