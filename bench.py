@@ -21,7 +21,6 @@ method) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -54,10 +53,14 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+# the sources the plain step kernel is compiled from
+STEP_KERNEL_SOURCES = ("contact.cuh", "step.cuh", "step_fused.cuh")
+
+
 def _kernel_digest():
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", "*"))):
-        with open(p, "rb") as f:
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -534,8 +537,10 @@ def run_surrogate(args):
     gen.manual_seed(args.seed + 5)
     act = torch.rand((T, E, 16, 3), device="cuda", generator=gen) * 2 - 1
     runs = {}
-    for name, sc, use_sur in (("plain_s5", sc5, False), ("surrogate", sc5, True),
-                              ("plain_s1", sc1, False)):
+    for name, sc, use_sur in (("plain_s5", sc5, False), ("surrogate", sc5, "fused"),
+                              ("surrogate_layered", sc5, "layered"), ("plain_s1", sc1, False)):
+        if use_sur:
+            sur.set_mode(use_sur)
         w = World(sc)
         nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
         pos = torch.empty((T, E, 16, 2), device="cuda")
@@ -567,6 +572,7 @@ def run_surrogate(args):
         "metric": "env-steps/s, learned surrogate step (with plain-step fallback)",
         "value": val["surrogate"], "unit": UNIT, "ms_per_step": runs["surrogate"]["ms"],
         "plain_s5_value": val["plain_s5"], "plain_s1_value": val["plain_s1"],
+        "layered_surrogate_value": val["surrogate_layered"],
         "surrogate_mean_pos_err_50": e_sur, "surrogate_pos_err_at_50": e_sur_end,
         "plain_s1_mean_pos_err_50": e_s1, "plain_s1_pos_err_at_50": e_s1_end,
         "fallback_envs_per_step": float(runs["surrogate"]["nfb"].mean()),

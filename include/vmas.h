@@ -337,6 +337,13 @@ int vmas_sur_destroy(vmas_surrogate *sur);
 /* h_params / out: host [vmas_sur_param_count()]; set_params resets Adam. */
 int vmas_sur_set_params(vmas_surrogate *sur, const float *h_params);
 int vmas_sur_get_params(vmas_surrogate *sur, float *h_params);
+/* Inference kernels of vmas_sur_forward and vmas_sur_step:
+ * VMAS_SUR_FUSED (the default): one kernel, one warp per env, everything on
+ * chip; VMAS_SUR_LAYERED: one GEMM launch per layer over all envs, with the
+ * activations in device memory (the path training uses).  Both give the
+ * same results. */
+enum { VMAS_SUR_FUSED = 0, VMAS_SUR_LAYERED = 1 };
+int vmas_sur_set_mode(vmas_surrogate *sur, int32_t mode);
 /* The network on the world's current state: d_out [n_envs * 16][8] (device,
  * may be NULL), row e * 16 + i for agent i of env e. */
 int vmas_sur_forward(vmas_surrogate *sur, vmas_world *world, const float *d_actions,

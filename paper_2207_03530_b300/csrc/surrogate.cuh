@@ -27,6 +27,15 @@ constexpr float kXScale = 0.01f, kVScale = 0.1f;
 
 using bf16 = __nv_bfloat16;
 
+// flat parameter layout (this order): We1 [64][16], be1 [64], We2 [64][64],
+// be2 [64], W1 [128][80], b1 [128], W2 [128][128], b2 [128], W3 [8][128], b3 [8]
+enum : int {
+  kOffWe1 = 0, kOffbe1 = kOffWe1 + 64 * 16, kOffWe2 = kOffbe1 + 64, kOffbe2 = kOffWe2 + 64 * 64,
+  kOffW1 = kOffbe2 + 64, kOffb1 = kOffW1 + 128 * 80, kOffW2 = kOffb1 + 128,
+  kOffb2 = kOffW2 + 128 * 128, kOffW3 = kOffb2 + 128, kOffb3 = kOffW3 + 8 * 128,
+  kParams = kOffb3 + 8
+};
+
 __device__ __forceinline__ float gelu(float z) {
   return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
 }
@@ -212,7 +221,7 @@ __global__ void features_kernel(const FeatureArgs f) {
   for (int j = 0; j < kAgents; ++j) {
     if (j == i) continue;
     const float dx = f.px[b + j] - x, dy = f.py[b + j] - y;
-    const float d = sqrtf(dx * dx + dy * dy);
+    const float d = sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
     if (!(d < kRadius)) continue;
     int p = n;  // insertion position among the n kept (n <= K)
     while (p > 0 && bd[p - 1] > d) --p;
@@ -356,37 +365,44 @@ struct PredictArgs {
   int *list, *list_len;
 };
 
+// Overlap of agent (x, y, r) with the walls at x = +-1, y = +-1.
+__device__ __forceinline__ float wall_overlap(float x, float y, float r) {
+  return fmaxf(fmaxf(x + r - 1.f, r - 1.f - x), fmaxf(y + r - 1.f, r - 1.f - y));
+}
+
 __global__ void predict_kernel(const PredictArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.E) return;
   const size_t b = (size_t)e * a.N;
-  float px[kAgents], py[kAgents], rr[kAgents];
+  float px[kAgents], py[kAgents], pvx[kAgents], pvy[kAgents], rr[kAgents];
   float worst = -1e30f;  // deepest predicted overlap
+  bool finite = true;
 #pragma unroll
   for (int i = 0; i < kAgents; ++i) {
     const float *o = a.out + ((size_t)e * kAgents + i) * 8;
-    px[i] = a.px[b + i] + kXScale * o[0];
-    py[i] = a.py[b + i] + kXScale * o[1];
+    px[i] = fmaf(kXScale, o[0], a.px[b + i]);
+    py[i] = fmaf(kXScale, o[1], a.py[b + i]);
+    pvx[i] = fmaf(kVScale, o[2], a.vx[b + i]);
+    pvy[i] = fmaf(kVScale, o[3], a.vy[b + i]);
     rr[i] = a.param[b + i].z;
-    worst = fmaxf(worst, fmaxf(fmaxf(px[i] + rr[i] - 1.f, rr[i] - 1.f - px[i]),
-                               fmaxf(py[i] + rr[i] - 1.f, rr[i] - 1.f - py[i])));
+    finite = finite && isfinite(px[i]) && isfinite(py[i]) && isfinite(pvx[i]) && isfinite(pvy[i]);
+    worst = fmaxf(worst, wall_overlap(px[i], py[i], rr[i]));
   }
   for (int i = 0; i < kAgents; ++i)
     for (int j = i + 1; j < kAgents; ++j) {
       const float dx = px[i] - px[j], dy = py[i] - py[j];
-      worst = fmaxf(worst, rr[i] + rr[j] - sqrtf(dx * dx + dy * dy));
+      worst = fmaxf(worst, rr[i] + rr[j] - sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
     }
-  if (!(worst <= a.limit)) {  // also catches a non-finite prediction
+  if (!finite || !(worst <= a.limit)) {
     a.list[atomicAdd(a.list_len, 1)] = e;
     return;
   }
 #pragma unroll
   for (int i = 0; i < kAgents; ++i) {
-    const float *o = a.out + ((size_t)e * kAgents + i) * 8;
     a.px[b + i] = px[i];
     a.py[b + i] = py[i];
-    a.vx[b + i] += kVScale * o[2];
-    a.vy[b + i] += kVScale * o[3];
+    a.vx[b + i] = pvx[i];
+    a.vy[b + i] = pvy[i];
   }
 }
 

@@ -1331,21 +1331,15 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
 // that predicts a whole world step of the 16-agent walled sphere world, with
 // the plain step as the fallback for envs whose prediction overlaps.
 
-#include "surrogate.cuh"
+#include "surrogate_fused.cuh"
 
 namespace {
 
 using vmas::sur::bf16;
 namespace sur = vmas::sur;
 
-// parameter layout (FP32, this order): We1 [64][16], be1 [64], We2 [64][64],
-// be2 [64], W1 [128][80], b1 [128], W2 [128][128], b2 [128], W3 [8][128], b3 [8]
-enum : int {
-  kOffWe1 = 0, kOffbe1 = kOffWe1 + 64 * 16, kOffWe2 = kOffbe1 + 64, kOffbe2 = kOffWe2 + 64 * 64,
-  kOffW1 = kOffbe2 + 64, kOffb1 = kOffW1 + 128 * 80, kOffW2 = kOffb1 + 128,
-  kOffb2 = kOffW2 + 128 * 128, kOffW3 = kOffb2 + 128, kOffb3 = kOffW3 + 8 * 128,
-  kSurParams = kOffb3 + 8
-};
+using namespace vmas::sur;  // parameter offsets kOff*
+constexpr int kSurParams = vmas::sur::kParams;
 constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
 
 }  // namespace
@@ -1353,6 +1347,8 @@ constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
 struct vmas_surrogate {
   int device = 0;
   int cap = 0;  // envs
+  int mode = VMAS_SUR_FUSED;
+  int n_sm = 0;
   int adam_t = 0;
   float *p32 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   bf16 *pbf = nullptr;
@@ -1584,6 +1580,35 @@ int sur_adam(vmas_surrogate *s, float lr, cudaStream_t st) {
   return VMAS_OK;
 }
 
+// The fused inference kernel over the world's envs: network output into
+// out (may be NULL); apply = true also applies the prediction and lists the
+// fallback envs.
+int sur_fused(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *out, bool apply,
+              float limit, cudaStream_t st) {
+  const int E = w->E;
+  if (E == 0) return VMAS_OK;
+  static bool attr_set[64] = {};
+  const size_t smem = sur::fused_smem_bytes();
+  if (s->device >= 0 && s->device < 64 && !attr_set[s->device]) {
+    VMAS_CUDA(cudaFuncSetAttribute(sur::sur_fused_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[s->device] = true;
+  }
+  sur::FusedArgs a{};
+  const size_t EN = (size_t)E * w->N;
+  a.E = E; a.N = w->N; a.A = w->A;
+  a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
+  a.param = w->param; a.actions = d_actions;
+  a.w = s->pbf; a.p = s->p32;
+  a.out = out; a.apply = apply ? 1 : 0; a.limit = limit;
+  a.list = s->list; a.list_len = s->list_len;
+  const int need = (E + sur::kFusedWarpsPerCta - 1) / sur::kFusedWarpsPerCta;
+  const int grid = std::max(1, std::min(need, s->n_sm));
+  sur::sur_fused_kernel<<<grid, sur::kFusedWarpsPerCta * 32, smem, st>>>(a);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
 __global__ void f32_to_bf16_kernel(const float *x, bf16 *y, int n) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) y[t] = __float2bfloat16_rn(x[t]);
@@ -1602,6 +1627,11 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
     return fail(VMAS_EINVAL, "max_envs must be 0.." + std::to_string(1 << 22));
   vmas_surrogate *s = new vmas_surrogate();
   cudaGetDevice(&s->device);
+  if (cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+      s->n_sm < 1) {
+    cudaGetLastError();
+    s->n_sm = 1;
+  }
   s->cap = max_envs;
   const size_t R = (size_t)max_envs * sur::kAgents, RK = R * sur::kK;
   const bool ok =
@@ -1657,11 +1687,20 @@ int vmas_sur_get_params(vmas_surrogate *s, float *h_params) {
   return VMAS_OK;
 }
 
+int vmas_sur_set_mode(vmas_surrogate *s, int32_t mode) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  if (mode != VMAS_SUR_FUSED && mode != VMAS_SUR_LAYERED) return fail(VMAS_EINVAL, "unknown mode");
+  s->mode = mode;
+  return VMAS_OK;
+}
+
 int vmas_sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_out,
                      void *stream) {
   int rc = sur_check(s, w, d_actions);
   if (rc) return rc;
   cudaStream_t st = as_stream(stream);
+  if (s->mode == VMAS_SUR_FUSED)
+    return sur_fused(s, w, d_actions, d_out ? d_out : s->out, false, 0.f, st);
   if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
   if (d_out && w->E)
     VMAS_CUDA(cudaMemcpyAsync(d_out, s->out, (size_t)w->E * sur::kAgents * 8 * sizeof(float),
@@ -1725,16 +1764,20 @@ int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, floa
     if (d_n_fallback) VMAS_CUDA(cudaMemsetAsync(d_n_fallback, 0, sizeof(int32_t), st));
     return VMAS_OK;
   }
-  if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
   VMAS_CUDA(cudaMemsetAsync(s->list_len, 0, sizeof(int), st));
-  sur::PredictArgs a{};
-  const size_t EN = (size_t)E * w->N;
-  a.E = E; a.N = w->N;
-  a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
-  a.param = w->param; a.out = s->out; a.limit = limit;
-  a.list = s->list; a.list_len = s->list_len;
-  sur::predict_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
-  VMAS_CUDA(cudaGetLastError());
+  if (s->mode == VMAS_SUR_FUSED) {
+    if ((rc = sur_fused(s, w, d_actions, nullptr, true, limit, st))) return rc;
+  } else {
+    if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
+    sur::PredictArgs a{};
+    const size_t EN = (size_t)E * w->N;
+    a.E = E; a.N = w->N;
+    a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
+    a.param = w->param; a.out = s->out; a.limit = limit;
+    a.list = s->list; a.list_len = s->list_len;
+    sur::predict_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
+    VMAS_CUDA(cudaGetLastError());
+  }
   // the plain step for the listed envs (grid sized for all; blocks past the
   // device-side count return at once)
   StepParams p = make_params(w);

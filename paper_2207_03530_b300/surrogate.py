@@ -115,6 +115,12 @@ class Surrogate:
         _lib.check(self._L.vmas_sur_get_params(self._handle(), flat.ctypes.data))
         return unflatten(flat)
 
+    def set_mode(self, mode: str) -> None:
+        """Inference kernels: "fused" (default; one warp per env, all on chip)
+        or "layered" (one GEMM per layer, the training path)."""
+        code = {"fused": 0, "layered": 1}[mode]
+        _lib.check(self._L.vmas_sur_set_mode(self._handle(), code))
+
     # -------------------------------------------------------------- network
     def _world(self, world: World, actions):
         _dev(actions)

@@ -133,29 +133,86 @@ def test_features_match_reference(vmas_lib, E, crowd):
     sur.close()
 
 
-def _cuda_forward(sc, w64, act):
+def _cuda_forward(sc, w64, act, mode="fused"):
     from paper_2207_03530_b300 import World
     from paper_2207_03530_b300.surrogate import Surrogate
 
     w = World(sc)
     sur = Surrogate(sc.n_envs, params={k: v.astype(np.float32) for k, v in w64.items()})
+    sur.set_mode(mode)
     out = sur.forward(w, torch.from_numpy(act).cuda()).cpu().numpy()
     return w, sur, out
 
 
-@pytest.mark.parametrize("E,crowd", [(48, 1.0), (21, 0.4)])
-def test_forward_matches_reference(vmas_lib, E, crowd):
+@pytest.mark.parametrize("mode", ["fused", "layered"])
+@pytest.mark.parametrize("E,crowd", [(48, 1.0), (21, 0.4), (37, 0.25)])
+def test_forward_matches_reference(vmas_lib, E, crowd, mode):
     sc = _sur_scene(E, 7, crowd)
     act = scenes.make_actions(sc, 1, 8)[0]
     st, S = _ref_inputs(sc)
     w64 = _weights(11)
     node, edge, mask = S.features(st, act.astype(np.float64), sc.size_a[:, :16], sc.mass[:, :16])
     ref = S.forward(w64, node, edge, mask)
-    w, sur, out = _cuda_forward(sc, w64, act)
+    w, sur, out = _cuda_forward(sc, w64, act, mode)
     err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
     assert err <= 5e-3, err
     w.close()
     sur.close()
+
+
+def test_fused_forward_full_size_sampled(vmas_lib):
+    """262,144 envs, the fused launch the benchmark times: 24 sampled envs
+    against the reference."""
+    from oracle import surrogate as S
+
+    E = 262144
+    sc = _sur_scene(E, 2)
+    act = scenes.make_actions(sc, 1, 4)[0]
+    w64 = _weights(8)
+    w, sur, out = _cuda_forward(sc, w64, act)
+    pick = np.random.default_rng(5).choice(E, 24, replace=False)
+    sub = sc.subset(pick)
+    node, edge, mask = S.features(sub.init_state.astype(np.float64), act[pick].astype(np.float64),
+                                  sub.size_a[:, :16], sub.mass[:, :16])
+    ref = S.forward(w64, node, edge, mask)
+    got = out.reshape(E, 16, 8)[pick].reshape(-1, 8)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 5e-3
+    w.close()
+    sur.close()
+
+
+def test_fused_equals_layered(vmas_lib):
+    """The fused kernel and the layered GEMM path share every rounding point
+    and summation order.  Their outputs are bitwise equal for all but a rare
+    row (about 1 in 20,000 in crowded scenes) where one hidden activation
+    rounds to the neighbouring bfloat16 value; fallback decisions and states
+    over a few surrogate steps agree accordingly."""
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.surrogate import Surrogate, init_params
+
+    E, T = 1500, 4
+    sc = _sur_scene(E, 6, 0.5)
+    acts = torch.from_numpy(scenes.make_actions(sc, T, 1)).cuda()
+    p = init_params(4)
+    p["W3"] *= 8.0  # some envs fall back, most do not
+    res = {}
+    for mode in ("fused", "layered"):
+        w = World(sc)
+        sur = Surrogate(E, params=p)
+        sur.set_mode(mode)
+        out = sur.forward(w, acts[0])
+        nfb = [int(sur.step(w, acts[t]).item()) for t in range(T)]
+        res[mode] = (out.cpu().numpy(), nfb, w.state().cpu().numpy())
+        w.close()
+        sur.close()
+    (of, nf, sf), (ol, nl, sl) = res["fused"], res["layered"]
+    same_rows = np.all(of == ol, axis=1)
+    assert same_rows.mean() >= 0.999, same_rows.mean()
+    assert np.abs(of - ol).max() <= 1e-2 * np.abs(ol).max()
+    assert 0 < sum(nl) < E * T
+    assert all(abs(a - b) <= max(2, 0.01 * b) for a, b in zip(nf, nl)), (nf, nl)
+    same_envs = np.all(sf == sl, axis=(1, 2))
+    assert same_envs.mean() >= 0.99, same_envs.mean()
 
 
 def test_gradient_matches_reference(vmas_lib):
