@@ -152,6 +152,17 @@ int vmas_step_host(vmas_world *world, const float *h_actions, void *stream);
  * Enqueues T kernels on `stream`. */
 int vmas_rollout(vmas_world *world, const float *d_actions, int32_t n_steps, void *stream);
 
+/* n_steps world steps between HOST buffers: h_actions [T][n_envs][n_actuated]
+ * [3] in, every step's state h_states [T][n_envs][n_entities][6] (as
+ * vmas_state) out.  Uploads, steps and downloads overlap: step t + 1's
+ * actions go up and step t's state comes down on the library's own copy
+ * streams while the steps run in order on `stream`, through two device
+ * buffers each way.  Pinned host memory makes the copies asynchronous.
+ * Returns when every state has arrived (it waits for `stream`), with
+ * VMAS_EDEVICE if a kernel raised the device error word. */
+int vmas_rollout_host(vmas_world *world, const float *h_actions, int32_t n_steps, float *h_states,
+                      void *stream);
+
 /* Read the state into caller memory as [n_envs][n_entities][6]
  * (x y vx vy theta omega).  out_is_device != 0: `out` is device memory and
  * the copy is enqueued on `stream`.  out_is_device == 0: `out` is host

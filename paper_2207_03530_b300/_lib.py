@@ -16,7 +16,7 @@ ABI_VERSION = 1
 # Every symbol include/vmas.h declares.
 SYMBOLS = (
     "vmas_world_create", "vmas_world_destroy", "vmas_world_info", "vmas_step",
-    "vmas_step_host", "vmas_rollout", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
+    "vmas_step_host", "vmas_rollout", "vmas_rollout_host", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
     "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
     "vmas_debug_body_axes", "vmas_step_noalloc", "vmas_diff_rollout", "vmas_diff_backward",
@@ -102,6 +102,7 @@ def load():
         "vmas_step": ([vp, vp, vp], ctypes.c_int),
         "vmas_step_host": ([vp, vp, vp], ctypes.c_int),
         "vmas_rollout": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_rollout_host": ([vp, vp, i32, vp, vp], ctypes.c_int),
         "vmas_state": ([vp, vp, i32, vp], ctypes.c_int),
         "vmas_set_state": ([vp, vp, i32, vp, vp], ctypes.c_int),
         "vmas_debug_pairs": ([vp, vp, vp], ctypes.c_int),

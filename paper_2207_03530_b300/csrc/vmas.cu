@@ -51,6 +51,12 @@ struct vmas_world {
   float *stage = nullptr;
   uint8_t *env_mask = nullptr;
   std::vector<int32_t> pi, pj;
+  // host-streaming rollouts (lazy): double-buffered device actions and
+  // state staging, an upload and a download stream, and their events
+  float *h_act[2] = {nullptr, nullptr};
+  float *h_stage[2] = {nullptr, nullptr};
+  cudaStream_t s_up = nullptr, s_down = nullptr;
+  cudaEvent_t ev_up[2] = {}, ev_used[2] = {}, ev_gathered[2] = {}, ev_down[2] = {};
 };
 
 namespace {
@@ -85,6 +91,15 @@ void free_world(vmas_world *w) {
   cudaFree(w->act);
   cudaFree(w->stage);
   cudaFree(w->env_mask);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(w->h_act[b]);
+    cudaFree(w->h_stage[b]);
+    cudaEvent_t evs[4] = {w->ev_up[b], w->ev_used[b], w->ev_gathered[b], w->ev_down[b]};
+    for (cudaEvent_t e : evs)
+      if (e) cudaEventDestroy(e);
+  }
+  if (w->s_up) cudaStreamDestroy(w->s_up);
+  if (w->s_down) cudaStreamDestroy(w->s_down);
   delete w;
 }
 
@@ -660,6 +675,70 @@ int vmas_rollout(vmas_world *w, const float *d_actions, int32_t n_steps, void *s
     if (rc) return rc;
   }
   return VMAS_OK;
+}
+
+static int ensure_streaming(vmas_world *w) {
+  if (w->s_down) return VMAS_OK;
+  const size_t act = (size_t)w->E * w->A * 3, st = (size_t)w->E * w->N * 6;
+  for (int b = 0; b < 2; ++b) {
+    VMAS_CUDA(cudaMalloc(&w->h_act[b], (act > 0 ? act : 1) * sizeof(float)));
+    VMAS_CUDA(cudaMalloc(&w->h_stage[b], (st > 0 ? st : 1) * sizeof(float)));
+    VMAS_CUDA(cudaEventCreateWithFlags(&w->ev_up[b], cudaEventDisableTiming));
+    VMAS_CUDA(cudaEventCreateWithFlags(&w->ev_used[b], cudaEventDisableTiming));
+    VMAS_CUDA(cudaEventCreateWithFlags(&w->ev_gathered[b], cudaEventDisableTiming));
+    VMAS_CUDA(cudaEventCreateWithFlags(&w->ev_down[b], cudaEventDisableTiming));
+  }
+  VMAS_CUDA(cudaStreamCreateWithFlags(&w->s_up, cudaStreamNonBlocking));
+  VMAS_CUDA(cudaStreamCreateWithFlags(&w->s_down, cudaStreamNonBlocking));
+  return VMAS_OK;
+}
+
+int vmas_rollout_host(vmas_world *w, const float *h_actions, int32_t n_steps, float *h_states,
+                      void *stream) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (n_steps < 0) return fail(VMAS_EINVAL, "n_steps < 0");
+  const size_t per_act = (size_t)w->E * w->A * 3, per_st = (size_t)w->E * w->N * 6;
+  if (n_steps == 0 || per_st == 0) return VMAS_OK;
+  if (per_act > 0 && !h_actions) return fail(VMAS_EINVAL, "h_actions is NULL");
+  if (!h_states) return fail(VMAS_EINVAL, "h_states is NULL");
+  int rc = ensure_streaming(w);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  // the upload and download streams start after the work already on `stream`
+  VMAS_CUDA(cudaEventRecord(w->ev_used[0], st));
+  VMAS_CUDA(cudaStreamWaitEvent(w->s_up, w->ev_used[0], 0));
+  VMAS_CUDA(cudaStreamWaitEvent(w->s_down, w->ev_used[0], 0));
+  VMAS_CUDA(cudaEventRecord(w->ev_used[1], st));
+  VMAS_CUDA(cudaEventRecord(w->ev_down[0], st));
+  VMAS_CUDA(cudaEventRecord(w->ev_down[1], st));
+  for (int t = 0; t < n_steps; ++t) {
+    const int b = t & 1;
+    // upload step t's actions once step t - 2 has consumed buffer b
+    if (per_act > 0) {
+      VMAS_CUDA(cudaStreamWaitEvent(w->s_up, w->ev_used[b], 0));
+      VMAS_CUDA(cudaMemcpyAsync(w->h_act[b], h_actions + per_act * t, per_act * sizeof(float),
+                                cudaMemcpyHostToDevice, w->s_up));
+      VMAS_CUDA(cudaEventRecord(w->ev_up[b], w->s_up));
+      VMAS_CUDA(cudaStreamWaitEvent(st, w->ev_up[b], 0));
+    }
+    StepParams p = make_params(w);
+    p.actions = w->h_act[b];
+    if ((rc = launch_step(p, st))) return rc;
+    VMAS_CUDA(cudaEventRecord(w->ev_used[b], st));
+    // stage the new state once the download of step t - 2 has left buffer b
+    VMAS_CUDA(cudaStreamWaitEvent(st, w->ev_down[b], 0));
+    gather_state_kernel<<<(unsigned)((per_st / 6 + 255) / 256), 256, 0, st>>>(
+        w->h_stage[b], w->planes, per_st / 6);
+    VMAS_CUDA(cudaGetLastError());
+    VMAS_CUDA(cudaEventRecord(w->ev_gathered[b], st));
+    VMAS_CUDA(cudaStreamWaitEvent(w->s_down, w->ev_gathered[b], 0));
+    VMAS_CUDA(cudaMemcpyAsync(h_states + per_st * t, w->h_stage[b], per_st * sizeof(float),
+                              cudaMemcpyDeviceToHost, w->s_down));
+    VMAS_CUDA(cudaEventRecord(w->ev_down[b], w->s_down));
+  }
+  VMAS_CUDA(cudaStreamSynchronize(w->s_down));
+  VMAS_CUDA(cudaStreamSynchronize(w->s_up));
+  return read_err(w, st, nullptr);
 }
 
 int vmas_world_set_rollout_tile(vmas_world *w, int32_t steps_per_launch) {

@@ -107,6 +107,28 @@ class World:
         _lib.check(self._L.vmas_rollout(self._handle(), _ptr(a) if a.numel() else None, T,
                                         _stream_handle(stream)))
 
+    def rollout_host(self, actions, states_out=None, stream=None) -> torch.Tensor:
+        """len(actions) steps between host buffers: actions [T, E, A, 3] (host;
+        pinned keeps the uploads asynchronous), every step's state into
+        states_out [T, E, N, 6] (host, allocated pinned if None).  Uploads,
+        steps and downloads overlap; returns states_out once all have arrived."""
+        if isinstance(actions, np.ndarray):
+            actions = torch.from_numpy(np.ascontiguousarray(actions, np.float32))
+        T = int(actions.shape[0])
+        a = self._actions(actions, T)
+        if a.is_cuda:
+            raise ValueError("rollout_host() takes host actions")
+        shape = (T, self.n_envs, self.n_entities, 6)
+        if states_out is None:
+            states_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+        if (tuple(states_out.shape) != shape or states_out.dtype != torch.float32
+                or states_out.is_cuda or not states_out.is_contiguous()):
+            raise ValueError("states_out must be a contiguous host float32 %s" % (shape,))
+        _lib.check(self._L.vmas_rollout_host(self._handle(), _ptr(a) if a.numel() else None, T,
+                                             _ptr(states_out) if states_out.numel() else None,
+                                             _stream_handle(stream)))
+        return states_out
+
     # ---------------------------------------------------------------- state
     def state(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """State [E, N, 6] (x, y, vx, vy, theta, omega).  Into ``out`` when

@@ -287,3 +287,28 @@ def test_body_axes_accuracy(vmas_lib):
     t64 = th.astype(np.float64)
     err = max(np.abs(cs[:, 0] - np.cos(t64)).max(), np.abs(cs[:, 1] - np.sin(t64)).max())
     assert err <= 1.5e-7, err
+
+
+def test_rollout_host_streams_every_state(vmas_lib):
+    """vmas_rollout_host overlaps uploads, steps and downloads through double
+    buffers: every step's state must equal the device-side step's, bitwise."""
+    sc = scenes.paper_scene(300, 6, dense=True)
+    T = 7
+    act = scenes.make_actions(sc, T, 2)
+    w1, w2 = _world(sc), _world(sc)
+    d_act = torch.from_numpy(act).cuda()
+    ref = []
+    for t in range(T):
+        w1.step(d_act[t])
+        ref.append(w1.state().cpu())
+    got = w2.rollout_host(torch.from_numpy(act).pin_memory())
+    for t in range(T):
+        assert torch.equal(got[t], ref[t]), t
+    # a second call continues from the streamed world's state
+    more = scenes.make_actions(sc, 2, 3)
+    got2 = w2.rollout_host(more)  # pageable actions: synchronous uploads
+    for t in range(2):
+        w1.step(torch.from_numpy(more[t]).cuda())
+        assert torch.equal(got2[t], w1.state().cpu()), t
+    for w in (w1, w2):
+        w.close()
