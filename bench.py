@@ -592,6 +592,121 @@ def dataclasses_replace(scene, **kw):
     return dataclasses.replace(scene, **kw)
 
 
+def run_sweep(args):
+    """Plain step at E in {1k, 4k, 16k, 30k, 131k, 262k} envs of the
+    paper-scale scene (the larger points hold more state than L2): per-step
+    CUDA events with the L2 flushed before each step, as in the headline."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    props = torch.cuda.get_device_properties(dev)
+    l2 = getattr(props, "L2_cache_size", 126 << 20) or (126 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = _peaks()
+    points = []
+    steps = min(args.steps, 50)
+    for E in (1000, 4000, 16000, 30000, 131072, 262144):
+        sc = scenes.paper_scene(E, args.seed, substeps=args.substeps)
+        w = World(sc)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1000 + args.seed)
+        act = torch.rand((3 + steps, E, sc.n_actuated, 3), device=dev, generator=gen) * 2 - 1
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        for t in range(3 + steps):
+            flush.zero_()
+            flush.sum()
+            if t >= 3:
+                ev[2 * (t - 3)].record()
+            w.step(act[t])
+            if t >= 3:
+                ev[2 * (t - 3) + 1].record()
+        torch.cuda.synchronize()
+        w.check()
+        ms = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps))
+        gbs = B_ALG_PER_ENV * E / (ms / 1e3) / 1e9
+        points.append({"envs": E, "state_mb": round(E * 24 * 6 * 4 / 1e6, 1),
+                       "us_per_step": round(ms * 1e3, 2), "env_steps_per_s": E / (ms / 1e3),
+                       "achieved_gbs": gbs, "hbm_frac": gbs / peak})
+        w.close()
+        del act
+    print(json.dumps({"form": "sweep", "metric": "env-steps/s vs env count, plain step",
+                      "unit": UNIT, "peak_gbs": peak, "peak_source": peak_kind,
+                      "l2_mb": l2 / 1e6, "points": points,
+                      "config": {"workload": "paper-scale scene (16 spheres + 4 boxes + 4 walls), "
+                                             "5 substeps, L2 flushed before every step"}}),
+          flush=True)
+    return 0
+
+
+def run_small(args):
+    """Small workload (BASELINE config 1): 32 envs x (4 agents + 2 landmarks),
+    1 substep, 100 steps: latency per step, launched one by one and replayed
+    from a CUDA graph captured around the same 100 launches.  A roofline
+    fraction at 4.6 KB of state is meaningless; it is reported, labelled
+    latency-bound."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+
+    build.build()
+    torch.cuda.set_device(0)
+    sc = scenes.small_scene(32, args.seed)
+    T = 100
+    w = World(sc)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1000 + args.seed)
+    act = torch.rand((T, sc.n_envs, sc.n_actuated, 3), device="cuda", generator=gen) * 2 - 1
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for t in range(T):  # warm-up (lazy loading) off the capture
+            w.step(act[t])
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        for t in range(T):
+            w.step(act[t])
+    b.record()
+    torch.cuda.synchronize()
+    eager_us = a.elapsed_time(b) * 1e3 / (reps * T)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for t in range(T):
+            w.step(act[t])
+    g.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    graph_us = a.elapsed_time(b) * 1e3 / (reps * T)
+    w.check()
+    w.close()
+    peak, peak_kind = _peaks()
+    b_env = 6 * 24 * 2 + 4 * 8  # state read + write, 4 agents x 2 action floats
+    gbs = b_env * 32 / (graph_us / 1e6) / 1e9
+    print(json.dumps({
+        "form": "small", "metric": "us per step (latency), 100-step rollout",
+        "value": graph_us, "unit": "us/step", "higher_is_better": False,
+        "eager_us_per_step": eager_us, "graph_us_per_step": graph_us,
+        "env_steps_per_s_graph": 32 / (graph_us / 1e6),
+        "roofline": {"bound": "latency", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "bytes_per_env_step": b_env,
+                     "note": "4.6 KB of state: launch- and latency-bound"},
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "32 envs x (4 agent spheres + 2 landmarks), 1 substep, 100 steps"}}),
+        flush=True)
+    return 0
+
+
 def run_lidar(args):
     """LIDAR on the paper-scale scene: 20 agents x 32 rays per env."""
     import torch
@@ -627,7 +742,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--form", choices=["plain", "adjoint", "lidar", "ragged", "surrogate"],
+    ap.add_argument("--form", choices=["plain", "adjoint", "lidar", "ragged", "surrogate",
+                                       "sweep", "small"],
                     default="plain",
                     help="plain: the fused world step (the headline); adjoint: "
                          "differentiable rollout forward + backward")
@@ -654,6 +770,10 @@ def main(argv=None):
         return run_ragged(args)
     if args.form == "surrogate":
         return run_surrogate(args)
+    if args.form == "sweep":
+        return run_sweep(args)
+    if args.form == "small":
+        return run_small(args)
     return run_native(args)
 
 
