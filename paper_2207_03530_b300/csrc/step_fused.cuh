@@ -153,14 +153,40 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
   float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
   uint32_t kd[SLOTS];  // kind byte; bits 8.. hold 1 + the entity's action row (0: none)
+  float4 prs[SLOTS];
+  if constexpr (!RAW) {
+    // every slot's loads first, so that they are in flight together (the
+    // processing below synchronises the warp once per slot)
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int a = lg + G * s;
+      const bool ok = valid && a < N;
+      const size_t ga_ = ok ? VIDX(eb + a, p.EN, 1) : 0;
+      kd[s] = ok ? p.kind[ga_] : 0u;
+      x[s] = ok ? p.px[ga_] : 0.f;
+      y[s] = ok ? p.py[ga_] : 0.f;
+      vx[s] = ok ? p.vx[ga_] : 0.f;
+      vy[s] = ok ? p.vy[ga_] : 0.f;
+      th[s] = ok ? p.th[ga_] : 0.f;
+      om[s] = ok ? p.om[ga_] : 0.f;
+      prs[s] = ok ? p.param[ga_] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // the action rows are read once the kind bytes give each entity its
+    // row: pull them towards L2 meanwhile
+    if (valid && A_e > 0 && p.actions) {
+      const char *a0 = reinterpret_cast<const char *>(p.actions + arow0 * 3);
+      for (int off = lg * 128; off < A_e * 12; off += G * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a0 + off));
+    }
+  }
   int act_base = 0;
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int a = lg + G * s;
     const bool ok = valid && a < N;
-    const size_t ga_ = ok ? VIDX(eb + a, p.EN, 1) : 0;
     float4 pr;
     if constexpr (RAW) {
+      const size_t ga_ = ok ? VIDX(eb + a, p.EN, 1) : 0;
       pr = make_float4(0.f, 0.f, 0.f, 0.f);
       kd[s] = 0u;
       x[s] = y[s] = vx[s] = vy[s] = th[s] = om[s] = 0.f;
@@ -184,14 +210,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
         }
       }
     } else {
-      kd[s] = ok ? p.kind[ga_] : 0u;
-      x[s] = ok ? p.px[ga_] : 0.f;
-      y[s] = ok ? p.py[ga_] : 0.f;
-      vx[s] = ok ? p.vx[ga_] : 0.f;
-      vy[s] = ok ? p.vy[ga_] : 0.f;
-      th[s] = ok ? p.th[ga_] : 0.f;
-      om[s] = ok ? p.om[ga_] : 0.f;
-      pr = ok ? p.param[ga_] : make_float4(0.f, 0.f, 0.f, 0.f);
+      pr = prs[s];
     }
     im[s] = pr.x;
     iI[s] = pr.y;
