@@ -170,7 +170,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(n_envs, substeps, seed, budget_s=12.0):
+def cpu_baseline(n_envs, substeps, seed, budget_s=20.0):
     """Oracle (FP64 C, OpenMP over envs) on the host cores, on a bounded
     sample of the workload: the first E_s envs of the same scene for T_s
     steps, sized to about `budget_s` seconds."""
