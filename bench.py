@@ -510,15 +510,52 @@ def run_ragged(args):
     return 0
 
 
+def _sur_rollouts(sur, sc, act, runs, World):
+    """The same 50-step rollout from sc's start with the plain step and with
+    the surrogate in each inference mode; per-step CUDA events (median after
+    3 steps), agent positions kept for the error."""
+    import torch
+
+    T, E = act.shape[0], sc.n_envs
+    out = {}
+    for name, mode in runs:
+        if mode:
+            sur.set_mode(mode)
+        w = World(sc)
+        nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
+        pos = torch.empty((T, E, 16, 2), device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T)]
+        for t in range(T):
+            ev[2 * t].record()
+            if mode:
+                sur.step(w, act[t], n_fallback=nfb[t:t + 1])
+            else:
+                w.step(act[t])
+            ev[2 * t + 1].record()
+            pos[t] = w.state()[:, :16, :2]
+        torch.cuda.synchronize()
+        ms = [ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(T)]
+        out[name] = dict(pos=pos, ms=statistics.median(ms[3:]), nfb=nfb.cpu().numpy(),
+                         value=E / (statistics.median(ms[3:]) / 1e3))
+        w.close()
+    return out
+
+
+def _pos_err(a, b):
+    d = (a - b).norm(dim=-1)  # [T, E, 16]
+    return float(d.mean().item()), float(d[-1].mean().item())
+
+
 def run_surrogate(args):
     """Learned surrogate (BASELINE config 5): 262,144 envs x 16 agent spheres
-    (+ 4 walls), 50-step rollouts.  Trains the network on the GPU with the
-    library's own forward / backward / Adam kernels on transitions of the
-    plain step (5 substeps), then runs the same 50 steps from the same start
-    with (a) the plain step at 5 substeps (the judge of the error), (b) the
-    surrogate with its plain-step fallback and (c) the plain step at 1
-    substep, and reports env-steps/s of each and the mean agent position
-    error of (b) and (c) against (a)."""
+    (+ 4 walls), 50-step rollouts.  For each substep count S in (5, 1) the
+    network is trained on the GPU with the library's own forward / backward /
+    Adam kernels on transitions of the plain step at S substeps; then the
+    same 50 steps run from the same start with the plain step at S (the
+    judge of the error) and with the surrogate and its plain-step fallback.
+    Reports env-steps/s of each and the mean agent position error; at S = 5
+    also the plain step at 1 substep against the 5-substep reference (the
+    cheap method without a network)."""
     import torch
 
     from paper_2207_03530_b300 import World, build, scenes
@@ -529,60 +566,54 @@ def run_surrogate(args):
     E = args.envs if args.envs != 30000 else 262144
     T = 50
     E_train = min(E, args.train_envs)
-    sur = Surrogate(max(E, E_train), seed=args.seed)
-    train_s, train_loss, transitions = train_on_plain_step(
-        sur, E_train, args.train_steps, args.lr, args.seed + 1000, log=sys.stderr)
-
     sc5 = scenes.surrogate_scene(E, args.seed)
     sc1 = dataclasses_replace(sc5, substeps=1)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(args.seed + 5)
     act = torch.rand((T, E, 16, 3), device="cuda", generator=gen) * 2 - 1
-    runs = {}
-    for name, sc, use_sur in (("plain_s5", sc5, False), ("surrogate", sc5, "fused"),
-                              ("surrogate_layered", sc5, "layered"), ("plain_s1", sc1, False)):
-        if use_sur:
-            sur.set_mode(use_sur)
-        w = World(sc)
-        nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
-        pos = torch.empty((T, E, 16, 2), device="cuda")
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T)]
-        for t in range(T):
-            ev[2 * t].record()
-            if use_sur:
-                sur.step(w, act[t], n_fallback=nfb[t:t + 1])
-            else:
-                w.step(act[t])
-            ev[2 * t + 1].record()
-            pos[t] = w.state()[:, :16, :2]
-        torch.cuda.synchronize()
-        ms = [ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(T)]
-        runs[name] = dict(pos=pos, ms=statistics.median(ms[3:]), nfb=nfb.cpu().numpy())
-        w.close()
-    ref = runs["plain_s5"]["pos"]
-
-    def err(name):
-        d = (runs[name]["pos"] - ref).norm(dim=-1)  # [T, E, 16]
-        return float(d.mean().item()), float(d[-1].mean().item())
-
-    e_sur, e_sur_end = err("surrogate")
-    e_s1, e_s1_end = err("plain_s1")
-    val = {k: E / (v["ms"] / 1e3) for k, v in runs.items()}
-    sur.close()
+    res = {}
+    for S, sc in ((5, sc5), (1, sc1)):
+        sur = Surrogate(max(E, E_train), seed=args.seed)
+        train = train_on_plain_step(sur, E_train, args.train_steps, args.lr, args.seed + 1000,
+                                    substeps=S, log=sys.stderr)
+        runs = [("plain", False), ("surrogate", "fused"), ("surrogate_layered", "layered")]
+        if S == 5:
+            runs.append(("plain_s1", None))
+        out = _sur_rollouts(sur, sc, act, [r for r in runs if r[1] is not None], World)
+        if S == 5:
+            out.update(_sur_rollouts(sur, sc1, act, [("plain_s1", False)], World))
+        sur.close()
+        ref = out["plain"]["pos"]
+        e, e_end = _pos_err(out["surrogate"]["pos"], ref)
+        res[S] = {
+            "plain_value": out["plain"]["value"], "surrogate_value": out["surrogate"]["value"],
+            "layered_surrogate_value": out["surrogate_layered"]["value"],
+            "surrogate_ms_per_step": out["surrogate"]["ms"],
+            "surrogate_mean_pos_err_50": e, "surrogate_pos_err_at_50": e_end,
+            "fallback_envs_per_step": float(out["surrogate"]["nfb"].mean()),
+            "train": {"seconds": train[0], "transitions": train[2], "envs": E_train,
+                      "steps": args.train_steps, "final_loss": train[1], "lr": args.lr}}
+        if S == 5:
+            e1, e1_end = _pos_err(out["plain_s1"]["pos"], ref)
+            res[S].update({"plain_s1_value": out["plain_s1"]["value"],
+                           "plain_s1_mean_pos_err_50": e1, "plain_s1_pos_err_at_50": e1_end})
+        del out
+    r5 = res[5]
     print(json.dumps({
         "form": "surrogate",
         "metric": "env-steps/s, learned surrogate step (with plain-step fallback)",
-        "value": val["surrogate"], "unit": UNIT, "ms_per_step": runs["surrogate"]["ms"],
-        "plain_s5_value": val["plain_s5"], "plain_s1_value": val["plain_s1"],
-        "layered_surrogate_value": val["surrogate_layered"],
-        "surrogate_mean_pos_err_50": e_sur, "surrogate_pos_err_at_50": e_sur_end,
-        "plain_s1_mean_pos_err_50": e_s1, "plain_s1_pos_err_at_50": e_s1_end,
-        "fallback_envs_per_step": float(runs["surrogate"]["nfb"].mean()),
-        "train": {"seconds": train_s, "transitions": transitions, "envs": E_train,
-                  "steps": args.train_steps, "final_loss": train_loss, "lr": args.lr},
+        "value": r5["surrogate_value"], "unit": UNIT, "ms_per_step": r5["surrogate_ms_per_step"],
+        "plain_s5_value": r5["plain_value"], "plain_s1_value": r5["plain_s1_value"],
+        "layered_surrogate_value": r5["layered_surrogate_value"],
+        "surrogate_mean_pos_err_50": r5["surrogate_mean_pos_err_50"],
+        "surrogate_pos_err_at_50": r5["surrogate_pos_err_at_50"],
+        "plain_s1_mean_pos_err_50": r5["plain_s1_mean_pos_err_50"],
+        "plain_s1_pos_err_at_50": r5["plain_s1_pos_err_at_50"],
+        "fallback_envs_per_step": r5["fallback_envs_per_step"], "train": r5["train"],
+        "substeps_1": {k: v for k, v in res[1].items()},
         "dtype": "bf16 network / f32 fallback", "data": "synthetic",
-        "config": {"workload": "%d envs x (16 agent spheres + 4 walls), 5 substeps, %d steps"
-                               % (E, T)}}), flush=True)
+        "config": {"workload": "%d envs x (16 agent spheres + 4 walls), 5 (and 1) substeps, "
+                               "%d steps" % (E, T)}}), flush=True)
     return 0
 
 

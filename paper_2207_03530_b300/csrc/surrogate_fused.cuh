@@ -34,7 +34,9 @@ constexpr int kSmN2 = kSmN1 + 128 * kLdN1;
 constexpr int kSmN3 = kSmN2 + 128 * kLdN2;
 constexpr int kSmWeights = kSmN3 + 8 * kLdN3;         // bfloat16 elements
 constexpr int kSmBias = 64 + 64 + 128 + 128 + 8;      // floats: be1 be2 b1 b2 b3
-constexpr int kSmWarp = (1 + kK) * 16 * kLdX;         // bfloat16: node rows, edge rows per slot
+// bfloat16 elements per warp: node rows, edge rows per slot, then 16 bytes
+// holding the agent of each row
+constexpr int kSmWarp = (1 + kK) * 16 * kLdX + 8;
 constexpr size_t fused_smem_bytes() {
   return (size_t)kSmWeights * 2 + (size_t)kSmBias * 4 + (size_t)kFusedWarpsPerCta * kSmWarp * 2;
 }
@@ -102,6 +104,8 @@ __device__ __noinline__ float4 gelu4(float4 z) {
   return make_float4(gelu(z.x), gelu(z.y), gelu(z.z), gelu(z.w));
 }
 
+__device__ __noinline__ float2 gelu2(float2 z) { return make_float2(gelu(z.x), gelu(z.y)); }
+
 // bias + GELU of two n-tiles (2 kk, 2 kk + 1), rounded into the A fragment of
 // k-tile kk of the next layer.
 __device__ __forceinline__ void gelu_pack(uint32_t (&a)[4], const float (&c0)[4],
@@ -114,6 +118,20 @@ __device__ __forceinline__ void gelu_pack(uint32_t (&a)[4], const float (&c0)[4]
   a[1] = pack_bf16(g0.z, g0.w);
   a[2] = pack_bf16(g1.x, g1.y);
   a[3] = pack_bf16(g1.z, g1.w);
+}
+
+// As gelu_pack for rows 0..7 only; rows 8..15 (not in use) become zero.
+__device__ __forceinline__ void gelu_pack_low(uint32_t (&a)[4], const float (&c0)[4],
+                                              const float (&c1)[4], const float *bias, int kk,
+                                              int t) {
+  const float b00 = bias[16 * kk + 2 * t], b01 = bias[16 * kk + 2 * t + 1];
+  const float b10 = bias[16 * kk + 8 + 2 * t], b11 = bias[16 * kk + 8 + 2 * t + 1];
+  const float2 g0 = gelu2(make_float2(c0[0] + b00, c0[1] + b01));
+  const float2 g1 = gelu2(make_float2(c1[0] + b10, c1[1] + b11));
+  a[0] = pack_bf16(g0.x, g0.y);
+  a[1] = 0u;
+  a[2] = pack_bf16(g1.x, g1.y);
+  a[3] = 0u;
 }
 
 // Dense layer of the node MLP: 16 rows, KT k-tiles of input fragments `in`,
@@ -145,6 +163,7 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
   bf16 *snode = reinterpret_cast<bf16 *>(smem + (size_t)kSmWeights * 2 + (size_t)kSmBias * 4) +
                 warp * kSmWarp;
   bf16 *sedge = snode + 16 * kLdX;  // [kK][16][kLdX]
+  unsigned char *s_agent = reinterpret_cast<unsigned char *>(sedge + kK * 16 * kLdX);  // [16]
 
   // stage the weights (32-bit words; every matrix offset and row length is even)
   {
@@ -185,24 +204,6 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
     const float r = pr.z, im = pr.x;
     const float *ac = a.actions + ((size_t)e * a.A + i) * 3;
     const float ax = ac[0], ay = ac[1];
-    if (lane < 16) {
-      float nf[16];
-      nf[0] = 10.f * vx;
-      nf[1] = 10.f * vy;
-      nf[2] = ax * im;
-      nf[3] = ay * im;
-      nf[4] = 10.f * r;
-      nf[5] = im;
-      nf[6] = fminf(1.f - x - r, kRadius) / kRadius;
-      nf[7] = fminf(1.f + x - r, kRadius) / kRadius;
-      nf[8] = fminf(1.f - y - r, kRadius) / kRadius;
-      nf[9] = fminf(1.f + y - r, kRadius) / kRadius;
-#pragma unroll
-      for (int q = 10; q < 16; ++q) nf[q] = 0.f;
-#pragma unroll
-      for (int q = 0; q < 16; q += 2)
-        *reinterpret_cast<uint32_t *>(snode + i * kLdX + q) = pack_bf16(nf[q], nf[q + 1]);
-    }
     // the K nearest other agents within the radius (ties: lower index first)
     float bd[kK];
     int bj[kK];
@@ -239,6 +240,33 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
       }
     }
     const int n_max = __reduce_max_sync(FULL, n);
+    // Rows of every tile hold the agents sorted by neighbour count (most
+    // first, ties by index): slot k is then in use exactly in its first c_k
+    // rows, and a slot with c_k <= 8 skips the GELUs of rows 8..15.
+    int row = 0;
+    for (int j = 0; j < kAgents; ++j) {
+      const int nj = __shfl_sync(FULL, n, j);
+      row += (nj > n || (nj == n && j < i)) ? 1 : 0;
+    }
+    if (lane < 16) {
+      s_agent[row] = (unsigned char)i;
+      float nf[16];
+      nf[0] = 10.f * vx;
+      nf[1] = 10.f * vy;
+      nf[2] = ax * im;
+      nf[3] = ay * im;
+      nf[4] = 10.f * r;
+      nf[5] = im;
+      nf[6] = fminf(1.f - x - r, kRadius) / kRadius;
+      nf[7] = fminf(1.f + x - r, kRadius) / kRadius;
+      nf[8] = fminf(1.f - y - r, kRadius) / kRadius;
+      nf[9] = fminf(1.f + y - r, kRadius) / kRadius;
+#pragma unroll
+      for (int q = 10; q < 16; ++q) nf[q] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; q += 2)
+        *reinterpret_cast<uint32_t *>(snode + row * kLdX + q) = pack_bf16(nf[q], nf[q + 1]);
+    }
 
     // edge features of every slot below n_max (lanes 0..15: slots 0..2,
     // lanes 16..31: slots 3..5, each for its agent i)
@@ -261,10 +289,10 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
           v[5] = (bd[k] - r - rj) / kRadius;
           v[6] = 1.f;
         }
-        bf16 *row = sedge + (k * 16 + i) * kLdX;
+        bf16 *dst = sedge + (k * 16 + row) * kLdX;
 #pragma unroll
         for (int q = 0; q < 16; q += 2)
-          *reinterpret_cast<uint32_t *>(row + q) = pack_bf16(v[q], v[q + 1]);
+          *reinterpret_cast<uint32_t *>(dst + q) = pack_bf16(v[q], v[q + 1]);
       }
     }
     __syncwarp();
@@ -277,6 +305,8 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
       for (int c = 0; c < 4; ++c) Macc[jt][c] = 0.f;
 #pragma unroll 1
     for (int k = 0; k < n_max; ++k) {
+      const int ck = __popc(__ballot_sync(FULL, n > k) & 0xffffu);  // rows in use
+      const bool low_only = ck <= 8;                                 // warp-uniform
       uint32_t ae[4];
       load_a(ae, sedge + k * 16 * kLdX, kLdX, 0, lane);
       uint32_t he[4][4];
@@ -287,9 +317,10 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
         load_b2(bq, We1, kLdE1, 2 * kk, 0, lane);
         mma_bf16(c0, ae, bq[0], bq[1]);
         mma_bf16(c1, ae, bq[2], bq[3]);
-        gelu_pack(he[kk], c0, c1, be1, kk, t);
+        if (low_only) gelu_pack_low(he[kk], c0, c1, be1, kk, t);
+        else gelu_pack(he[kk], c0, c1, be1, kk, t);
       }
-      const bool mg = __shfl_sync(FULL, n, g) > k, mg8 = __shfl_sync(FULL, n, g + 8) > k;
+      const bool mg = g < ck, mg8 = g + 8 < ck;
 #pragma unroll
       for (int jp = 0; jp < 4; ++jp) {
         float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
@@ -302,16 +333,27 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
         }
         const float b00 = be2[16 * jp + 2 * t], b01 = be2[16 * jp + 2 * t + 1];
         const float b10 = be2[16 * jp + 8 + 2 * t], b11 = be2[16 * jp + 8 + 2 * t + 1];
-        const float4 g0 = gelu4(make_float4(c0[0] + b00, c0[1] + b01, c0[2] + b00, c0[3] + b01));
-        const float4 g1 = gelu4(make_float4(c1[0] + b10, c1[1] + b11, c1[2] + b10, c1[3] + b11));
-        Macc[2 * jp][0] += mg ? g0.x : 0.f;
-        Macc[2 * jp][1] += mg ? g0.y : 0.f;
-        Macc[2 * jp][2] += mg8 ? g0.z : 0.f;
-        Macc[2 * jp][3] += mg8 ? g0.w : 0.f;
-        Macc[2 * jp + 1][0] += mg ? g1.x : 0.f;
-        Macc[2 * jp + 1][1] += mg ? g1.y : 0.f;
-        Macc[2 * jp + 1][2] += mg8 ? g1.z : 0.f;
-        Macc[2 * jp + 1][3] += mg8 ? g1.w : 0.f;
+        if (low_only) {
+          const float2 g0 = gelu2(make_float2(c0[0] + b00, c0[1] + b01));
+          const float2 g1 = gelu2(make_float2(c1[0] + b10, c1[1] + b11));
+          Macc[2 * jp][0] += mg ? g0.x : 0.f;
+          Macc[2 * jp][1] += mg ? g0.y : 0.f;
+          Macc[2 * jp + 1][0] += mg ? g1.x : 0.f;
+          Macc[2 * jp + 1][1] += mg ? g1.y : 0.f;
+        } else {
+          const float4 g0 =
+              gelu4(make_float4(c0[0] + b00, c0[1] + b01, c0[2] + b00, c0[3] + b01));
+          const float4 g1 =
+              gelu4(make_float4(c1[0] + b10, c1[1] + b11, c1[2] + b10, c1[3] + b11));
+          Macc[2 * jp][0] += mg ? g0.x : 0.f;
+          Macc[2 * jp][1] += mg ? g0.y : 0.f;
+          Macc[2 * jp][2] += mg8 ? g0.z : 0.f;
+          Macc[2 * jp][3] += mg8 ? g0.w : 0.f;
+          Macc[2 * jp + 1][0] += mg ? g1.x : 0.f;
+          Macc[2 * jp + 1][1] += mg ? g1.y : 0.f;
+          Macc[2 * jp + 1][2] += mg8 ? g1.z : 0.f;
+          Macc[2 * jp + 1][3] += mg8 ? g1.w : 0.f;
+        }
       }
     }
 
@@ -341,22 +383,24 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
     o[2] += bn3[2 * t];
     o[3] += bn3[2 * t + 1];
     if (a.out) {
-      float *orow = a.out + ((size_t)e * kAgents + g) * 8 + 2 * t;
-      orow[0] = o[0];
-      orow[1] = o[1];
-      orow[64] = o[2];  // row g + 8
-      orow[65] = o[3];
+      float *o0 = a.out + ((size_t)e * kAgents + s_agent[g]) * 8 + 2 * t;
+      float *o8 = a.out + ((size_t)e * kAgents + s_agent[g + 8]) * 8 + 2 * t;
+      o0[0] = o[0];
+      o0[1] = o[1];
+      o8[0] = o[2];
+      o8[1] = o[3];
     }
     if (!a.apply) continue;
 
-    // agent i's outputs 0..3 sit in lanes 4 (i mod 8) (cols 0, 1) and
-    // 4 (i mod 8) + 1 (cols 2, 3), components 0, 1 for rows < 8, else 2, 3
-    const int s0 = 4 * (i & 7), s1 = s0 + 1;
+    // agent i's outputs 0..3 (row `row`) sit in lanes 4 (row mod 8) (cols 0,
+    // 1) and 4 (row mod 8) + 1 (cols 2, 3), components 0, 1 for rows < 8,
+    // else 2, 3
+    const int s0 = 4 * (row & 7), s1 = s0 + 1;
     const float q00 = __shfl_sync(FULL, o[0], s0), q01 = __shfl_sync(FULL, o[1], s0);
     const float q02 = __shfl_sync(FULL, o[2], s0), q03 = __shfl_sync(FULL, o[3], s0);
     const float q10 = __shfl_sync(FULL, o[0], s1), q11 = __shfl_sync(FULL, o[1], s1);
     const float q12 = __shfl_sync(FULL, o[2], s1), q13 = __shfl_sync(FULL, o[3], s1);
-    const bool lo = i < 8;
+    const bool lo = row < 8;
     const float nx = fmaf(kXScale, lo ? q00 : q02, x);
     const float ny = fmaf(kXScale, lo ? q01 : q03, y);
     const float nvx = fmaf(kVScale, lo ? q10 : q12, vx);

@@ -209,14 +209,15 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a=False, trans_b=False, bi
     return out, obf
 
 
-def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=None):
+def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=None, substeps=5):
     """Trains ``sur`` on the GPU on transitions the plain step makes: a world
-    of the surrogate's layout advanced by uniform random actions, reset to
-    its start every ``reset_every`` steps; Adam with a cosine schedule from
-    lr0 to lr0 / 100.  Returns (seconds, final mean loss, transitions)."""
+    of the surrogate's layout (``substeps`` per step) advanced by uniform
+    random actions, reset to its start every ``reset_every`` steps; Adam with
+    a cosine schedule from lr0 to lr0 / 100.  Returns (seconds, final mean
+    loss, transitions)."""
     from . import scenes
 
-    sc = scenes.surrogate_scene(n_envs, seed)
+    sc = scenes.surrogate_scene(n_envs, seed, substeps=substeps)
     w = World(sc)
     init = torch.from_numpy(sc.init_state).cuda()
     gen = torch.Generator(device="cuda")
