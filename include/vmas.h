@@ -364,11 +364,17 @@ int vmas_sur_forward(vmas_surrogate *sur, vmas_world *world, const float *d_acti
  * [vmas_sur_param_count()] (may be NULL).  The world is not changed. */
 int vmas_sur_loss_grad(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
                        const float *d_target, float *d_loss, float *d_grad, void *stream);
-/* One Adam update with the gradient of the last loss_grad / train_step. */
-int vmas_sur_adam(vmas_surrogate *sur, float lr, void *stream);
-/* One training step on a fresh transition: the network on the current state,
- * then the plain step (vmas_step) advances the world and its result is the
- * target; loss (d_loss, may be NULL), gradient and one Adam update. */
+/* One Adam update with the gradient d_grad [vmas_sur_param_count()] (device;
+ * NULL = the gradient of the last loss_grad / train_grad / train_step), e.g.
+ * one averaged over data-parallel ranks. */
+int vmas_sur_adam(vmas_surrogate *sur, float lr, const float *d_grad, void *stream);
+/* The gradient half of a training step on a fresh transition: the network on
+ * the current state, then the plain step (vmas_step) advances the world and
+ * its result is the target; loss into d_loss [1] and the gradient, kept for
+ * vmas_sur_adam and copied to d_grad (both device, may be NULL). */
+int vmas_sur_train_grad(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
+                        float *d_loss, float *d_grad, void *stream);
+/* vmas_sur_train_grad then one Adam update. */
 int vmas_sur_train_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions, float lr,
                         float *d_loss, void *stream);
 /* One world step by the surrogate.  Envs whose predicted agents overlap one

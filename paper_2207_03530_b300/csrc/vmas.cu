@@ -1802,21 +1802,28 @@ int vmas_sur_loss_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
   return VMAS_OK;
 }
 
-int vmas_sur_adam(vmas_surrogate *s, float lr, void *stream) {
+int vmas_sur_adam(vmas_surrogate *s, float lr, const float *d_grad, void *stream) {
   if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
   if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
-  return sur_adam(s, lr, as_stream(stream));
+  cudaStream_t st = as_stream(stream);
+  if (d_grad && d_grad != s->grad)
+    VMAS_CUDA(cudaMemcpyAsync(s->grad, d_grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st));
+  return sur_adam(s, lr, st);
 }
 
-int vmas_sur_train_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float lr,
-                        float *d_loss, void *stream) {
-  int rc = sur_check(s, w, d_actions);
+// Forward on the world's current state, the plain step (the world advances)
+// as the target, loss and gradient into s->grad.
+static int sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
+                          float *d_loss, cudaStream_t st) {
+  int rc = ensure_training(s);
   if (rc) return rc;
-  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
-  if ((rc = ensure_training(s))) return rc;
-  cudaStream_t st = as_stream(stream);
   const int E = w->E, R = E * sur::kAgents;
-  if (E == 0) return VMAS_OK;
+  if (E == 0) {
+    VMAS_CUDA(cudaMemsetAsync(s->grad, 0, kSurParams * sizeof(float), st));
+    if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
+    return VMAS_OK;
+  }
   const size_t EN = (size_t)E * w->N;
   float *px = w->planes, *py = px + EN, *vx = px + 2 * EN, *vy = px + 3 * EN;
   if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
@@ -1828,7 +1835,29 @@ int vmas_sur_train_step(vmas_surrogate *s, vmas_world *w, const float *d_actions
   sur::targets_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save,
                                                            s->target);
   VMAS_CUDA(cudaGetLastError());
-  if ((rc = sur_backward(s, E, s->target, d_loss, st))) return rc;
+  return sur_backward(s, E, s->target, d_loss, st);
+}
+
+int vmas_sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_loss,
+                        float *d_grad, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
+  if (d_grad)
+    VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st));
+  return VMAS_OK;
+}
+
+int vmas_sur_train_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float lr,
+                        float *d_loss, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
+  if (w->E == 0) return VMAS_OK;
   return sur_adam(s, lr, st);
 }
 

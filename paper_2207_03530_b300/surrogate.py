@@ -148,8 +148,29 @@ class Surrogate:
                                               _p(loss), _p(grad), _stream_handle(stream)))
         return loss, grad
 
-    def adam(self, lr: float, stream=None) -> None:
-        _lib.check(self._L.vmas_sur_adam(self._handle(), float(lr), _stream_handle(stream)))
+    def adam(self, lr: float, grad=None, stream=None) -> None:
+        """One Adam update with ``grad`` [param_count()] (CUDA float32), or
+        with the last computed gradient when None."""
+        if grad is not None:
+            _dev(grad)
+            if grad.numel() != param_count():
+                raise ValueError("grad must have %d elements" % param_count())
+        _lib.check(self._L.vmas_sur_adam(self._handle(), float(lr), _p(grad),
+                                         _stream_handle(stream)))
+
+    def train_grad(self, world: World, actions, loss=None, grad=None, stream=None):
+        """The gradient half of a training step on the transition the plain
+        step makes from the world's current state (the world advances).
+        Returns (loss [1], grad [param_count()])."""
+        w = self._world(world, actions)
+        dev = actions.device
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        if grad is None:
+            grad = torch.zeros(param_count(), dtype=torch.float32, device=dev)
+        _lib.check(self._L.vmas_sur_train_grad(self._handle(), w, _p(actions), _p(loss),
+                                               _p(grad), _stream_handle(stream)))
+        return loss, grad
 
     def train_step(self, world: World, actions, lr: float, loss=None, stream=None):
         """One training step on the transition the plain step makes from the
@@ -209,32 +230,67 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a=False, trans_b=False, bi
     return out, obf
 
 
-def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=None, substeps=5):
+def allreduce_mean(tensors, group=None):
+    """Average CUDA tensors over the ranks of a torch.distributed group in
+    place: directly with NCCL, through host memory with gloo."""
+    import torch.distributed as dist
+
+    ws = dist.get_world_size(group)
+    for t in tensors:
+        if dist.get_backend(group) == "nccl":
+            dist.all_reduce(t, group=group)
+            t.div_(ws)
+        else:
+            h = t.cpu()
+            dist.all_reduce(h, group=group)
+            t.copy_(h.div_(ws))
+
+
+def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=None, substeps=5,
+                        group=None, envs=None):
     """Trains ``sur`` on the GPU on transitions the plain step makes: a world
     of the surrogate's layout (``substeps`` per step) advanced by uniform
     random actions, reset to its start every ``reset_every`` steps; Adam with
     a cosine schedule from lr0 to lr0 / 100.  Returns (seconds, final mean
-    loss, transitions)."""
+    loss, transitions).
+
+    Data parallel: with a torch.distributed ``group`` every rank steps its
+    own share ``envs`` (an index array into the n_envs of the scene, e.g.
+    ``sharding.env_range``) and the gradient and loss are averaged over the
+    ranks (equal shares) before each Adam update, so every rank applies the
+    same update."""
     from . import scenes
 
     sc = scenes.surrogate_scene(n_envs, seed, substeps=substeps)
+    if envs is not None:
+        sc = sc.subset(envs)
     w = World(sc)
     init = torch.from_numpy(sc.init_state).cuda()
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed + 17)
     losses = torch.zeros(n_steps, device="cuda")
+    grad = torch.zeros(param_count(), device="cuda") if group is not None else None
+    pick = torch.from_numpy(np.asarray(envs, np.int64)).cuda() if envs is not None else None
     torch.cuda.synchronize()
     t0 = time.time()
     for t in range(n_steps):
         if t % reset_every == 0:
             w.set_state(init)
+        # the same action stream on every rank: each takes its envs' rows
         act = torch.rand((n_envs, 16, 3), device="cuda", generator=gen) * 2 - 1
+        if pick is not None:
+            act = act.index_select(0, pick).contiguous()
         lr = lr0 * (0.01 + 0.99 * 0.5 * (1 + math.cos(math.pi * t / n_steps)))
-        sur.train_step(w, act, lr, loss=losses[t:t + 1])
+        if group is None:
+            sur.train_step(w, act, lr, loss=losses[t:t + 1])
+        else:
+            sur.train_grad(w, act, loss=losses[t:t + 1], grad=grad)
+            allreduce_mean([grad, losses[t:t + 1]], group)
+            sur.adam(lr, grad)
         if log and (t % 200 == 0 or t == n_steps - 1):
             print("train step %d loss %.3e" % (t, losses[t].item()), file=log, flush=True)
     torch.cuda.synchronize()
     secs = time.time() - t0
     w.close()
     tail = max(1, n_steps // 20)
-    return secs, float(losses[-tail:].mean().item()), n_envs * n_steps
+    return secs, float(losses[-tail:].mean().item()), sc.n_envs * n_steps

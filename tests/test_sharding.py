@@ -69,3 +69,30 @@ def test_gloo_two_ranks_shard_and_gather(tmp_path, orc):
     whole = orc.step(sc, sc.init_state, act)
     assert np.array_equal(gathered, whole)
     assert np.load(tmp_path / "tmax.npy")[0] == 2.0
+
+
+def _mean_worker(rank, ws, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2207_03530_b300.surrogate import allreduce_mean
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    g = torch.arange(6, dtype=torch.float32) * (rank + 1)
+    loss = torch.tensor([float(rank)])
+    allreduce_mean([g, loss[0:1]])
+    if rank == 0:
+        np.save(os.path.join(out_dir, "mean.npy"), np.concatenate([g.numpy(), loss.numpy()]))
+    dist.destroy_process_group()
+
+
+def test_gloo_gradient_average(tmp_path):
+    """The surrogate's data-parallel update averages gradients over ranks
+    (host-side reduction with gloo): two ranks, world size 2."""
+    ws, port = 2, _free_port()
+    mp.start_processes(_mean_worker, args=(ws, port, str(tmp_path)), nprocs=ws,
+                       start_method="spawn")
+    got = np.load(tmp_path / "mean.npy")
+    np.testing.assert_allclose(got[:6], np.arange(6) * 1.5)
+    assert got[6] == 0.5
