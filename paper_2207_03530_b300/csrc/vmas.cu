@@ -1,6 +1,10 @@
 // Host side of the VMAS C ABI (include/vmas.h): world creation, device
 // layout, launches and error handling.  The physics lives in step_fused.cuh,
-// step.cuh and contact.cuh.
+// step.cuh and contact.cuh; the differentiable rollout in diff.cuh, LIDAR in
+// lidar.cuh, the learned surrogate in surrogate.cuh (layered GEMM path,
+// training) and surrogate_fused.cuh (fused inference).  Sections below: the
+// world, the allocation-free step, the differentiable rollout and LIDAR, the
+// packed ragged worlds, the surrogate.
 //
 // Device layout of a world (all library-owned, allocated once at create):
 //   state   6 FP32 planes px, py, vx, vy, th, om, each [E * N], env-major
@@ -12,7 +16,8 @@
 //   pairs   uint16 [P] canonical pair list i | j << 8;
 //   err     int32 device error word;
 //   act     FP32 [E * A * 3] staging for host actions;
-//   stage   FP32 [E * N * 6] staging for host state transfers (lazy).
+//   stage   FP32 [E * N * 6] staging for host state transfers (lazy);
+//   h_act / h_stage  two of each, for host-streaming rollouts (lazy).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1428,6 +1433,7 @@ struct vmas_surrogate {
   int cap = 0;  // envs
   int mode = VMAS_SUR_FUSED;
   int n_sm = 0;
+  bool fused_ready = false;  // shared-memory opt-in of the fused kernel done
   int adam_t = 0;
   float *p32 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   bf16 *pbf = nullptr;
@@ -1666,12 +1672,11 @@ int sur_fused(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *o
               float limit, cudaStream_t st) {
   const int E = w->E;
   if (E == 0) return VMAS_OK;
-  static bool attr_set[64] = {};
   const size_t smem = sur::fused_smem_bytes();
-  if (s->device >= 0 && s->device < 64 && !attr_set[s->device]) {
+  if (!s->fused_ready) {  // > 48 KB of dynamic shared memory needs an opt-in
     VMAS_CUDA(cudaFuncSetAttribute(sur::sur_fused_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set[s->device] = true;
+    s->fused_ready = true;
   }
   sur::FusedArgs a{};
   const size_t EN = (size_t)E * w->N;
@@ -1740,7 +1745,6 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
 
 int vmas_sur_destroy(vmas_surrogate *s) {
   if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
-  cudaSetDevice(s->device);
   free_sur(s);
   return VMAS_OK;
 }
