@@ -111,6 +111,36 @@ def test_null_arguments(L):
     assert L.vmas_state(None, None, 0, None) == _lib.VMAS_EINVAL
     assert L.vmas_world_destroy(None) == _lib.VMAS_OK
     assert "NULL" in L.vmas_last_error().decode()
+    assert L.vmas_rollout_host(None, None, 1, None, None) == _lib.VMAS_EINVAL
+
+
+def test_surrogate_null_and_bad_arguments(L):
+    """The surrogate entry points reject bad arguments before any CUDA call."""
+    E = _lib.VMAS_EINVAL
+    h = ctypes.c_void_p()
+    assert L.vmas_sur_param_count() == 33160
+    assert L.vmas_sur_create(5, None) == E
+    assert L.vmas_sur_create(-1, ctypes.byref(h)) == E
+    assert L.vmas_sur_create(1 << 23, ctypes.byref(h)) == E
+    assert L.vmas_sur_destroy(None) == E
+    assert L.vmas_sur_set_params(None, None) == E
+    assert L.vmas_sur_get_params(None, None) == E
+    assert L.vmas_sur_set_mode(None, 0) == E
+    assert L.vmas_sur_forward(None, None, None, None, None) == E
+    assert L.vmas_sur_loss_grad(None, None, None, None, None, None, None) == E
+    assert L.vmas_sur_adam(None, 1e-3, None, None) == E
+    assert L.vmas_sur_train_grad(None, None, None, None, None, None) == E
+    assert L.vmas_sur_train_step(None, None, None, 1e-3, None, None) == E
+    assert L.vmas_sur_step(None, None, None, 0.01, None, None) == E
+    assert L.vmas_sur_debug_features(None, None, None, None, None, None, None) == E
+    assert "NULL" in L.vmas_last_error().decode()
+    # GEMM diagnostic: sizes and combinations are checked first
+    assert L.vmas_debug_gemm_bf16(0, 0, -1, 8, 8, None, 8, None, 8, None, 0, None, None, 1,
+                                  None) == E
+    assert L.vmas_debug_gemm_bf16(0, 0, 8, 8, 8, None, 8, None, 8, None, 1, None, None, 2,
+                                  None) == E
+    assert L.vmas_debug_gemm_bf16(0, 0, 8, 8, 8, None, 4, None, 8, None, 0, None, None, 1,
+                                  None) == E
 
 
 def test_binding_refuses_to_run_without_library(monkeypatch):
