@@ -1251,20 +1251,49 @@ int vmas_ragged_rollout(vmas_ragged *r, const float *d_actions, int32_t n_steps,
     if (r->graph) cudaGraphDestroy(r->graph);
     r->gexec = nullptr;
     r->graph = nullptr;
-    cudaStream_t cap;
-    VMAS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    // The size classes touch disjoint envs, so each class's chain of tiles
+    // is its own branch of the graph (forked from and joined back into the
+    // capture stream): a class with few, slow envs no longer holds the GPU
+    // while the others wait.
+    constexpr int C = vmas_ragged::kClasses;
+    cudaStream_t cap = nullptr, cs[C] = {};
+    cudaEvent_t fork = nullptr, join[C] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int c = 0; c < C && e == cudaSuccess; ++c) {
+      e = cudaStreamCreateWithFlags(&cs[c], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     int rc = VMAS_OK;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      for (int t = 0; t < n_steps && rc == VMAS_OK; t += r->tile)
-        rc = ragged_launch_tile(r, d_actions + (size_t)t * r->total_act * 3,
-                                std::min(r->tile, n_steps - t), cap);
+      e = cudaEventRecord(fork, cap);
+      for (int c = 0; c < C && e == cudaSuccess; ++c) {
+        const int n = r->cls_begin[c + 1] - r->cls_begin[c];
+        e = cudaStreamWaitEvent(cs[c], fork, 0);
+        for (int t = 0; n > 0 && t < n_steps && rc == VMAS_OK && e == cudaSuccess; t += r->tile) {
+          StepParams p = ragged_params(r, c);
+          p.actions = d_actions + (size_t)t * r->total_act * 3;
+          p.tile = std::min(r->tile, n_steps - t);
+          rc = launch_ragged_class(p, r->lanes[c], r->slots[c], n, cs[c]);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(join[c], cs[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[c], 0);
+      }
       cudaError_t e2 = cudaStreamEndCapture(cap, &r->graph);
       if (e == cudaSuccess) e = e2;
     }
     if (e == cudaSuccess && rc == VMAS_OK) e = cudaGraphInstantiate(&r->gexec, r->graph, 0);
-    cudaStreamDestroy(cap);
-    if (rc) return rc;
+    for (int c = 0; c < C; ++c) {
+      if (join[c]) cudaEventDestroy(join[c]);
+      if (cs[c]) cudaStreamDestroy(cs[c]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
+    if (rc) {
+      cudaGetLastError();
+      return rc;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "rollout graph capture");
     r->graph_actions = d_actions;
     r->graph_T = n_steps;
