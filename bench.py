@@ -65,25 +65,45 @@ def _kernel_digest():
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+def _recorded_profile():
+    """(DRAM bytes per launch, headline ncu figures) of the step kernel from
+    the committed ncu summary, if it was taken on the current kernel sources;
+    (None, None) otherwise."""
+    import re
+
     path = os.path.join(ROOT, "profiles", "world_step_paper30k.md")
     try:
         text = open(path).read()
     except OSError:
-        return None
+        return None, None
     fields = {}
     for line in text.splitlines():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
     if fields.get("kernel sources sha256 prefix") != _kernel_digest():
-        return None
+        return None, None
     try:
-        return float(fields["dram bytes per launch (read+write)"])
+        traffic = float(fields["dram bytes per launch (read+write)"])
     except (KeyError, ValueError):
-        return None
+        return None, None
+
+    def pct(key, pattern):
+        m = re.search(pattern, fields.get(key, ""))
+        return float(m.group(1)) if m else None
+
+    figures = {
+        "dram_throughput_pct": pct("gpu__dram_throughput", r"([\d.]+) %"),
+        "issue_active_pct": pct("smsp__issue_active", r"([\d.]+) %"),
+        "fma_pipe_pct": pct("pipes (of active)", r"FMA ([\d.]+) %"),
+        "warps_per_sm": pct("sm__warps_active", r"([\d.]+) warps"),
+        "binds": "latency: neither HBM nor the FP32 pipes are saturated",
+    }
+    return traffic, figures
+
+
+def _recorded_traffic():
+    return _recorded_profile()[0]
 
 
 class ClockSampler:
@@ -359,7 +379,7 @@ def run_native(args):
     peak, peak_kind = _peaks()
     avg_ms = statistics.mean(kern_ms)
     achieved = B_ALG_PER_ENV * E / (avg_ms / 1e3) / 1e9
-    traffic = _recorded_traffic()
+    traffic, ncu_figures = _recorded_profile()
     clocks = sampler.summary()
 
     if rank == 0:
@@ -371,7 +391,8 @@ def run_native(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
-                         "bytes_per_env_step": B_ALG_PER_ENV, "kernel": "world_step_kernel"},
+                         "bytes_per_env_step": B_ALG_PER_ENV, "kernel": "world_step_kernel",
+                         "ncu": ncu_figures},
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
