@@ -17,9 +17,10 @@
 // The contact mask is piecewise constant (no term from the jump at g = 0);
 // forces on immovable entities are dropped, so their lF is 0.
 //
-// Layout: one warp per environment, entity i in lane i (N <= 32); the pair
-// sums of lane i run over j = 0 .. N-1 in order, the same order as a serial
-// loop over canonical pairs.  Checkpoints every K steps hold (x, y, vx, vy)
+// Layout: groups of G lanes (G = 4, 8, 16 or 32, the smallest power of two
+// >= N), one environment per group and 32 / G per warp, entity i in lane i
+// of its group (N <= 32); the pair sums of entity i run over j = 0 .. N-1 in
+// order, the same order as a serial loop over canonical pairs.  Checkpoints every K steps hold (x, y, vx, vy)
 // of every entity; the backward pass re-runs each K-step segment forward from
 // its checkpoint into shared memory (positions at every substep start) and
 // sweeps it backward, segments last to first.
@@ -79,10 +80,12 @@ struct DiffLane {
   int row;
 };
 
-__device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, int lane) {
+// Entity `ent` of env e (its group's lanes in gmask; valid = the group has an env).
+__device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, bool valid, int ent,
+                                              unsigned gmask, int lane) {
   DiffLane L{};
-  L.ok = lane < p.N;
-  const size_t t = (size_t)e * p.N + lane;
+  L.ok = valid && ent < p.N;
+  const size_t t = L.ok ? (size_t)e * p.N + ent : 0;
   L.kd = L.ok ? p.kind[t] : 0u;
   const float4 pr = L.ok ? p.param[t] : make_float4(0.f, 0.f, 0.f, 0.f);
   L.im = pr.x;
@@ -90,13 +93,13 @@ __device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, int la
   L.r = pr.z;
   L.mov = (L.kd & kMovable) != 0u;
   L.act = (L.kd & kActuated) != 0u;
-  const unsigned bal = __ballot_sync(0xffffffffu, L.ok && L.act);
+  const unsigned bal = __ballot_sync(0xffffffffu, L.ok && L.act) & gmask;
   L.row = __popc(bal & ((1u << lane) - 1u));
   if (L.row >= p.A) L.act = false;
   return L;
 }
 
-// One forward substep for lane i; s_pos holds every entity's (x, y).
+// One forward substep of entity `lane` of its env; s_pos holds every entity's (x, y).
 __device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane &L, int lane,
                                              const float2 *s_pos, const uint8_t *s_kind,
                                              const float *s_r, float fax, float fay, float &x,
@@ -121,25 +124,31 @@ __device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane
   }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const DiffParams p) {
+  constexpr int EPW = 32 / G;
   __shared__ float2 s_pos_all[kDiffWarps][32];
   __shared__ uint8_t s_kind_all[kDiffWarps][32];
   __shared__ float s_r_all[kDiffWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * kDiffWarps + warp;
-  if (e >= p.E) return;  // whole warp leaves together
-  float2 *s_pos = s_pos_all[warp];
-  uint8_t *s_kind = s_kind_all[warp];
-  float *s_r = s_r_all[warp];
-  const DiffLane L = diff_lane(p, e, lane);
-  const size_t t0 = (size_t)e * p.N + lane;
+  const int grp = lane / G, ent = lane % G;
+  const int e0 = (blockIdx.x * kDiffWarps + warp) * EPW;
+  if (e0 >= p.E) return;  // whole warp leaves together
+  const int e = e0 + grp;
+  const bool valid = e < p.E;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G);
+  float2 *s_pos = s_pos_all[warp] + grp * G;
+  uint8_t *s_kind = s_kind_all[warp] + grp * G;
+  float *s_r = s_r_all[warp] + grp * G;
+  const DiffLane L = diff_lane(p, e, valid, ent, gmask, lane);
+  const size_t t0 = L.ok ? (size_t)e * p.N + ent : 0;
   float x = L.ok ? p.px[t0] : 0.f, y = L.ok ? p.py[t0] : 0.f;
   float vx = L.ok ? p.vx[t0] : 0.f, vy = L.ok ? p.vy[t0] : 0.f;
-  s_kind[lane] = (uint8_t)L.kd;
-  s_r[lane] = L.r;
+  s_kind[ent] = (uint8_t)L.kd;
+  s_r[ent] = L.r;
   for (int t = 0; t < p.T; ++t) {
     if (t % p.K == 0 && L.ok) {
-      float4 *c = reinterpret_cast<float4 *>(p.ckpt) + ((size_t)(t / p.K) * p.E + e) * p.N + lane;
+      float4 *c = reinterpret_cast<float4 *>(p.ckpt) + ((size_t)(t / p.K) * p.E + e) * p.N + ent;
       *c = make_float4(x, y, vx, vy);
     }
     float fax = 0.f, fay = 0.f;
@@ -149,9 +158,9 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
       fay = a[1];
     }
     for (int s = 0; s < p.S; ++s) {
-      s_pos[lane] = make_float2(x, y);
+      s_pos[ent] = make_float2(x, y);
       __syncwarp();
-      diff_substep(p, L, lane, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
+      diff_substep(p, L, ent, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
       __syncwarp();
     }
   }
@@ -161,8 +170,8 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
     const float dx = x - gl[0], dy = y - gl[1];
     l = dx * dx + dy * dy;
   }
-  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if (lane == 0) p.loss[e] = l;
+  for (int o = G / 2; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (ent == 0 && valid) p.loss[e] = l;
 }
 
 // Dynamic shared memory per warp: positions at the K * S + 1 substep starts
@@ -171,27 +180,34 @@ __host__ __device__ inline size_t diff_traj_bytes(int K, int S) {
   return (size_t)(K * S + 1) * 32 * sizeof(float2);
 }
 
+template <int G>
 __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const DiffParams p) {
+  constexpr int EPW = 32 / G;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ float2 s_lf_all[kDiffWarps][32];
   __shared__ uint8_t s_kind_all[kDiffWarps][32];
   __shared__ float s_r_all[kDiffWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * kDiffWarps + warp;
-  if (e >= p.E) return;
-  float2 *traj = reinterpret_cast<float2 *>(dsm + warp * diff_traj_bytes(p.K, p.S));
-  float2 *s_lf = s_lf_all[warp];
-  uint8_t *s_kind = s_kind_all[warp];
-  float *s_r = s_r_all[warp];
-  const DiffLane L = diff_lane(p, e, lane);
-  s_kind[lane] = (uint8_t)L.kd;
-  s_r[lane] = L.r;
+  const int grp = lane / G, ent = lane % G;
+  const int e0 = (blockIdx.x * kDiffWarps + warp) * EPW;
+  if (e0 >= p.E) return;  // whole warp leaves together
+  const int e = e0 + grp;
+  const bool valid = e < p.E;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G);
+  // traj row q holds the 32 lanes' positions; this group's are at grp * G
+  float2 *traj = reinterpret_cast<float2 *>(dsm + warp * diff_traj_bytes(p.K, p.S)) + grp * G;
+  float2 *s_lf = s_lf_all[warp] + grp * G;
+  uint8_t *s_kind = s_kind_all[warp] + grp * G;
+  float *s_r = s_r_all[warp] + grp * G;
+  const DiffLane L = diff_lane(p, e, valid, ent, gmask, lane);
+  s_kind[ent] = (uint8_t)L.kd;
+  s_r[ent] = L.r;
   float lx = 0.f, ly = 0.f, lvx = 0.f, lvy = 0.f;
   const int nseg = (p.T + p.K - 1) / p.K;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int ta = seg * p.K, tb = min(p.T, ta + p.K);
     // re-run the segment forward, keeping every substep-start position
-    const float4 c = L.ok ? reinterpret_cast<const float4 *>(p.ckpt)[((size_t)seg * p.E + e) * p.N + lane]
+    const float4 c = L.ok ? reinterpret_cast<const float4 *>(p.ckpt)[((size_t)seg * p.E + e) * p.N + ent]
                           : make_float4(0.f, 0.f, 0.f, 0.f);
     float x = c.x, y = c.y, vx = c.z, vy = c.w;
     int q = 0;
@@ -203,9 +219,9 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
         fay = a[1];
       }
       for (int s = 0; s < p.S; ++s, ++q) {
-        traj[q * 32 + lane] = make_float2(x, y);
+        traj[q * 32 + ent] = make_float2(x, y);
         __syncwarp();
-        diff_substep(p, L, lane, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
+        diff_substep(p, L, ent, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
         __syncwarp();
       }
     }
@@ -230,12 +246,12 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
         }
         gax += lfx;
         gay += lfy;
-        s_lf[lane] = make_float2(lfx, lfy);
+        s_lf[ent] = make_float2(lfx, lfy);
         __syncwarp();
         if (L.ok && (L.kd & kCollidable)) {
-          const float2 me = traj[q * 32 + lane];
+          const float2 me = traj[q * 32 + ent];
           for (int j = 0; j < p.N; ++j) {
-            if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+            if (j == ent || !pair_active(L.kd, s_kind[j])) continue;
             const float2 o = traj[q * 32 + j];
             float fx, fy, J[3];
             if (sphere_force(me.x, me.y, o.x, o.y, L.r + s_r[j], p, fx, fy, J)) {

@@ -829,6 +829,10 @@ int vmas_debug_err_words(vmas_world *w, int32_t *out) {
 }
 #endif
 
+// Lanes per env of the differentiable rollout kernels: the smallest power
+// of two that holds the env's entities.
+static int diff_group_lanes(int N) { return N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32; }
+
 static int diff_setup(vmas_world *w, int32_t T, int32_t K, vmas::DiffParams *p) {
   if (!w) return fail(VMAS_EINVAL, "world is NULL");
   if (!w->diff_ok)
@@ -872,8 +876,15 @@ int vmas_diff_rollout(vmas_world *w, const float *d_actions, int32_t n_steps,
   p.goals = d_goals;
   p.ckpt = d_ckpt;
   p.loss = d_loss;
-  const int grid = (w->E + vmas::kDiffWarps - 1) / vmas::kDiffWarps;
-  vmas::diff_forward_kernel<<<grid, vmas::kDiffWarps * 32, 0, as_stream(stream)>>>(p);
+  const int G = diff_group_lanes(w->N), per_cta = vmas::kDiffWarps * (32 / G);
+  const int grid = (w->E + per_cta - 1) / per_cta;
+  cudaStream_t st = as_stream(stream);
+  switch (G) {
+    case 4: vmas::diff_forward_kernel<4><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 8: vmas::diff_forward_kernel<8><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 16: vmas::diff_forward_kernel<16><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    default: vmas::diff_forward_kernel<32><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+  }
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
 }
@@ -893,9 +904,13 @@ int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
   if (smem > 220 * 1024)
     return fail(VMAS_EINVAL, "ckpt_every * substeps too large for on-chip segment replay; "
                              "use a shorter checkpoint interval");
+  const int G = diff_group_lanes(w->N), per_cta = vmas::kDiffWarps * (32 / G);
+  auto kern = G == 4 ? vmas::diff_backward_kernel<4>
+                     : G == 8 ? vmas::diff_backward_kernel<8>
+                              : G == 16 ? vmas::diff_backward_kernel<16>
+                                        : vmas::diff_backward_kernel<32>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(vmas::diff_backward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   }
   cudaStream_t st = as_stream(stream);
@@ -906,8 +921,8 @@ int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
   p.ckpt = const_cast<float *>(d_ckpt);
   p.dloss = d_dloss;
   p.grad = d_grad;
-  const int grid = (w->E + vmas::kDiffWarps - 1) / vmas::kDiffWarps;
-  vmas::diff_backward_kernel<<<grid, vmas::kDiffWarps * 32, smem, st>>>(p);
+  const int grid = (w->E + per_cta - 1) / per_cta;
+  kern<<<grid, vmas::kDiffWarps * 32, smem, st>>>(p);
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
 }
