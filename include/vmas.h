@@ -64,7 +64,9 @@ enum {
 /* Bits of the device error word reported through VMAS_EDEVICE. */
 enum {
   VMAS_DEVERR_NONFINITE = 1, /* a state value became NaN or Inf */
-  VMAS_DEVERR_BAD_ENTITY = 4 /* vmas_step_noalloc met an invalid entity and left it inert */
+  VMAS_DEVERR_BAD_ENTITY = 4, /* vmas_step_noalloc met an invalid entity and left it inert */
+  VMAS_DEVERR_TIMEOUT = 8     /* a step's staging copies did not arrive in time; its CTA
+                                 left its envs unchanged */
 };
 
 /* Largest supported entity count per environment. */

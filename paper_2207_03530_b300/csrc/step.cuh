@@ -57,6 +57,11 @@ struct StepParams {
   // listed stepping (plain kernels): only envs env_list[0 .. *env_count) are
   // stepped; nullptr = all E envs
   const int *env_list, *env_count;
+  // 1: a full CTA of the one-step plain kernel stages its contiguous slice of
+  // state, parameters, kinds and actions into shared memory with bulk (TMA)
+  // copies; the host sets it only when every copy is 16-byte aligned and the
+  // staging fits the CTA's shared memory
+  int bulk;
   // caller-owned buffers of the allocation-free entry point (RAW kernels):
   float *aos_state;                    // [E][N][6] x y vx vy th om, read and written
   const uint8_t *r_shape, *r_flags;    // [E * N]
@@ -64,6 +69,44 @@ struct StepParams {
 };
 
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
+
+// ---- bulk (TMA) copies into shared memory, completed on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Global -> shared bulk copy of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned), counted against the mbarrier's transaction bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Wait for phase `parity` of the mbarrier to complete, at most `tries` polls;
+// false if it did not.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int tries) {
+  for (int i = 0; i < tries; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 // Self-checking build (compiled with -DVMAS_CHECKED only): every shared and
 // global index goes through VIDX, which records the first index outside

@@ -104,6 +104,31 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     if (p.env_list && (int)(blockIdx.x * kFusedWarps * EPW) >= *p.env_count) return;
   }
   uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
+  // Bulk staging (one-step plain kernels, full CTAs): the CTA's envs are
+  // contiguous in every plane, so one thread issues a bulk copy per plane,
+  // for the parameters, the actions and the kinds into the per-env area
+  // (which is free until the poses are published), counted on one mbarrier.
+  constexpr int CE = kFusedWarps * EPW;  // envs per CTA
+  __shared__ __align__(8) unsigned long long s_mbar;
+  bool bulk = false;
+  if constexpr (!RAW && !RAGGED && !TILED)
+    bulk = p.bulk && !p.env_list && (blockIdx.x + 1) * CE <= p.E;
+  unsigned char *stage = smem + align16(2 * P);
+  const uint32_t plane_b = (uint32_t)(CE * NL * 4), param_b = 4 * plane_b;
+  const uint32_t act_b = (uint32_t)(CE * p.A * 12), kind_b = (uint32_t)(CE * NL);
+  if (bulk && threadIdx.x == 0) {
+    const uint32_t bar = smem_u32(&s_mbar);
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, 6 * plane_b + param_b + act_b + kind_b);
+    const size_t e0 = (size_t)blockIdx.x * CE * NL;
+    const float *planes[6] = {p.px, p.py, p.vx, p.vy, p.th, p.om};
+    for (int f = 0; f < 6; ++f) bulk_g2s(smem_u32(stage + f * plane_b), planes[f] + e0, plane_b, bar);
+    bulk_g2s(smem_u32(stage + 6 * plane_b), p.param + e0, param_b, bar);
+    if (act_b)
+      bulk_g2s(smem_u32(stage + 6 * plane_b + param_b),
+               p.actions + (size_t)blockIdx.x * CE * p.A * 3, act_b, bar);
+    bulk_g2s(smem_u32(stage + 6 * plane_b + param_b + act_b), p.kind + e0, kind_b, bar);
+  }
   for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / G, lg = lane % G;
@@ -154,7 +179,38 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
   uint32_t kd[SLOTS];  // kind byte; bits 8.. hold 1 + the entity's action row (0: none)
   float4 prs[SLOTS];
-  if constexpr (!RAW) {
+  const int le = warp * EPW + grp;  // this env's index within the CTA
+  if (bulk) {
+    // bounded wait for the staging copies; a CTA whose copies did not arrive
+    // flags the error, waits once more for them (bounded) and leaves its
+    // envs unchanged
+    const bool late = !mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        atomicOr(p.err, 8);  // VMAS_DEVERR_TIMEOUT
+        mbar_wait(smem_u32(&s_mbar), 0, 1 << 22);
+      }
+      __syncthreads();
+      return;
+    }
+    const float *sp = reinterpret_cast<const float *>(stage);
+    const float4 *sq = reinterpret_cast<const float4 *>(stage + 6 * plane_b);
+    const unsigned char *sk = stage + 6 * plane_b + param_b + act_b;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int a = lg + G * s;
+      const bool ok = a < N;
+      const int q = le * NL + (ok ? a : 0);
+      kd[s] = ok ? sk[q] : 0u;
+      x[s] = ok ? sp[q] : 0.f;
+      y[s] = ok ? sp[CE * NL + q] : 0.f;
+      vx[s] = ok ? sp[2 * CE * NL + q] : 0.f;
+      vy[s] = ok ? sp[3 * CE * NL + q] : 0.f;
+      th[s] = ok ? sp[4 * CE * NL + q] : 0.f;
+      om[s] = ok ? sp[5 * CE * NL + q] : 0.f;
+      prs[s] = ok ? sq[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else if constexpr (!RAW) {
     // every slot's loads first, so that they are in flight together (the
     // processing below synchronises the warp once per slot)
 #pragma unroll
@@ -179,7 +235,47 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a0 + off));
     }
   }
+  // the k-th actuated entity of the env (entity order = slot-major) reads row k
   int act_base = 0;
+  auto assign_rows = [&]() {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const bool ok = valid && lg + G * s < N;
+      const bool actuated = ok && (kd[s] & kActuated);
+      const unsigned gb = __ballot_sync(FULL, actuated) & gbits;
+      const int r = act_base + __popc(gb & lt);
+      act_base += __popc(gb);
+      if (actuated && r < A_e) kd[s] |= (uint32_t)(r + 1) << 8;
+    }
+  };
+  // Eq. 1: action + gravity, constant over a step (only movable bodies
+  // integrate, so only their mass matters); a staged step reads its actions
+  // from shared memory
+  auto load_actions = [&](int t) {
+    const float *base = (bulk && t == 0)
+                            ? reinterpret_cast<const float *>(stage + 6 * plane_b + param_b) +
+                                  (size_t)le * p.A * 3
+                            : p.actions + (size_t)t * p.act_step + arow0 * 3;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      float fax = 0.f, fay = 0.f;
+      tau[s] = 0.f;
+      if (kd[s] >> 8) {
+        const float *ap = base + ((kd[s] >> 8) - 1) * 3;
+        fax = ap[0];
+        fay = ap[1];
+        tau[s] = (kd[s] & kRotatable) ? ap[2] : 0.f;
+      }
+      const float m = prs[s].x > 0.f ? 1.f / prs[s].x : 0.f;
+      fbx[s] = fax + m * p.gx;
+      fby[s] = fay + m * p.gy;
+    }
+  };
+  if constexpr (!RAW) {
+    assign_rows();
+    load_actions(0);
+    if (bulk) __syncthreads();  // staging read: the per-env area may now be written
+  }
 #pragma unroll
   for (int s = 0; s < SLOTS; ++s) {
     const int a = lg + G * s;
@@ -209,6 +305,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
                            sh == kSphere ? sa : 0.5f * sa, sh == kBox ? 0.5f * sb : 0.f);
         }
       }
+      prs[s] = pr;
     } else {
       pr = prs[s];
     }
@@ -224,32 +321,11 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
       s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
     }
-    // the k-th actuated entity of the env (entity order = slot-major) reads row k
-    const bool actuated = ok && (kd[s] & kActuated);
-    const unsigned gb = __ballot_sync(FULL, actuated) & gbits;
-    const int r = act_base + __popc(gb & lt);
-    act_base += __popc(gb);
-    if (actuated && r < A_e) kd[s] |= (uint32_t)(r + 1) << 8;
   }
-  // Eq. 1: action + gravity, constant over a step (only movable bodies
-  // integrate, so only their mass matters)
-  auto load_actions = [&](int t) {
-#pragma unroll
-    for (int s = 0; s < SLOTS; ++s) {
-      float fax = 0.f, fay = 0.f;
-      tau[s] = 0.f;
-      if (kd[s] >> 8) {
-        const float *ap = p.actions + (size_t)t * p.act_step + (arow0 + (kd[s] >> 8) - 1) * 3;
-        fax = ap[0];
-        fay = ap[1];
-        tau[s] = (kd[s] & kRotatable) ? ap[2] : 0.f;
-      }
-      const float m = im[s] > 0.f ? 1.f / im[s] : 0.f;
-      fbx[s] = fax + m * p.gx;
-      fby[s] = fay + m * p.gy;
-    }
-  };
-  load_actions(0);
+  if constexpr (RAW) {
+    assign_rows();
+    load_actions(0);
+  }
 
   const float move_limit = 0.499f * p.skin;
   bool full = false;    // group scans all pairs (list overflow)

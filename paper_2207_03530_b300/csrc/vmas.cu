@@ -208,8 +208,25 @@ int group_lanes(int N) {
   return N <= 8 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : 32;
 }
 
-int launch_step(const StepParams &p, cudaStream_t st, bool tiled = false) {
-  if (p.E == 0) return VMAS_OK;
+// Whether the one-step kernel may stage a full CTA's inputs with bulk copies:
+// every copy a multiple of 16 bytes from a 16-byte aligned address, and the
+// staging no larger than the CTA's per-env shared memory it borrows.
+bool bulk_staging_ok(const StepParams &p) {
+  const int G = group_lanes(p.N), CE = vmas::kFusedWarps * (32 / G);
+  const size_t ents = (size_t)CE * p.N;
+  if (ents % 16 != 0) return false;  // kind bytes
+  auto misaligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) != 0; };
+  const void *bases[9] = {p.px, p.py, p.vx, p.vy, p.th, p.om, p.param, p.kind, p.actions};
+  for (int k = 0; k < 9; ++k)
+    if ((k < 8 || p.A > 0) && misaligned(bases[k])) return false;
+  const size_t stage = ents * (6 * 4 + 16 + 1) + (size_t)CE * p.A * 12;
+  return stage <= (size_t)CE * vmas::fused_env_bytes(p.N, G);
+}
+
+int launch_step(const StepParams &p0, cudaStream_t st, bool tiled = false) {
+  if (p0.E == 0) return VMAS_OK;
+  StepParams p = p0;
+  p.bulk = !tiled && !p.env_list && bulk_staging_ok(p) ? 1 : 0;
   switch (group_lanes(p.N)) {
     case 4: return tiled ? launch_step_g<4, true>(p, st) : launch_step_g<4, false>(p, st);
     case 8: return tiled ? launch_step_g<8, true>(p, st) : launch_step_g<8, false>(p, st);
