@@ -272,6 +272,13 @@ int vmas_diff_backward(vmas_world *world, const float *d_actions, int32_t n_step
                        const float *d_goals, int32_t ckpt_every, const float *d_ckpt,
                        const float *d_dloss, float *d_grad, void *stream);
 
+/* Test hook for failure detection without a GPU fault: while `on` is set,
+ * every CTA of vmas_step that stages its inputs with bulk copies waits for 16
+ * transaction bytes that no copy delivers, so its bounded wait runs out (in
+ * a few seconds); the CTA then sets VMAS_DEVERR_TIMEOUT and leaves its envs
+ * unchanged, and the context stays usable.  Off by default. */
+int vmas_debug_stage_timeout(vmas_world *world, int32_t on);
+
 /* Diagnostic: the cosine and sine the step uses for a body angle, for n
  * device angles d_theta into device d_cos_sin [n][2] (cos, sin); the
  * library's own range reduction and series, absolute error about 1e-7. */

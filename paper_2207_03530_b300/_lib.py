@@ -19,7 +19,8 @@ SYMBOLS = (
     "vmas_step_host", "vmas_rollout", "vmas_rollout_host", "vmas_state", "vmas_set_state", "vmas_debug_pairs",
     "vmas_pair_table", "vmas_check", "vmas_last_error", "vmas_abi_version",
     "vmas_world_set_skin", "vmas_world_get_skin", "vmas_world_set_stats", "vmas_world_get_stats",
-    "vmas_debug_body_axes", "vmas_step_noalloc", "vmas_diff_rollout", "vmas_diff_backward",
+    "vmas_debug_body_axes", "vmas_debug_stage_timeout", "vmas_step_noalloc",
+    "vmas_diff_rollout", "vmas_diff_backward",
     "vmas_lidar", "vmas_world_set_rollout_tile",
     "vmas_ragged_create", "vmas_ragged_destroy", "vmas_ragged_info", "vmas_ragged_action_offsets",
     "vmas_ragged_step", "vmas_ragged_rollout", "vmas_ragged_state", "vmas_ragged_set_state",
@@ -115,6 +116,7 @@ def load():
         "vmas_world_set_stats": ([vp, i32], ctypes.c_int),
         "vmas_world_get_stats": ([vp, vp, i32, vp], ctypes.c_int),
         "vmas_debug_body_axes": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_debug_stage_timeout": ([vp, i32], ctypes.c_int),
         "vmas_step_noalloc": ([P(StepNoallocArgs), vp], ctypes.c_int),
         "vmas_diff_rollout": ([vp, vp, i32, vp, i32, vp, vp, vp], ctypes.c_int),
         "vmas_diff_backward": ([vp, vp, i32, vp, i32, vp, vp, vp, vp], ctypes.c_int),

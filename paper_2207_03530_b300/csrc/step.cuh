@@ -62,6 +62,9 @@ struct StepParams {
   // copies; the host sets it only when every copy is 16-byte aligned and the
   // staging fits the CTA's shared memory
   int bulk;
+  // test hook: extra transaction bytes the staging mbarrier waits for, which
+  // no copy delivers, so that its bounded wait runs out (0 in normal use)
+  uint32_t stage_extra_tx;
   // caller-owned buffers of the allocation-free entry point (RAW kernels):
   float *aos_state;                    // [E][N][6] x y vx vy th om, read and written
   const uint8_t *r_shape, *r_flags;    // [E * N]
@@ -91,17 +94,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-// Wait for phase `parity` of the mbarrier to complete, at most `tries` polls;
-// false if it did not.
+// Wait for phase `parity` of the mbarrier to complete: at most `tries` polls,
+// each suspending the thread for at most about 1 us, so at most about
+// tries us in all; false if it did not complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int tries) {
   for (int i = 0; i < tries; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000u)
         : "memory");
     if (done) return true;
   }

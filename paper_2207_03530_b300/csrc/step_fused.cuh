@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   if (bulk && threadIdx.x == 0) {
     const uint32_t bar = smem_u32(&s_mbar);
     mbar_init(bar, 1);
-    mbar_expect_tx(bar, 6 * plane_b + param_b + act_b + kind_b);
+    mbar_expect_tx(bar, 6 * plane_b + param_b + act_b + kind_b + p.stage_extra_tx);
     const size_t e0 = (size_t)blockIdx.x * CE * NL;
     const float *planes[6] = {p.px, p.py, p.vx, p.vy, p.th, p.om};
     for (int f = 0; f < 6; ++f) bulk_g2s(smem_u32(stage + f * plane_b), planes[f] + e0, plane_b, bar);
@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     // bounded wait for the staging copies; a CTA whose copies did not arrive
     // flags the error, waits once more for them (bounded) and leaves its
     // envs unchanged
-    const bool late = !mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);
+    const bool late = !mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);  // about 1 s
     if (__syncthreads_or(late)) {
       if (threadIdx.x == 0) {
         atomicOr(p.err, 8);  // VMAS_DEVERR_TIMEOUT
-        mbar_wait(smem_u32(&s_mbar), 0, 1 << 22);
+        mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);
       }
       __syncthreads();
       return;

@@ -45,6 +45,7 @@ struct vmas_world {
   float skin = 0;  // candidate-list margin
   bool diff_ok = false;  // every entity a sphere, N <= 32 (differentiable rollout)
   bool sur_ok = false;   // 16 actuated agent spheres then 4 fixed walls (surrogate)
+  bool stage_timeout_test = false;  // vmas_debug_stage_timeout
   int tile = 1;          // world steps per launch in vmas_rollout
   float *planes = nullptr;  // 6 * E * N
   float4 *param = nullptr;
@@ -138,6 +139,7 @@ StepParams make_params(const vmas_world *w) {
   p.tile = 1;
   p.act_step = (size_t)w->E * w->A * 3;
   p.EN = EN;
+  p.stage_extra_tx = w->stage_timeout_test ? 16u : 0u;
   return p;
 }
 
@@ -966,6 +968,12 @@ int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, voi
   const size_t smem = (size_t)w->N * (16 + 8 + 1) + 16;
   vmas::lidar_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
   VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int vmas_debug_stage_timeout(vmas_world *w, int32_t on) {
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  w->stage_timeout_test = on != 0;
   return VMAS_OK;
 }
 

@@ -312,3 +312,25 @@ def test_rollout_host_streams_every_state(vmas_lib):
         assert torch.equal(got2[t], w1.state().cpu()), t
     for w in (w1, w2):
         w.close()
+
+
+def test_bulk_staged_and_plain_loads_agree_bitwise(vmas_lib):
+    """Full CTAs stage their inputs with bulk copies when every copy is
+    16-byte aligned; an action array that starts 4 bytes past a 16-byte
+    boundary turns staging off.  Both paths must give the same bits."""
+    sc = scenes.paper_scene(1000, 8, dense=True)
+    act = torch.from_numpy(scenes.make_actions(sc, 3, 4)).cuda()
+    n = act[0].numel()
+    raw = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+    off = raw[1:1 + n].view(act[0].shape)  # starts 4 bytes past the allocation
+    assert off.data_ptr() % 16 == 4 and act[0].data_ptr() % 16 == 0
+    w1, w2 = _world(sc), _world(sc)
+    for t in range(3):
+        w1.step(act[t])
+        off.copy_(act[t])
+        w2.step(off)
+    assert torch.equal(w1.state(), w2.state())
+    w1.check()
+    w2.check()
+    w1.close()
+    w2.close()
