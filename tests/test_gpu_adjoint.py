@@ -104,3 +104,39 @@ def test_rejects_non_sphere_worlds(vmas_lib):
     with pytest.raises(_lib.VmasError):
         rollout_loss(w, a, torch.zeros((4, sc.n_actuated, 2), device="cuda"))
     w.close()
+
+
+def _sphere_subset(sc, ents, A):
+    import dataclasses
+
+    kw = dataclasses.asdict(sc)
+    for key in ("shape", "flags", "size_a", "size_b", "mass", "inertia", "init_state"):
+        kw[key] = np.ascontiguousarray(getattr(sc, key)[:, ents])
+    kw.update(n_entities=len(ents), n_actuated=A)
+    return scenes.Scene(**kw)
+
+
+@pytest.mark.parametrize("which,E", [("n3", 5), ("n6", 17), ("n16", 7), ("n16", 1)])
+def test_lane_groups_of_every_width(vmas_lib, orc, which, E):
+    """Envs of 3, 6 and 16 spheres take 4, 8 and 16 lanes (8, 4 and 2 envs
+    per warp); env counts that leave groups of a warp empty."""
+    from paper_2207_03530_b300 import World
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    if which == "n6":
+        sc = scenes.small_scene(E, 4, dense=True)
+    else:
+        base = scenes.paper_scene(E, 5, dense=True)
+        n = 3 if which == "n3" else 16
+        sc = _sphere_subset(base, list(range(n)), n)
+    T = 20
+    act = scenes.make_actions(sc, T, 6)
+    goals = scenes.make_goals(sc, 7)
+    w = World(sc)
+    a = torch.from_numpy(act).cuda().requires_grad_(True)
+    loss = rollout_loss(w, a, torch.from_numpy(goals).cuda(), ckpt_every=7)
+    loss.sum().backward()
+    ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
+    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= 1e-4
+    assert _relerr(a.grad.cpu().numpy(), ref_grad) <= 2e-3
+    w.close()

@@ -334,3 +334,11 @@ def test_bulk_staged_and_plain_loads_agree_bitwise(vmas_lib):
     w2.check()
     w1.close()
     w2.close()
+
+
+def test_empty_world_streamed_rollout(vmas_lib):
+    sc = scenes.small_scene(4, 0).subset([])
+    w = _world(sc)
+    out = w.rollout_host(np.zeros((3, 0, 4, 3), np.float32))
+    assert tuple(out.shape) == (3, 0, 6, 6)
+    w.close()
