@@ -53,6 +53,23 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+def _tensor_peak():
+    """Dense bf16 TFLOP/s (burst) of the B300s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1800.0, "fallback"
+
+
+def _hbm_roofline(bytes_per_env_step, env_steps_per_s, note):
+    peak, kind = _peaks()
+    gbs = bytes_per_env_step * env_steps_per_s / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_source": "%s hbm_gbs" % kind, "bytes_per_env_step": bytes_per_env_step,
+            "note": note}
+
+
 # the sources the plain step kernel is compiled from
 STEP_KERNEL_SOURCES = ("contact.cuh", "step.cuh", "step_fused.cuh")
 
@@ -461,9 +478,16 @@ def run_adjoint(args):
     got = grad.cpu().numpy()[:, pick]
     err = float(np.abs(got - ref).max() / np.abs(ref).max())
     w.close()
+    # per env-step: actions read by the forward and by the backward, the
+    # action gradient written, checkpoints (x, y, vx, vy of every entity every
+    # K steps) written and read back
+    A_, N_ = sc.n_actuated, sc.n_entities
+    b_env = 2 * A_ * 12 + A_ * 12 + 2 * N_ * 16 / K
     print(json.dumps({
         "form": "adjoint", "metric": "env-steps/s, differentiable rollout forward + backward",
         "value": E * T / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+        "roofline": _hbm_roofline(b_env, E * T / (ms / 1e3),
+                                  "latency-bound (profiles/diff_backward_kernel_4k.md)"),
         "plain_step_value": E * T / (plain_ms / 1e3), "rollout_steps": T, "ckpt_every": K,
         "grad_rel_err_vs_fp64_oracle": err, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "%d envs x (8 agent spheres + 2 landmarks), 3 substeps, %d steps"
@@ -520,9 +544,15 @@ def run_ragged(args):
     torch.cuda.synchronize()
     padded = E * 17 / (a.elapsed_time(b) / 1e3)
     w.close()
+    # per env-step, as for the plain step: state read + write of every
+    # entity and the useful action rows (the tiled rollout touches the state
+    # once per launch, so this is what a one-step launch would move)
+    b_env = (int(counts.sum()) * 48 + int(rw.n_action_rows) * 12) / E
     print(json.dumps({
         "form": "ragged", "metric": "env-steps/s, ragged rollout (CUDA graph, autotuned)",
         "value": value, "unit": UNIT, "ms_per_rollout": ms, "rollout_steps": T,
+        "roofline": _hbm_roofline(b_env, value, "latency-bound size classes "
+                                  "(profiles/world_step_ragged_class128_8k.md)"),
         "entities": int(counts.sum()), "envs": E, "lanes_per_class": [int(x) for x in lanes],
         "steps_per_launch": tile, "padded_regular_world_value": padded, "dtype": "f32",
         "data": "synthetic",
@@ -620,10 +650,26 @@ def run_surrogate(args):
                            "plain_s1_mean_pos_err_50": e1, "plain_s1_pos_err_at_50": e1_end})
         del out
     r5 = res[5]
+    # useful network FLOPs per env: the edge MLP on every present edge (up to
+    # 6 nearest agents within 0.3, counted on the start state) and the node
+    # MLP on the 16 agents
+    xy = sc5.init_state[:, :16, :2].astype(np.float64)
+    d = np.linalg.norm(xy[:, :, None, :] - xy[:, None, :, :], axis=-1)
+    d[:, np.arange(16), np.arange(16)] = np.inf
+    edges = float(np.minimum((d < 0.3).sum(-1), 6).sum(-1).mean())
+    flop_env = 2.0 * (edges * (16 * 64 + 64 * 64) + 16 * (80 * 128 + 128 * 128 + 128 * 8))
+    tpeak, tkind = _tensor_peak()
+    tflops = flop_env * r5["surrogate_value"] / 1e12
+    roof = {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+            "frac": tflops / tpeak, "peak_source": "%s bf16_tflops (burst)" % tkind,
+            "flop_per_env": flop_env, "edges_per_env": edges,
+            "note": "instruction-issue-bound on the GELUs, not on the tensor pipe "
+                    "(profiles/sur_fused_kernel_16k.md)"}
     print(json.dumps({
         "form": "surrogate",
         "metric": "env-steps/s, learned surrogate step (with plain-step fallback)",
         "value": r5["surrogate_value"], "unit": UNIT, "ms_per_step": r5["surrogate_ms_per_step"],
+        "roofline": roof,
         "plain_s5_value": r5["plain_value"], "plain_s1_value": r5["plain_s1_value"],
         "layered_surrogate_value": r5["layered_surrogate_value"],
         "surrogate_mean_pos_err_50": r5["surrogate_mean_pos_err_50"],
