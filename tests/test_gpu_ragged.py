@@ -158,3 +158,31 @@ def test_regular_world_tiled_rollout_is_bitwise(vmas_lib):
         outs.append(w.state().cpu().numpy())
         w.close()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_full_config_sampled_envs(vmas_lib, orc):
+    """65,536 ragged envs (2.55 M entities) with the benchmark's autotuned
+    lanes and steps per launch: one graph step against the oracle on 32
+    sampled envs, then an 8-step graph rollout bitwise equal to stepping."""
+    sc, counts = scenes.ragged_scene(65536, 0)
+    rw = _ragged(sc, counts)
+    rw2 = _ragged(sc, counts)
+    T = 9
+    act = scenes.make_actions(sc, T, 1)
+    pact = torch.from_numpy(_packed_actions(rw, sc, act)).cuda()
+    rw.autotune(pact[:8])
+    lanes, tile = rw.tuning()
+    rw2.set_tuning(lanes, tile)
+    rw.rollout(pact[:1])
+    got = rw.state().cpu().numpy()
+    full, sel = _unpack_state(got, counts, sc.n_entities)
+    pick = np.random.default_rng(3).choice(sc.n_envs, 32, replace=False)
+    sub = sc.subset(pick)
+    ref = orc.step(sub, sub.init_state, act[:1, pick], threads=8)
+    assert normwise_err(full[pick][sel[pick]], ref[sel[pick]]).max() <= TOL
+    rw.rollout(pact[1:])
+    for t in range(T):
+        rw2.step(pact[t])
+    assert np.array_equal(rw.state().cpu().numpy(), rw2.state().cpu().numpy())
+    rw.close()
+    rw2.close()
