@@ -426,7 +426,7 @@ def run_native(args):
 
 
 def run_adjoint(args):
-    """Differentiable rollout (BASELINE config 4): 4,096 envs x (8 agents + 2
+    """Differentiable rollout workload: 4,096 envs x (8 agents + 2
     landmarks), 3 substeps, 50 steps, checkpoint every 10.  Times forward +
     backward (hand-written adjoint) and the plain step on the same scene,
     and checks 4 sampled envs' gradients against the FP64 oracle."""
@@ -496,7 +496,7 @@ def run_adjoint(args):
 
 
 def run_ragged(args):
-    """Ragged batching (BASELINE config 3): 65,536 envs of 2-64 agents,
+    """Ragged batching workload: 65,536 envs of 2-64 agents,
     0-8 boxes, 0-4 walls, packed without padding; autotuned lanes per env and
     steps per launch; a 500-step rollout captured in a CUDA graph.  Also
     times the same scene padded to its largest env on the regular world."""
@@ -598,12 +598,12 @@ def _pos_err(a, b):
 
 
 def run_surrogate(args):
-    """Learned surrogate (BASELINE config 5): 262,144 envs x 16 agent spheres
+    """Learned surrogate workload: 262,144 envs x 16 agent spheres
     (+ 4 walls), 50-step rollouts.  For each substep count S in (5, 1) the
     network is trained on the GPU with the library's own forward / backward /
     Adam kernels on transitions of the plain step at S substeps; then the
     same 50 steps run from the same start with the plain step at S (the
-    judge of the error) and with the surrogate and its plain-step fallback.
+    reference for the error) and with the surrogate and its plain-step fallback.
     Reports env-steps/s of each and the mean agent position error; at S = 5
     also the plain step at 1 substep against the 5-substep reference (the
     cheap method without a network)."""
@@ -741,7 +741,7 @@ def run_sweep(args):
 
 
 def run_small(args):
-    """Small workload (BASELINE config 1): 32 envs x (4 agents + 2 landmarks),
+    """Small workload: 32 envs x (4 agents + 2 landmarks),
     1 substep, 100 steps: latency per step, launched one by one and replayed
     from a CUDA graph captured around the same 100 launches.  A roofline
     fraction at 4.6 KB of state is meaningless; it is reported, labelled
