@@ -66,10 +66,6 @@ struct GemmArgs {
 
 constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
 
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
   __shared__ __align__(16) bf16 As[kBM][kBK + kPad];  // [m][k]
@@ -88,39 +84,65 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   const bf16 zero = __float2bfloat16_rn(0.f);
+  // 16-byte loads of 8 consecutive elements where the operand allows them
+  const bool vecA = ((reinterpret_cast<uintptr_t>(g.A) | (uintptr_t)g.lda * 2) & 15u) == 0;
+  const bool vecB = ((reinterpret_cast<uintptr_t>(g.B) | (uintptr_t)g.ldb * 2) & 15u) == 0;
+  // Stage a 64 x 32 tile T[r][kk] of an operand X whose element (r, k) is at
+  // X[k ld + r] (KMAJOR = false) or X[r ld + k] (true), rows < R, k < kend.
+  auto stage = [&](bf16 (*T)[kBK + kPad], const bf16 *X, int ld, int r0, int R, int k0, bool vec,
+                   bool kmajor) {
+    for (int q = tid; q < kBM * kBK / 8; q += 128) {
+      // chunk of 8 along the contiguous dimension
+      const int a = kmajor ? q / (kBK / 8) : q % (kBM / 8);  // row chunk / row
+      const int b = kmajor ? q % (kBK / 8) : q / (kBM / 8);  // k chunk / k
+      if (kmajor) {
+        const int r = r0 + a, k = k0 + 8 * b;
+        if (vec && r < R && k + 8 <= kend) {
+          *reinterpret_cast<uint4 *>(&T[a][8 * b]) =
+              *reinterpret_cast<const uint4 *>(X + (size_t)r * ld + k);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            T[a][8 * b + i] = (r < R && k + i < kend) ? X[(size_t)r * ld + k + i] : zero;
+        }
+      } else {
+        const int r = r0 + 8 * a, k = k0 + b;
+        if (vec && r + 8 <= R && k < kend) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(X + (size_t)k * ld + r);
+          const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) T[8 * a + i][b] = e[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            T[8 * a + i][b] = (r + i < R && k < kend) ? X[(size_t)k * ld + r + i] : zero;
+        }
+      }
+    }
+  };
   for (int k0 = kbeg; k0 < kend; k0 += kBK) {
     // stage the tiles (bounds-checked, zero filled)
-    for (int q = tid; q < kBM * kBK; q += 128) {
-      const int mm = TA ? (q % kBM) : (q / kBK), kk = TA ? (q / kBM) : (q % kBK);
-      const int m = m0 + mm, k = k0 + kk;
-      bf16 v = zero;
-      if (m < g.M && k < kend) v = TA ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-      As[mm][kk] = v;
-    }
-    for (int q = tid; q < kBN * kBK; q += 128) {
-      const int nn = TB ? (q / kBK) : (q % kBN), kk = TB ? (q % kBK) : (q / kBN);
-      const int n = n0 + nn, k = k0 + kk;
-      bf16 v = zero;
-      if (n < g.N && k < kend) v = TB ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
-      Bs[nn][kk] = v;
-    }
+    stage(As, g.A, g.lda, m0, g.M, k0, vecA, !TA);
+    stage(Bs, g.B, g.ldb, n0, g.N, k0, vecB, TB);
     __syncthreads();
 #pragma unroll
     for (int ks = 0; ks < kBK; ks += 16) {
       uint32_t af[2][4], bfr[4][2];
+      // fragment pairs are adjacent bfloat16 values: one 32-bit load each
+      auto ld2 = [](const bf16 *q) { return *reinterpret_cast<const uint32_t *>(q); };
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int r = wm + a * 16 + gi, c = ks + 2 * ti;
-        af[a][0] = pack2(As[r][c], As[r][c + 1]);
-        af[a][1] = pack2(As[r + 8][c], As[r + 8][c + 1]);
-        af[a][2] = pack2(As[r][c + 8], As[r][c + 9]);
-        af[a][3] = pack2(As[r + 8][c + 8], As[r + 8][c + 9]);
+        af[a][0] = ld2(&As[r][c]);
+        af[a][1] = ld2(&As[r + 8][c]);
+        af[a][2] = ld2(&As[r][c + 8]);
+        af[a][3] = ld2(&As[r + 8][c + 8]);
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int n = wn + b * 8 + gi, c = ks + 2 * ti;
-        bfr[b][0] = pack2(Bs[n][c], Bs[n][c + 1]);
-        bfr[b][1] = pack2(Bs[n][c + 8], Bs[n][c + 9]);
+        bfr[b][0] = ld2(&Bs[n][c]);
+        bfr[b][1] = ld2(&Bs[n][c + 8]);
       }
 #pragma unroll
       for (int a = 0; a < 2; ++a)
