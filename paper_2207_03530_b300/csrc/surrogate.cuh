@@ -350,12 +350,18 @@ __global__ void loss_kernel(int R, const float *out, const float *y, float *d_ou
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// One block of 256 threads: strided partial sums, then a tree.
 __global__ void finish_loss_kernel(const float *part, int n, int R, float *loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    float s = 0.f;
-    for (int q = 0; q < n; ++q) s += part[q];
-    *loss = s / (4.f * (float)R);
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *loss = red[0] / (4.f * (float)R);
 }
 
 // Adam on FP32 master parameters; weights (not biases) mirrored to bfloat16.

@@ -1590,13 +1590,19 @@ int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, 
   return VMAS_OK;
 }
 
-// Column sums of x [M][N] (N <= 128) into out [N].
+// Column sums of x [M][N] (N <= 128) into out [N]: up to 4,096 row chunks
+// summed in parallel, then the chunk sums per column (two stages).
 int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *part) {
-  const int chunks = std::max(1, std::min(kSplitCap, (M + 1023) / 1024));
+  const int chunks = std::max(1, std::min(4096, (M + 255) / 256));
   const int chunk = (M + chunks - 1) / chunks;
   sur::col_sum_kernel<<<chunks, 128, 0, st>>>(part, x, M, N, chunk > 0 ? chunk : 1);
   VMAS_CUDA(cudaGetLastError());
-  sur::sum_partials_kernel<<<1, 128, 0, st>>>(out, part, chunks, (size_t)N);
+  // second stage: 64 groups of chunks, then the groups
+  const int groups = std::min(64, chunks), per = (chunks + groups - 1) / groups;
+  float *part2 = part + (size_t)chunks * N;
+  sur::col_sum_kernel<<<groups, 128, 0, st>>>(part2, part, chunks, N, per);
+  VMAS_CUDA(cudaGetLastError());
+  sur::sum_partials_kernel<<<1, 128, 0, st>>>(out, part2, groups, (size_t)N);
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
 }
@@ -1667,7 +1673,7 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
   sur::loss_kernel<<<lb, 256, 0, st>>>(R, s->out, target, s->d_out, s->d_outbf, s->loss_part);
   VMAS_CUDA(cudaGetLastError());
   if (d_loss) {
-    sur::finish_loss_kernel<<<1, 32, 0, st>>>(s->loss_part, lb, R, d_loss);
+    sur::finish_loss_kernel<<<1, 256, 0, st>>>(s->loss_part, lb, R, d_loss);
     VMAS_CUDA(cudaGetLastError());
   }
   int rc;
