@@ -444,7 +444,7 @@ def run_adjoint(args):
     goals = torch.from_numpy(scenes.make_goals(sc, args.seed + 2)).cuda()
 
     def fwd_bwd():
-        a = act.clone().requires_grad_(True)
+        a = act.detach().requires_grad_(True)  # a fresh leaf on the same storage
         rollout_loss(w, a, goals, ckpt_every=K).sum().backward()
         return a.grad
 
@@ -458,6 +458,34 @@ def run_adjoint(args):
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / args.steps
+    # the same forward + backward captured once into a CUDA graph (autograd
+    # included) and replayed: no host work per iteration
+    graph_ms = None
+    try:
+        static_a = act.detach().clone().requires_grad_(True)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                static_a.grad = None
+                rollout_loss(w, static_a, goals, ckpt_every=K).sum().backward()
+        torch.cuda.current_stream().wait_stream(side)
+        static_a.grad = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            rollout_loss(w, static_a, goals, ckpt_every=K).sum().backward()
+        g.replay()
+        torch.cuda.synchronize()
+        if not torch.equal(static_a.grad, grad):
+            raise RuntimeError("graphed gradient differs")
+        t0.record()
+        for _ in range(args.steps):
+            g.replay()
+        t1.record()
+        torch.cuda.synchronize()
+        graph_ms = t0.elapsed_time(t1) / args.steps
+    except Exception as exc:  # capture is an optional extra measurement
+        print("graph capture of the adjoint skipped: %s" % exc, file=sys.stderr)
     # plain fused step on the same scene, same actions
     for t in range(3):
         w.step(act[t])
@@ -486,6 +514,8 @@ def run_adjoint(args):
     print(json.dumps({
         "form": "adjoint", "metric": "env-steps/s, differentiable rollout forward + backward",
         "value": E * T / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+        "graphed_value": E * T / (graph_ms / 1e3) if graph_ms else None,
+        "graphed_ms_per_rollout": graph_ms,
         "roofline": _hbm_roofline(b_env, E * T / (ms / 1e3),
                                   "latency-bound (profiles/diff_backward_kernel_4k.md)"),
         "plain_step_value": E * T / (plain_ms / 1e3), "rollout_steps": T, "ckpt_every": K,
