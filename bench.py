@@ -417,7 +417,8 @@ def run_native(args):
             "wall_s_timed_region": wall,
         }
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.envs, args.substeps, args.seed)
+            line["cpu_baseline"] = cpu_baseline(args.envs, args.substeps, args.seed,
+                                                budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
     world.close()
     if dist:
@@ -882,6 +883,8 @@ def main(argv=None):
     ap.add_argument("--train-steps", type=int, default=1500, help="surrogate form")
     ap.add_argument("--lr", type=float, default=2e-3, help="surrogate form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of host work the CPU-baseline sample is sized to")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--stats", action="store_true",
                     help="print step counters per env-step to stderr (extra pass)")
