@@ -71,7 +71,7 @@ def _hbm_roofline(bytes_per_env_step, env_steps_per_s, note):
 
 
 # the sources the plain step kernel is compiled from
-STEP_KERNEL_SOURCES = ("contact.cuh", "step.cuh", "step_fused.cuh")
+STEP_KERNEL_SOURCES = ("contact.cuh", "params.cuh", "step.cuh", "step_fused.cuh")
 
 
 def _kernel_digest():

@@ -1,4 +1,9 @@
-"""Build the CUDA library libvmas.so in-tree for sm_103a with nvcc."""
+"""Build the CUDA library libvmas.so in-tree for sm_103a with nvcc.
+
+The host code is three translation units (the world and its step, the
+packed ragged worlds, the surrogate); each compiles to an object in its own
+nvcc process, in parallel, and one nvcc call links them.
+"""
 from __future__ import annotations
 
 import glob
@@ -8,14 +13,14 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libvmas.so")
-SOURCES = [os.path.join(PKG, "csrc", "vmas.cu")]
+SOURCES = [os.path.join(PKG, "csrc", f) for f in ("vmas.cu", "ragged.cu", "surrogate_host.cu")]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-              "-Xcompiler", "-fPIC", "-shared"]
+              "-Xcompiler", "-fPIC"]
 
 
 def _inputs():
     return SOURCES + glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + \
-        [os.path.join(ROOT, "include", "vmas.h"), __file__]
+        [os.path.join(PKG, "csrc", "host.h"), os.path.join(ROOT, "include", "vmas.h"), __file__]
 
 
 def stale() -> bool:
@@ -30,12 +35,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    tag = ".tmp%d" % os.getpid()
+    objs = [LIB[:-3] + "_" + os.path.basename(src)[:-3] + tag + ".o" for src in SOURCES]
+    procs = []
+    try:
+        for src, obj in zip(SOURCES, objs):
+            cmd = [nvcc, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", "-o", obj, src]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            procs.append((cmd, subprocess.Popen(cmd)))
+        for cmd, pr in procs:
+            if pr.wait() != 0:
+                raise subprocess.CalledProcessError(pr.returncode, cmd)
+        tmp = LIB + tag
+        subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
+                        "-o", tmp, *objs], check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for pr in procs:
+            if pr[1].poll() is None:
+                pr[1].kill()
+                pr[1].wait()
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 

@@ -1,0 +1,542 @@
+// ------------------------------------------------------------------------
+// Learned surrogate (surrogate.cuh): a per-agent message-passing network
+// that predicts a whole world step of the 16-agent walled sphere world, with
+// the plain step as the fallback for envs whose prediction overlaps.
+
+#include "host.h"
+#include "surrogate_fused.cuh"
+
+using namespace vmas_host;
+
+namespace {
+
+using vmas::sur::bf16;
+namespace sur = vmas::sur;
+
+using namespace vmas::sur;  // parameter offsets kOff*
+constexpr int kSurParams = vmas::sur::kParams;
+constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
+
+}  // namespace
+
+struct vmas_surrogate {
+  int device = 0;
+  int cap = 0;  // envs
+  int mode = VMAS_SUR_FUSED;
+  int n_sm = 0;
+  bool fused_ready = false;  // shared-memory opt-in of the fused kernel done
+  int adam_t = 0;
+  float *p32 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  bf16 *pbf = nullptr;
+  // forward
+  bf16 *node = nullptr, *edge = nullptr, *he = nullptr, *zin = nullptr, *h1 = nullptr,
+       *h2 = nullptr;
+  float *mask = nullptr, *ze2 = nullptr, *out = nullptr;
+  // training (allocated on first use)
+  float *ze1 = nullptr, *z1 = nullptr, *z2 = nullptr;
+  float *d_out = nullptr, *g128 = nullptr, *d_zin = nullptr, *ge = nullptr;
+  bf16 *d_outbf = nullptr, *g128bf = nullptr, *gebf = nullptr;
+  float *part = nullptr, *loss_part = nullptr, *save = nullptr, *target = nullptr;
+  int *list = nullptr, *list_len = nullptr;
+};
+
+namespace {
+
+void free_sur(vmas_surrogate *s) {
+  if (!s) return;
+  void *ptrs[] = {s->p32,   s->grad,  s->adam_m, s->adam_v, s->pbf,    s->node,   s->edge,
+                  s->he,    s->zin,   s->h1,     s->h2,     s->mask,   s->ze2,    s->out,
+                  s->ze1,   s->z1,    s->z2,     s->d_out,  s->g128,   s->d_zin,  s->ge,
+                  s->d_outbf, s->g128bf, s->gebf, s->part,  s->loss_part, s->save, s->target,
+                  s->list,  s->list_len};
+  for (void *q : ptrs) cudaFree(q);
+  delete s;
+}
+
+template <typename T>
+bool dalloc(T **ptr, size_t count) {
+  return cudaMalloc((void **)ptr, (count > 0 ? count : 1) * sizeof(T)) == cudaSuccess;
+}
+
+int ensure_training(vmas_surrogate *s) {
+  if (s->ze1) return VMAS_OK;
+  const size_t R = (size_t)s->cap * sur::kAgents, RK = R * sur::kK;
+  const bool ok = dalloc(&s->ze1, RK * 64) && dalloc(&s->z1, R * 128) && dalloc(&s->z2, R * 128) &&
+                  dalloc(&s->d_out, R * 8) && dalloc(&s->d_outbf, R * 8) &&
+                  dalloc(&s->g128, R * 128) && dalloc(&s->g128bf, R * 128) &&
+                  dalloc(&s->d_zin, R * 80) && dalloc(&s->ge, RK * 64) &&
+                  dalloc(&s->gebf, RK * 64) && dalloc(&s->save, R * 4) &&
+                  dalloc(&s->target, R * 4);
+  if (!ok) {
+    cudaGetLastError();
+    return fail(VMAS_ENOMEM, "cudaMalloc failed for the surrogate's training buffers");
+  }
+  return VMAS_OK;
+}
+
+unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// C = A B (+ bias, GELU) through gemm_bf16_kernel; `splits` > 1 sums K in
+// chunks into part, reduced into out_f32 (then no bias / bf16 output).
+int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, int lda,
+         const bf16 *B, int ldb, const float *bias, int act, float *out_f32, int ldc_f,
+         bf16 *out_bf, int ldc_b, float *part = nullptr, int splits = 1) {
+  if (M == 0 || N == 0) return VMAS_OK;
+  sur::GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
+  g.bias = bias; g.act = act;
+  g.ldc_f = ldc_f; g.out_bf = out_bf; g.ldc_b = ldc_b;
+  if (splits > 1 && K > 0) {
+    int chunk = (K + splits - 1) / splits;
+    chunk = (chunk + sur::kBK - 1) / sur::kBK * sur::kBK;
+    splits = (K + chunk - 1) / chunk;
+    g.kchunk = chunk;
+    g.out_f32 = part;
+    g.ldc_f = N;
+  } else {
+    splits = 1;
+    g.kchunk = K > 0 ? K : 1;
+    g.out_f32 = out_f32;
+  }
+  const dim3 grid(blocks_for((size_t)M, sur::kBM), blocks_for((size_t)N, sur::kBN), splits);
+  if (!ta && !tb) sur::gemm_bf16_kernel<false, false><<<grid, 128, 0, st>>>(g);
+  else if (!ta && tb) sur::gemm_bf16_kernel<false, true><<<grid, 128, 0, st>>>(g);
+  else if (ta && !tb) sur::gemm_bf16_kernel<true, false><<<grid, 128, 0, st>>>(g);
+  else sur::gemm_bf16_kernel<true, true><<<grid, 128, 0, st>>>(g);
+  VMAS_CUDA(cudaGetLastError());
+  if (g.out_f32 == part && part) {
+    const size_t MN = (size_t)M * N;
+    sur::sum_partials_kernel<<<blocks_for(MN, 256), 256, 0, st>>>(out_f32, part, splits, MN);
+    VMAS_CUDA(cudaGetLastError());
+  }
+  return VMAS_OK;
+}
+
+// Column sums of x [M][N] (N <= 128) into out [N]: up to 4,096 row chunks
+// summed in parallel, then the chunk sums per column (two stages).
+int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *part) {
+  const int chunks = std::max(1, std::min(4096, (M + 255) / 256));
+  const int chunk = (M + chunks - 1) / chunks;
+  sur::col_sum_kernel<<<chunks, 128, 0, st>>>(part, x, M, N, chunk > 0 ? chunk : 1);
+  VMAS_CUDA(cudaGetLastError());
+  // second stage: 64 groups of chunks, then the groups
+  const int groups = std::min(64, chunks), per = (chunks + groups - 1) / groups;
+  float *part2 = part + (size_t)chunks * N;
+  sur::col_sum_kernel<<<groups, 128, 0, st>>>(part2, part, chunks, N, per);
+  VMAS_CUDA(cudaGetLastError());
+  sur::sum_partials_kernel<<<1, 128, 0, st>>>(out, part2, groups, (size_t)N);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int sur_check(vmas_surrogate *s, vmas_world *w, const float *d_actions) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  if (!w) return fail(VMAS_EINVAL, "world is NULL");
+  if (!w->sur_ok)
+    return fail(VMAS_EINVAL, "world layout is not 16 actuated agent spheres then 4 fixed lines");
+  if (w->E > s->cap)
+    return fail(VMAS_EINVAL, "world has " + std::to_string(w->E) + " envs, surrogate capacity " +
+                                 std::to_string(s->cap));
+  if (w->E > 0 && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
+  return VMAS_OK;
+}
+
+// Features of the world's current state, then the network; train = true also
+// keeps the FP32 pre-activations the backward needs.
+int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool train,
+                cudaStream_t st) {
+  const int E = w->E;
+  const int R = E * sur::kAgents, RK = R * sur::kK;
+  if (E == 0) return VMAS_OK;
+  sur::FeatureArgs f{};
+  const size_t EN = (size_t)E * w->N;
+  f.E = E; f.N = w->N; f.A = w->A;
+  f.px = w->planes; f.py = w->planes + EN; f.vx = w->planes + 2 * EN; f.vy = w->planes + 3 * EN;
+  f.param = w->param; f.actions = d_actions;
+  f.node = s->node; f.edge = s->edge; f.mask = s->mask;
+  sur::features_kernel<<<blocks_for(R, 128), 128, 0, st>>>(f);
+  VMAS_CUDA(cudaGetLastError());
+  const bf16 *W = s->pbf;
+  const float *P = s->p32;
+  int rc;
+  // edge MLP
+  if ((rc = gemm(st, false, true, RK, 64, 16, s->edge, 16, W + kOffWe1, 16, P + kOffbe1, 1,
+                 train ? s->ze1 : nullptr, 64, s->he, 64)))
+    return rc;
+  if ((rc = gemm(st, false, true, RK, 64, 64, s->he, 64, W + kOffWe2, 64, P + kOffbe2, 0, s->ze2,
+                 64, nullptr, 0)))
+    return rc;
+  sur::aggregate_kernel<<<blocks_for((size_t)R * 80, 256), 256, 0, st>>>(R, s->ze2, s->mask,
+                                                                          s->node, s->zin);
+  VMAS_CUDA(cudaGetLastError());
+  // node MLP
+  if ((rc = gemm(st, false, true, R, 128, 80, s->zin, 80, W + kOffW1, 80, P + kOffb1, 1,
+                 train ? s->z1 : nullptr, 128, s->h1, 128)))
+    return rc;
+  if ((rc = gemm(st, false, true, R, 128, 128, s->h1, 128, W + kOffW2, 128, P + kOffb2, 1,
+                 train ? s->z2 : nullptr, 128, s->h2, 128)))
+    return rc;
+  return gemm(st, false, true, R, 8, 128, s->h2, 128, W + kOffW3, 128, P + kOffb3, 0, s->out, 8,
+              nullptr, 0);
+}
+
+// Loss against target [R][4] and the gradient into s->grad (after sur_forward
+// with train = true).
+int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, cudaStream_t st) {
+  const int R = E * sur::kAgents, RK = R * sur::kK;
+  float *G = s->grad;
+  const bf16 *W = s->pbf;
+  VMAS_CUDA(cudaMemsetAsync(G, 0, kSurParams * sizeof(float), st));
+  if (E == 0) {
+    if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
+    return VMAS_OK;
+  }
+  const int lb = (int)blocks_for((size_t)R * 8, 256);
+  sur::loss_kernel<<<lb, 256, 0, st>>>(R, s->out, target, s->d_out, s->d_outbf, s->loss_part);
+  VMAS_CUDA(cudaGetLastError());
+  if (d_loss) {
+    sur::finish_loss_kernel<<<1, 256, 0, st>>>(s->loss_part, lb, R, d_loss);
+    VMAS_CUDA(cudaGetLastError());
+  }
+  int rc;
+  const int sp = kSplitCap;
+  // output layer
+  if ((rc = gemm(st, true, false, 8, 128, R, s->d_outbf, 8, s->h2, 128, nullptr, 0, G + kOffW3,
+                 128, nullptr, 0, s->part, sp)))
+    return rc;
+  if ((rc = col_sum(st, G + kOffb3, s->d_out, R, 8, s->part))) return rc;
+  if ((rc = gemm(st, false, false, R, 128, 8, s->d_outbf, 8, W + kOffW3, 128, nullptr, 0, s->g128,
+                 128, nullptr, 0)))
+    return rc;
+  // node layer 2
+  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
+                                                                           s->z2, s->g128, s->g128bf);
+  VMAS_CUDA(cudaGetLastError());
+  if ((rc = gemm(st, true, false, 128, 128, R, s->g128bf, 128, s->h1, 128, nullptr, 0, G + kOffW2,
+                 128, nullptr, 0, s->part, sp)))
+    return rc;
+  if ((rc = col_sum(st, G + kOffb2, s->g128, R, 128, s->part))) return rc;
+  if ((rc = gemm(st, false, false, R, 128, 128, s->g128bf, 128, W + kOffW2, 128, nullptr, 0,
+                 s->g128, 128, nullptr, 0)))
+    return rc;
+  // node layer 1
+  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
+                                                                           s->z1, s->g128, s->g128bf);
+  VMAS_CUDA(cudaGetLastError());
+  if ((rc = gemm(st, true, false, 128, 80, R, s->g128bf, 128, s->zin, 80, nullptr, 0, G + kOffW1, 80,
+                 nullptr, 0, s->part, sp)))
+    return rc;
+  if ((rc = col_sum(st, G + kOffb1, s->g128, R, 128, s->part))) return rc;
+  if ((rc = gemm(st, false, false, R, 80, 128, s->g128bf, 128, W + kOffW1, 80, nullptr, 0, s->d_zin,
+                 80, nullptr, 0)))
+    return rc;
+  // edge layer 2 (through the masked sum)
+  sur::edge_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>(R, s->d_zin, s->mask,
+                                                                           s->ze2, s->ge, s->gebf);
+  VMAS_CUDA(cudaGetLastError());
+  if ((rc = gemm(st, true, false, 64, 64, RK, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
+                 nullptr, 0, s->part, sp)))
+    return rc;
+  if ((rc = col_sum(st, G + kOffbe2, s->ge, RK, 64, s->part))) return rc;
+  if ((rc = gemm(st, false, false, RK, 64, 64, s->gebf, 64, W + kOffWe2, 64, nullptr, 0, s->ge, 64,
+                 nullptr, 0)))
+    return rc;
+  // edge layer 1
+  sur::gelu_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>((size_t)RK * 64, s->ge,
+                                                                          s->ze1, s->ge, s->gebf);
+  VMAS_CUDA(cudaGetLastError());
+  if ((rc = gemm(st, true, false, 64, 16, RK, s->gebf, 64, s->edge, 16, nullptr, 0, G + kOffWe1, 16,
+                 nullptr, 0, s->part, sp)))
+    return rc;
+  return col_sum(st, G + kOffbe1, s->ge, RK, 64, s->part);
+}
+
+int sur_adam(vmas_surrogate *s, float lr, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  ++s->adam_t;
+  const float c1 = (float)(1.0 - std::pow((double)b1, s->adam_t));
+  const float c2 = (float)(1.0 - std::pow((double)b2, s->adam_t));
+  sur::adam_kernel<<<blocks_for(kSurParams, 256), 256, 0, st>>>(
+      kSurParams, s->p32, s->grad, s->adam_m, s->adam_v, s->pbf, lr, b1, b2, eps, c1, c2);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+// The fused inference kernel over the world's envs: network output into
+// out (may be NULL); apply = true also applies the prediction and lists the
+// fallback envs.
+int sur_fused(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *out, bool apply,
+              float limit, cudaStream_t st) {
+  const int E = w->E;
+  if (E == 0) return VMAS_OK;
+  const size_t smem = sur::fused_smem_bytes();
+  if (!s->fused_ready) {  // > 48 KB of dynamic shared memory needs an opt-in
+    VMAS_CUDA(cudaFuncSetAttribute(sur::sur_fused_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    s->fused_ready = true;
+  }
+  sur::FusedArgs a{};
+  const size_t EN = (size_t)E * w->N;
+  a.E = E; a.N = w->N; a.A = w->A;
+  a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
+  a.param = w->param; a.actions = d_actions;
+  a.w = s->pbf; a.p = s->p32;
+  a.out = out; a.apply = apply ? 1 : 0; a.limit = limit;
+  a.list = s->list; a.list_len = s->list_len;
+  const int need = (E + sur::kFusedWarpsPerCta - 1) / sur::kFusedWarpsPerCta;
+  const int grid = std::max(1, std::min(need, s->n_sm));
+  sur::sur_fused_kernel<<<grid, sur::kFusedWarpsPerCta * 32, smem, st>>>(a);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+__global__ void f32_to_bf16_kernel(const float *x, bf16 *y, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = __float2bfloat16_rn(x[t]);
+}
+
+}  // namespace
+
+extern "C" {
+
+int vmas_sur_param_count(void) { return kSurParams; }
+
+int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
+  if (!out) return fail(VMAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_envs < 0 || max_envs > (1 << 22))
+    return fail(VMAS_EINVAL, "max_envs must be 0.." + std::to_string(1 << 22));
+  vmas_surrogate *s = new vmas_surrogate();
+  cudaGetDevice(&s->device);
+  if (cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+      s->n_sm < 1) {
+    cudaGetLastError();
+    s->n_sm = 1;
+  }
+  s->cap = max_envs;
+  const size_t R = (size_t)max_envs * sur::kAgents, RK = R * sur::kK;
+  const bool ok =
+      dalloc(&s->p32, kSurParams) && dalloc(&s->grad, kSurParams) && dalloc(&s->adam_m, kSurParams) &&
+      dalloc(&s->adam_v, kSurParams) && dalloc(&s->pbf, kSurParams) && dalloc(&s->node, R * 16) &&
+      dalloc(&s->edge, RK * 16) && dalloc(&s->he, RK * 64) && dalloc(&s->zin, R * 80) &&
+      dalloc(&s->h1, R * 128) && dalloc(&s->h2, R * 128) && dalloc(&s->mask, RK) &&
+      dalloc(&s->ze2, RK * 64) && dalloc(&s->out, R * 8) &&
+      dalloc(&s->part, (size_t)kSplitCap * 128 * 128) && dalloc(&s->loss_part, R * 8 / 256 + 1) &&
+      dalloc(&s->list, (size_t)max_envs) && dalloc(&s->list_len, 1);
+  if (!ok) {
+    cudaGetLastError();
+    free_sur(s);
+    return fail(VMAS_ENOMEM, "cudaMalloc failed while creating the surrogate");
+  }
+  cudaError_t e = cudaMemset(s->p32, 0, kSurParams * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->pbf, 0, kSurParams * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, kSurParams * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, kSurParams * sizeof(float));
+  if (e != cudaSuccess) {
+    free_sur(s);
+    return cuda_fail(e, "surrogate init");
+  }
+  *out = s;
+  return VMAS_OK;
+}
+
+int vmas_sur_destroy(vmas_surrogate *s) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  free_sur(s);
+  return VMAS_OK;
+}
+
+int vmas_sur_set_params(vmas_surrogate *s, const float *h_params) {
+  if (!s || !h_params) return fail(VMAS_EINVAL, "surrogate or h_params is NULL");
+  for (int q = 0; q < kSurParams; ++q)
+    if (!std::isfinite(h_params[q])) return fail(VMAS_EINVAL, "a parameter is not finite");
+  VMAS_CUDA(cudaMemcpy(s->p32, h_params, kSurParams * sizeof(float), cudaMemcpyHostToDevice));
+  f32_to_bf16_kernel<<<blocks_for(kSurParams, 256), 256>>>(s->p32, s->pbf, kSurParams);
+  VMAS_CUDA(cudaGetLastError());
+  VMAS_CUDA(cudaMemset(s->adam_m, 0, kSurParams * sizeof(float)));
+  VMAS_CUDA(cudaMemset(s->adam_v, 0, kSurParams * sizeof(float)));
+  VMAS_CUDA(cudaDeviceSynchronize());
+  s->adam_t = 0;
+  return VMAS_OK;
+}
+
+int vmas_sur_get_params(vmas_surrogate *s, float *h_params) {
+  if (!s || !h_params) return fail(VMAS_EINVAL, "surrogate or h_params is NULL");
+  VMAS_CUDA(cudaDeviceSynchronize());
+  VMAS_CUDA(cudaMemcpy(h_params, s->p32, kSurParams * sizeof(float), cudaMemcpyDeviceToHost));
+  return VMAS_OK;
+}
+
+int vmas_sur_set_mode(vmas_surrogate *s, int32_t mode) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  if (mode != VMAS_SUR_FUSED && mode != VMAS_SUR_LAYERED) return fail(VMAS_EINVAL, "unknown mode");
+  s->mode = mode;
+  return VMAS_OK;
+}
+
+int vmas_sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_out,
+                     void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (s->mode == VMAS_SUR_FUSED)
+    return sur_fused(s, w, d_actions, d_out ? d_out : s->out, false, 0.f, st);
+  if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
+  if (d_out && w->E)
+    VMAS_CUDA(cudaMemcpyAsync(d_out, s->out, (size_t)w->E * sur::kAgents * 8 * sizeof(float),
+                              cudaMemcpyDeviceToDevice, st));
+  return VMAS_OK;
+}
+
+int vmas_sur_loss_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
+                       const float *d_target, float *d_loss, float *d_grad, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  if (w->E > 0 && !d_target) return fail(VMAS_EINVAL, "d_target is NULL");
+  if ((rc = ensure_training(s))) return rc;
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
+  if ((rc = sur_backward(s, w->E, d_target, d_loss, st))) return rc;
+  if (d_grad)
+    VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st));
+  return VMAS_OK;
+}
+
+int vmas_sur_adam(vmas_surrogate *s, float lr, const float *d_grad, void *stream) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
+  cudaStream_t st = as_stream(stream);
+  if (d_grad && d_grad != s->grad)
+    VMAS_CUDA(cudaMemcpyAsync(s->grad, d_grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st));
+  return sur_adam(s, lr, st);
+}
+
+// Forward on the world's current state, the plain step (the world advances)
+// as the target, loss and gradient into s->grad.
+static int sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
+                          float *d_loss, cudaStream_t st) {
+  int rc = ensure_training(s);
+  if (rc) return rc;
+  const int E = w->E, R = E * sur::kAgents;
+  if (E == 0) {
+    VMAS_CUDA(cudaMemsetAsync(s->grad, 0, kSurParams * sizeof(float), st));
+    if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
+    return VMAS_OK;
+  }
+  const size_t EN = (size_t)E * w->N;
+  float *px = w->planes, *py = px + EN, *vx = px + 2 * EN, *vy = px + 3 * EN;
+  if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
+  sur::save_agents_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save);
+  VMAS_CUDA(cudaGetLastError());
+  StepParams p = make_params(w);
+  p.actions = d_actions;
+  if ((rc = launch_step(p, st))) return rc;
+  sur::targets_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save,
+                                                           s->target);
+  VMAS_CUDA(cudaGetLastError());
+  return sur_backward(s, E, s->target, d_loss, st);
+}
+
+int vmas_sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_loss,
+                        float *d_grad, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
+  if (d_grad)
+    VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st));
+  return VMAS_OK;
+}
+
+int vmas_sur_train_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float lr,
+                        float *d_loss, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
+  if (w->E == 0) return VMAS_OK;
+  return sur_adam(s, lr, st);
+}
+
+int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float limit,
+                  int32_t *d_n_fallback, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  if (!(limit >= 0) || !std::isfinite(limit)) return fail(VMAS_EINVAL, "limit must be >= 0");
+  cudaStream_t st = as_stream(stream);
+  const int E = w->E;
+  if (E == 0) {
+    if (d_n_fallback) VMAS_CUDA(cudaMemsetAsync(d_n_fallback, 0, sizeof(int32_t), st));
+    return VMAS_OK;
+  }
+  VMAS_CUDA(cudaMemsetAsync(s->list_len, 0, sizeof(int), st));
+  if (s->mode == VMAS_SUR_FUSED) {
+    if ((rc = sur_fused(s, w, d_actions, nullptr, true, limit, st))) return rc;
+  } else {
+    if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
+    sur::PredictArgs a{};
+    const size_t EN = (size_t)E * w->N;
+    a.E = E; a.N = w->N;
+    a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
+    a.param = w->param; a.out = s->out; a.limit = limit;
+    a.list = s->list; a.list_len = s->list_len;
+    sur::predict_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
+    VMAS_CUDA(cudaGetLastError());
+  }
+  // the plain step for the listed envs (grid sized for all; blocks past the
+  // device-side count return at once)
+  StepParams p = make_params(w);
+  p.actions = d_actions;
+  p.env_list = s->list;
+  p.env_count = s->list_len;
+  if ((rc = launch_step(p, st))) return rc;
+  if (d_n_fallback)
+    VMAS_CUDA(cudaMemcpyAsync(d_n_fallback, s->list_len, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return VMAS_OK;
+}
+
+int vmas_sur_debug_features(vmas_surrogate *s, vmas_world *w, const float *d_actions,
+                            uint16_t *d_node, uint16_t *d_edge, float *d_mask, void *stream) {
+  int rc = sur_check(s, w, d_actions);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
+  const size_t R = (size_t)w->E * sur::kAgents, RK = R * sur::kK;
+  if (!R) return VMAS_OK;
+  if (d_node) VMAS_CUDA(cudaMemcpyAsync(d_node, s->node, R * 16 * 2, cudaMemcpyDeviceToDevice, st));
+  if (d_edge) VMAS_CUDA(cudaMemcpyAsync(d_edge, s->edge, RK * 16 * 2, cudaMemcpyDeviceToDevice, st));
+  if (d_mask) VMAS_CUDA(cudaMemcpyAsync(d_mask, s->mask, RK * 4, cudaMemcpyDeviceToDevice, st));
+  return VMAS_OK;
+}
+
+int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N, int32_t K,
+                         const uint16_t *d_a, int32_t lda, const uint16_t *d_b, int32_t ldb,
+                         const float *d_bias, int32_t gelu, float *d_out_f32, uint16_t *d_out_bf16,
+                         int32_t splits, void *stream) {
+  if (M < 0 || N < 0 || K < 0 || splits < 1 || splits > kSplitCap)
+    return fail(VMAS_EINVAL, "bad GEMM sizes");
+  if (splits > 1 && (d_bias || d_out_bf16 || gelu))
+    return fail(VMAS_EINVAL, "split-K GEMMs take no bias, GELU or bfloat16 output");
+  if ((size_t)M * N == 0) return VMAS_OK;
+  if ((K > 0 && (!d_a || !d_b)) || (!d_out_f32 && !d_out_bf16))
+    return fail(VMAS_EINVAL, "NULL buffer");
+  if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N))
+    return fail(VMAS_EINVAL, "leading dimension too small");
+  cudaStream_t st = as_stream(stream);
+  float *part = nullptr;
+  if (splits > 1) VMAS_CUDA(cudaMalloc(&part, (size_t)splits * M * N * sizeof(float)));
+  const int rc = gemm(st, trans_a, trans_b, M, N, K, reinterpret_cast<const bf16 *>(d_a), lda,
+                      reinterpret_cast<const bf16 *>(d_b), ldb, d_bias, gelu ? 1 : 0, d_out_f32, N,
+                      reinterpret_cast<bf16 *>(d_out_bf16), N, part, splits);
+  if (part) {
+    cudaStreamSynchronize(st);
+    cudaFree(part);
+  }
+  return rc;
+}
+
+}  // extern "C"

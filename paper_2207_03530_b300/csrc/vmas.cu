@@ -2,9 +2,8 @@
 // layout, launches and error handling.  The physics lives in step_fused.cuh,
 // step.cuh and contact.cuh; the differentiable rollout in diff.cuh, LIDAR in
 // lidar.cuh, the learned surrogate in surrogate.cuh (layered GEMM path,
-// training) and surrogate_fused.cuh (fused inference).  Sections below: the
-// world, the allocation-free step, the differentiable rollout and LIDAR, the
-// packed ragged worlds, the surrogate.
+// training) and surrogate_fused.cuh (fused inference).  This file: the world,
+// the allocation-free step, the differentiable rollout and LIDAR.
 //
 // Device layout of a world (all library-owned, allocated once at create):
 //   state   6 FP32 planes px, py, vx, vy, th, om, each [E * N], env-major
@@ -18,54 +17,17 @@
 //   act     FP32 [E * A * 3] staging for host actions;
 //   stage   FP32 [E * N * 6] staging for host state transfers (lazy);
 //   h_act / h_stage  two of each, for host-streaming rollouts (lazy).
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cmath>
-#include <mutex>
-#include <cstdint>
-#include <cstdio>
-#include <cstring>
-#include <string>
-#include <vector>
-
+//
+// The packed ragged worlds live in ragged.cu, the surrogate's host side in
+// surrogate_host.cu; host.h holds what the three share.
 #include "diff.cuh"
+#include "host.h"
 #include "lidar.cuh"
 #include "step_fused.cuh"
-#include "vmas.h"
 
 static_assert(vmas::kStatCount == VMAS_STATS_COUNT, "stats layout");
 
-using vmas::StepParams;
-
-struct vmas_world {
-  int device = 0;
-  int E = 0, N = 0, A = 0, S = 0, P = 0;
-  float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0;
-  float skin = 0;  // candidate-list margin
-  bool diff_ok = false;  // every entity a sphere, N <= 32 (differentiable rollout)
-  bool sur_ok = false;   // 16 actuated agent spheres then 4 fixed walls (surrogate)
-  bool stage_timeout_test = false;  // vmas_debug_stage_timeout
-  int tile = 1;          // world steps per launch in vmas_rollout
-  float *planes = nullptr;  // 6 * E * N
-  float4 *param = nullptr;
-  unsigned long long *stats = nullptr;  // optional step counters
-  uint8_t *kind = nullptr;
-  uint16_t *pairs = nullptr;
-  int *err = nullptr;
-  float *act = nullptr;
-  float *stage = nullptr;
-  uint8_t *env_mask = nullptr;
-  std::vector<int32_t> pi, pj;
-  // host-streaming rollouts (lazy): double-buffered device actions and
-  // state staging, an upload and a download stream, and their events
-  float *h_act[2] = {nullptr, nullptr};
-  float *h_stage[2] = {nullptr, nullptr};
-  cudaStream_t s_up = nullptr, s_down = nullptr;
-  cudaEvent_t ev_up[2] = {}, ev_used[2] = {}, ev_gathered[2] = {}, ev_down[2] = {};
-};
-
-namespace {
+namespace vmas_host {
 
 thread_local std::string g_last_error;
 
@@ -77,14 +39,6 @@ int fail(int code, const std::string &msg) {
 int cuda_fail(cudaError_t e, const char *what) {
   return fail(VMAS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define VMAS_CUDA(call)                          \
-  do {                                           \
-    cudaError_t e_ = (call);                     \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 void free_world(vmas_world *w) {
   if (!w) return;
@@ -225,7 +179,7 @@ bool bulk_staging_ok(const StepParams &p) {
   return stage <= (size_t)CE * vmas::fused_env_bytes(p.N, G);
 }
 
-int launch_step(const StepParams &p0, cudaStream_t st, bool tiled = false) {
+int launch_step(const StepParams &p0, cudaStream_t st, bool tiled) {
   if (p0.E == 0) return VMAS_OK;
   StepParams p = p0;
   p.bulk = !tiled && !p.env_list && bulk_staging_ok(p) ? 1 : 0;
@@ -364,7 +318,9 @@ int launch_raw_g(const StepParams &p, cudaStream_t st) {
   }
 }
 
-}  // namespace
+}  // namespace vmas_host
+
+using namespace vmas_host;
 
 extern "C" {
 
@@ -988,1033 +944,6 @@ int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void
 int vmas_check(vmas_world *w, void *stream, int32_t *bits) {
   if (!w) return fail(VMAS_EINVAL, "world is NULL");
   return read_err(w, as_stream(stream), bits);
-}
-
-}  // extern "C"
-
-// ============================================================================
-// Packed ragged worlds: environments with different entity counts.
-//
-// Entities of all envs are packed without padding.  Envs are sorted into size
-// classes of capacity 8, 16, 32, 64, 128 entities (smallest class that holds
-// the env); each class is stepped by the fused kernel compiled for its (lanes
-// per env, entities per lane) choice, which the autotuner picks by timing, as
-// it picks the number of world steps per launch of a rollout.  Rollouts are
-// captured into a CUDA graph (one node per class per tile of steps) and
-// replayed.
-// ============================================================================
-
-struct vmas_ragged {
-  static constexpr int kClasses = 5;
-  int device = 0;
-  int E = 0, S = 0;
-  size_t total = 0, total_act = 0;
-  float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0, skin = 0;
-  int cap[kClasses] = {8, 16, 32, 64, 128};
-  int cls_begin[kClasses + 1] = {};  // sorted env ranges per class
-  int lanes[kClasses] = {};          // chosen lanes per env
-  int slots[kClasses] = {};          // chosen entities per lane
-  int tile = 1;                      // steps per launch in rollouts
-  float *planes = nullptr;           // 6 planes x total, sorted order
-  float4 *param = nullptr;
-  uint8_t *kind = nullptr;
-  uint16_t *pairs[kClasses] = {};    // canonical pair table per class capacity
-  int *soff = nullptr, *perm = nullptr, *aoff = nullptr;
-  int *to_sorted = nullptr;          // caller entity index -> sorted entity index
-  int *err = nullptr;
-  float *stage = nullptr;            // [total][6]
-  float *backup = nullptr;           // autotuner's copy of the planes
-  std::vector<int> h_aoff;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const float *graph_actions = nullptr;
-  int graph_T = -1, graph_version = -1;
-  int version = 0;                   // bumps whenever the tuning changes
-};
-
-namespace {
-
-void free_ragged(vmas_ragged *r) {
-  if (!r) return;
-  if (r->gexec) cudaGraphExecDestroy(r->gexec);
-  if (r->graph) cudaGraphDestroy(r->graph);
-  cudaFree(r->planes);
-  cudaFree(r->param);
-  cudaFree(r->kind);
-  for (auto *q : r->pairs) cudaFree(q);
-  cudaFree(r->soff);
-  cudaFree(r->perm);
-  cudaFree(r->aoff);
-  cudaFree(r->to_sorted);
-  cudaFree(r->err);
-  cudaFree(r->stage);
-  cudaFree(r->backup);
-  delete r;
-}
-
-StepParams ragged_params(const vmas_ragged *r, int c) {
-  StepParams p{};
-  p.E = r->E;
-  p.N = r->cap[c];
-  p.P = r->cap[c] * (r->cap[c] - 1) / 2;
-  p.A = 0;
-  p.S = r->S;
-  p.h = (float)((double)r->dt / (double)r->S);
-  p.damp = (float)(1.0 - (double)r->drag);
-  p.gx = r->gx;
-  p.gy = r->gy;
-  p.ck = (float)((double)r->c * (double)r->k);
-  p.inv_k = (float)(1.0 / (double)r->k);
-  p.vmax = r->vmax;
-  p.skin = r->skin;
-  const size_t T = r->total;
-  p.px = r->planes;
-  p.py = r->planes + T;
-  p.vx = r->planes + 2 * T;
-  p.vy = r->planes + 3 * T;
-  p.th = r->planes + 4 * T;
-  p.om = r->planes + 5 * T;
-  p.param = r->param;
-  p.kind = r->kind;
-  p.pairs = r->pairs[c];
-  p.err = r->err;
-  p.tile = 1;
-  p.act_step = r->total_act * 3;
-  p.EN = T;
-  p.soff = r->soff;
-  p.perm = r->perm;
-  p.aoff = r->aoff;
-  p.env_begin = r->cls_begin[c];
-  p.env_end = r->cls_begin[c + 1];
-  return p;
-}
-
-// One tile of `tile` steps for every class, actions of the tile's first step
-// at d_actions.
-int ragged_launch_tile(vmas_ragged *r, const float *d_actions, int tile, cudaStream_t st) {
-  for (int c = 0; c < vmas_ragged::kClasses; ++c) {
-    const int n = r->cls_begin[c + 1] - r->cls_begin[c];
-    if (n == 0) continue;
-    StepParams p = ragged_params(r, c);
-    p.actions = d_actions;
-    p.tile = tile;
-    const int rc = launch_ragged_class(p, r->lanes[c], r->slots[c], n, st);
-    if (rc) return rc;
-  }
-  return VMAS_OK;
-}
-
-__global__ void ragged_gather_kernel(float *aos, const float *planes, const int *to_sorted,
-                                     size_t total) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const size_t s = (size_t)to_sorted[t];
-  for (int f = 0; f < 6; ++f) aos[t * 6 + f] = planes[f * total + s];
-}
-
-__global__ void ragged_scatter_kernel(float *planes, const float *aos, const int *to_sorted,
-                                      size_t total) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const size_t s = (size_t)to_sorted[t];
-  for (int f = 0; f < 6; ++f) planes[f * total + s] = aos[t * 6 + f];
-}
-
-}  // namespace
-
-extern "C" {
-
-int vmas_ragged_create(const vmas_ragged_desc *d, vmas_ragged **out) {
-  if (!out) return fail(VMAS_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!d || !d->env_offsets) return fail(VMAS_EINVAL, "desc or env_offsets is NULL");
-  if (d->n_envs < 0 || d->substeps < 1) return fail(VMAS_EINVAL, "n_envs >= 0 and substeps >= 1");
-  if (!(d->dt > 0) || !(d->contact_margin > 0) || !(d->contact_force >= 0) || !(d->max_speed >= 0))
-    return fail(VMAS_EINVAL, "dt, contact_margin must be > 0; contact_force, max_speed >= 0");
-  const int E = d->n_envs;
-  if (d->env_offsets[0] != 0) return fail(VMAS_EINVAL, "env_offsets[0] must be 0");
-  std::vector<int> cnt(E), cls(E);
-  for (int e = 0; e < E; ++e) {
-    cnt[e] = d->env_offsets[e + 1] - d->env_offsets[e];
-    if (cnt[e] < 1 || cnt[e] > VMAS_MAX_ENTITIES)
-      return fail(VMAS_EINVAL, "env " + std::to_string(e) + " has " + std::to_string(cnt[e]) +
-                                   " entities (1.." + std::to_string(VMAS_MAX_ENTITIES) + " allowed)");
-  }
-  const size_t total = E ? (size_t)d->env_offsets[E] : 0;
-  if (total && (!d->shape || !d->flags || !d->size_a || !d->size_b || !d->mass || !d->inertia ||
-                !d->init_state))
-    return fail(VMAS_EINVAL, "a per-entity array is NULL");
-  vmas_ragged *r = new vmas_ragged();
-  cudaGetDevice(&r->device);
-  r->E = E;
-  r->S = d->substeps;
-  r->total = total;
-  r->dt = d->dt;
-  r->drag = d->drag;
-  r->gx = d->gx;
-  r->gy = d->gy;
-  r->c = d->contact_force;
-  r->k = d->contact_margin;
-  r->vmax = d->max_speed;
-  // classes, sorted order (stable by class)
-  for (int e = 0; e < E; ++e) {
-    int c = 0;
-    while (r->cap[c] < cnt[e]) ++c;
-    cls[e] = c;
-  }
-  std::vector<int> perm;
-  for (int c = 0; c < vmas_ragged::kClasses; ++c) {
-    r->cls_begin[c] = (int)perm.size();
-    for (int e = 0; e < E; ++e)
-      if (cls[e] == c) perm.push_back(e);
-    // default: fewest lanes that keep 4 entities or fewer per lane
-    r->lanes[c] = std::max(4, r->cap[c] / 4);
-    r->slots[c] = r->cap[c] / r->lanes[c];
-  }
-  r->cls_begin[vmas_ragged::kClasses] = (int)perm.size();
-  // packed parameters in sorted order; action offsets in caller order
-  std::vector<int> soff(E + 1, 0), to_sorted(total);
-  r->h_aoff.assign(E + 1, 0);
-  std::vector<float4> param(total);
-  std::vector<uint8_t> kind(total);
-  std::vector<float> planes(total * 6);
-  std::vector<float> bound;
-  for (int e = 0; e < E; ++e) {
-    int na = 0;
-    for (int i = d->env_offsets[e]; i < d->env_offsets[e + 1]; ++i)
-      if (d->flags[i] & VMAS_ACTUATED) ++na;
-    r->h_aoff[e + 1] = r->h_aoff[e] + na;
-  }
-  r->total_act = (size_t)r->h_aoff[E];
-  size_t pos = 0;
-  for (int s = 0; s < E; ++s) {
-    const int e = perm[s];
-    soff[s] = (int)pos;
-    for (int i = d->env_offsets[e]; i < d->env_offsets[e + 1]; ++i, ++pos) {
-      const int sh = d->shape[i], fl = d->flags[i];
-      const double a = d->size_a[i], b = d->size_b[i], m = d->mass[i];
-      if (sh > 2 || (fl & ~15) || !(a > 0) || (sh == VMAS_BOX && !(b > 0)) ||
-          ((fl & VMAS_MOVABLE) && !(m > 0))) {
-        free_ragged(r);
-        return fail(VMAS_EINVAL, "invalid entity " + std::to_string(i));
-      }
-      double I = d->inertia[i];
-      if (I == 0)
-        I = sh == VMAS_BOX ? m * (a * a + b * b) / 12.0 : (sh == VMAS_LINE ? m * a * a / 12.0 : 0.5 * m * a * a);
-      if ((fl & VMAS_ROTATABLE) && !(I > 0)) {
-        free_ragged(r);
-        return fail(VMAS_EINVAL, "rotatable entity needs inertia > 0 at " + std::to_string(i));
-      }
-      const double ha = sh == VMAS_SPHERE ? a : 0.5 * a, hb = sh == VMAS_BOX ? 0.5 * b : 0.0;
-      param[pos] = make_float4((fl & VMAS_MOVABLE) ? (float)(1.0 / m) : 0.f,
-                               (fl & VMAS_ROTATABLE) ? (float)(1.0 / I) : 0.f, (float)ha, (float)hb);
-      kind[pos] = (uint8_t)(sh | (fl << 2));
-      to_sorted[i] = (int)pos;
-      for (int f = 0; f < 6; ++f) planes[f * total + pos] = d->init_state[(size_t)i * 6 + f];
-      if (fl & VMAS_MOVABLE) bound.push_back((float)std::sqrt(ha * ha + hb * hb));
-    }
-  }
-  soff[E] = (int)pos;
-  float med = 0.05f;
-  if (!bound.empty()) {
-    std::nth_element(bound.begin(), bound.begin() + bound.size() / 2, bound.end());
-    med = bound[bound.size() / 2];
-  }
-  r->skin = 0.5f * med;
-  auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
-    if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) return false;
-    return !bytes || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
-  };
-  bool ok = up((void **)&r->planes, planes.data(), planes.size() * sizeof(float)) &&
-            up((void **)&r->param, param.data(), param.size() * sizeof(float4)) &&
-            up((void **)&r->kind, kind.data(), kind.size()) &&
-            up((void **)&r->soff, soff.data(), soff.size() * sizeof(int)) &&
-            up((void **)&r->perm, perm.data(), perm.size() * sizeof(int)) &&
-            up((void **)&r->aoff, r->h_aoff.data(), r->h_aoff.size() * sizeof(int)) &&
-            up((void **)&r->to_sorted, to_sorted.data(), to_sorted.size() * sizeof(int)) &&
-            cudaMalloc((void **)&r->err, 4 * sizeof(int)) == cudaSuccess &&
-            cudaMemset(r->err, 0, 4 * sizeof(int)) == cudaSuccess;
-  for (int c = 0; c < vmas_ragged::kClasses && ok; ++c) {
-    std::vector<uint16_t> pt;
-    for (int i = 0; i < r->cap[c]; ++i)
-      for (int j = i + 1; j < r->cap[c]; ++j) pt.push_back((uint16_t)(i | (j << 8)));
-    ok = up((void **)&r->pairs[c], pt.data(), pt.size() * sizeof(uint16_t));
-  }
-  if (!ok) {
-    cudaGetLastError();
-    free_ragged(r);
-    return fail(VMAS_ENOMEM, "allocation or upload failed while creating the ragged world");
-  }
-  *out = r;
-  return VMAS_OK;
-}
-
-int vmas_ragged_destroy(vmas_ragged *r) {
-  if (!r) return VMAS_OK;
-  cudaDeviceSynchronize();
-  free_ragged(r);
-  return VMAS_OK;
-}
-
-int vmas_ragged_info(const vmas_ragged *r, int32_t *n_envs, int64_t *n_entities,
-                     int64_t *n_action_rows, int32_t *class_envs) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (n_envs) *n_envs = r->E;
-  if (n_entities) *n_entities = (int64_t)r->total;
-  if (n_action_rows) *n_action_rows = (int64_t)r->total_act;
-  if (class_envs)
-    for (int c = 0; c < vmas_ragged::kClasses; ++c) class_envs[c] = r->cls_begin[c + 1] - r->cls_begin[c];
-  return VMAS_OK;
-}
-
-int vmas_ragged_action_offsets(const vmas_ragged *r, int32_t *out) {
-  if (!r || !out) return fail(VMAS_EINVAL, "NULL argument");
-  std::memcpy(out, r->h_aoff.data(), r->h_aoff.size() * sizeof(int32_t));
-  return VMAS_OK;
-}
-
-int vmas_ragged_step(vmas_ragged *r, const float *d_actions, void *stream) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (r->total_act && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
-  return ragged_launch_tile(r, d_actions, 1, as_stream(stream));
-}
-
-int vmas_ragged_rollout(vmas_ragged *r, const float *d_actions, int32_t n_steps, void *stream) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (n_steps < 0) return fail(VMAS_EINVAL, "n_steps < 0");
-  if (n_steps == 0 || r->E == 0) return VMAS_OK;
-  if (r->total_act && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
-  cudaStream_t st = as_stream(stream);
-  if (!(r->gexec && r->graph_actions == d_actions && r->graph_T == n_steps &&
-        r->graph_version == r->version)) {
-    if (r->gexec) cudaGraphExecDestroy(r->gexec);
-    if (r->graph) cudaGraphDestroy(r->graph);
-    r->gexec = nullptr;
-    r->graph = nullptr;
-    // The size classes touch disjoint envs, so each class's chain of tiles
-    // is its own branch of the graph (forked from and joined back into the
-    // capture stream): a class with few, slow envs no longer holds the GPU
-    // while the others wait.
-    constexpr int C = vmas_ragged::kClasses;
-    cudaStream_t cap = nullptr, cs[C] = {};
-    cudaEvent_t fork = nullptr, join[C] = {};
-    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    for (int c = 0; c < C && e == cudaSuccess; ++c) {
-      e = cudaStreamCreateWithFlags(&cs[c], cudaStreamNonBlocking);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[c], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    int rc = VMAS_OK;
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      e = cudaEventRecord(fork, cap);
-      for (int c = 0; c < C && e == cudaSuccess; ++c) {
-        const int n = r->cls_begin[c + 1] - r->cls_begin[c];
-        e = cudaStreamWaitEvent(cs[c], fork, 0);
-        for (int t = 0; n > 0 && t < n_steps && rc == VMAS_OK && e == cudaSuccess; t += r->tile) {
-          StepParams p = ragged_params(r, c);
-          p.actions = d_actions + (size_t)t * r->total_act * 3;
-          p.tile = std::min(r->tile, n_steps - t);
-          rc = launch_ragged_class(p, r->lanes[c], r->slots[c], n, cs[c]);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(join[c], cs[c]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[c], 0);
-      }
-      cudaError_t e2 = cudaStreamEndCapture(cap, &r->graph);
-      if (e == cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess && rc == VMAS_OK) e = cudaGraphInstantiate(&r->gexec, r->graph, 0);
-    for (int c = 0; c < C; ++c) {
-      if (join[c]) cudaEventDestroy(join[c]);
-      if (cs[c]) cudaStreamDestroy(cs[c]);
-    }
-    if (fork) cudaEventDestroy(fork);
-    if (cap) cudaStreamDestroy(cap);
-    if (rc) {
-      cudaGetLastError();
-      return rc;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "rollout graph capture");
-    r->graph_actions = d_actions;
-    r->graph_T = n_steps;
-    r->graph_version = r->version;
-  }
-  VMAS_CUDA(cudaGraphLaunch(r->gexec, st));
-  return VMAS_OK;
-}
-
-int vmas_ragged_state(vmas_ragged *r, float *out, int32_t out_is_device, void *stream) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (!r->total) return VMAS_OK;
-  if (!out) return fail(VMAS_EINVAL, "out is NULL");
-  cudaStream_t st = as_stream(stream);
-  float *dst = out;
-  if (!out_is_device) {
-    if (!r->stage) VMAS_CUDA(cudaMalloc(&r->stage, r->total * 6 * sizeof(float)));
-    dst = r->stage;
-  }
-  ragged_gather_kernel<<<(unsigned)((r->total + 255) / 256), 256, 0, st>>>(dst, r->planes,
-                                                                          r->to_sorted, r->total);
-  VMAS_CUDA(cudaGetLastError());
-  if (!out_is_device) {
-    VMAS_CUDA(cudaMemcpyAsync(out, r->stage, r->total * 6 * sizeof(float), cudaMemcpyDeviceToHost, st));
-    int h = 0;
-    VMAS_CUDA(cudaMemcpyAsync(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VMAS_CUDA(cudaStreamSynchronize(st));
-    if (h) {
-      cudaMemset(r->err, 0, sizeof(int));
-      return fail(VMAS_EDEVICE, "device error word set (bits " + std::to_string(h) + ")");
-    }
-  }
-  return VMAS_OK;
-}
-
-int vmas_ragged_set_state(vmas_ragged *r, const float *d_state, void *stream) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (!r->total) return VMAS_OK;
-  if (!d_state) return fail(VMAS_EINVAL, "d_state is NULL");
-  ragged_scatter_kernel<<<(unsigned)((r->total + 255) / 256), 256, 0, as_stream(stream)>>>(
-      r->planes, d_state, r->to_sorted, r->total);
-  VMAS_CUDA(cudaGetLastError());
-  return VMAS_OK;
-}
-
-int vmas_ragged_set_tuning(vmas_ragged *r, const int32_t *lanes, int32_t steps_per_launch) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (steps_per_launch < 1 || steps_per_launch > 1024)
-    return fail(VMAS_EINVAL, "steps_per_launch must be 1..1024");
-  if (lanes) {
-    for (int c = 0; c < vmas_ragged::kClasses; ++c) {
-      const int g = lanes[c], sl = r->cap[c] / g;
-      const bool ok = (g == 4 || g == 8 || g == 16 || g == 32) && g * sl == r->cap[c] && sl >= 1 &&
-                      sl <= 4 && sl != 3;
-      if (!ok) return fail(VMAS_EINVAL, "lanes for class " + std::to_string(c) + " invalid");
-    }
-    for (int c = 0; c < vmas_ragged::kClasses; ++c) {
-      r->lanes[c] = lanes[c];
-      r->slots[c] = r->cap[c] / lanes[c];
-    }
-  }
-  r->tile = steps_per_launch;
-  ++r->version;
-  return VMAS_OK;
-}
-
-int vmas_ragged_get_tuning(const vmas_ragged *r, int32_t *lanes, int32_t *steps_per_launch) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (lanes)
-    for (int c = 0; c < vmas_ragged::kClasses; ++c) lanes[c] = r->lanes[c];
-  if (steps_per_launch) *steps_per_launch = r->tile;
-  return VMAS_OK;
-}
-
-int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps, void *stream) {
-  if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (n_steps < 1) return fail(VMAS_EINVAL, "n_steps must be >= 1");
-  if (r->total_act && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
-  cudaStream_t st = as_stream(stream);
-  const size_t bytes = r->total * 6 * sizeof(float);
-  if (!r->backup) VMAS_CUDA(cudaMalloc(&r->backup, bytes ? bytes : 16));
-  VMAS_CUDA(cudaMemcpyAsync(r->backup, r->planes, bytes, cudaMemcpyDeviceToDevice, st));
-  cudaEvent_t a, b;
-  VMAS_CUDA(cudaEventCreate(&a));
-  VMAS_CUDA(cudaEventCreate(&b));
-  const int tiles[] = {1, 2, 4, 8, 16};
-  int rc = VMAS_OK;
-  for (int c = 0; c < vmas_ragged::kClasses && rc == VMAS_OK; ++c) {
-    const int n = r->cls_begin[c + 1] - r->cls_begin[c];
-    if (n == 0) continue;
-    float best = 3.4e38f;
-    int best_g = r->lanes[c];
-    for (int g = 4; g <= 32 && rc == VMAS_OK; g *= 2) {
-      const int sl = r->cap[c] / g;
-      if (sl < 1 || sl > 4 || sl == 3 || g * sl != r->cap[c]) continue;
-      StepParams p = ragged_params(r, c);
-      float ms = 0;
-      for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {  // first pass warms up
-        cudaEventRecord(a, st);
-        for (int t = 0; t < n_steps && rc == VMAS_OK; ++t) {
-          p.actions = d_actions + (size_t)t * r->total_act * 3;
-          rc = launch_ragged_class(p, g, sl, n, st);
-        }
-        cudaEventRecord(b, st);
-        cudaEventSynchronize(b);
-        cudaEventElapsedTime(&ms, a, b);
-      }
-      if (ms < best) { best = ms; best_g = g; }
-    }
-    r->lanes[c] = best_g;
-    r->slots[c] = r->cap[c] / best_g;
-  }
-  // steps per launch, all classes together
-  float best = 3.4e38f;
-  int best_tile = 1;
-  for (int ti = 0; ti < 5 && rc == VMAS_OK; ++ti) {
-    const int tile = tiles[ti];
-    if (tile > n_steps) break;
-    float ms = 0;
-    for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {
-      cudaEventRecord(a, st);
-      for (int t = 0; t + tile <= n_steps && rc == VMAS_OK; t += tile)
-        rc = ragged_launch_tile(r, d_actions + (size_t)t * r->total_act * 3, tile, st);
-      cudaEventRecord(b, st);
-      cudaEventSynchronize(b);
-      cudaEventElapsedTime(&ms, a, b);
-    }
-    const float per_step = ms / (float)((n_steps / tile) * tile);
-    if (per_step < best) { best = per_step; best_tile = tile; }
-  }
-  r->tile = best_tile;
-  ++r->version;
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  cudaError_t e = cudaMemcpyAsync(r->planes, r->backup, bytes, cudaMemcpyDeviceToDevice, st);
-  if (rc == VMAS_OK && e != cudaSuccess) rc = cuda_fail(e, "restore after autotune");
-  if (rc == VMAS_OK) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
-  }
-  return rc;
-}
-
-}  // extern "C"
-
-// ------------------------------------------------------------------------
-// Learned surrogate (surrogate.cuh): a per-agent message-passing network
-// that predicts a whole world step of the 16-agent walled sphere world, with
-// the plain step as the fallback for envs whose prediction overlaps.
-
-#include "surrogate_fused.cuh"
-
-namespace {
-
-using vmas::sur::bf16;
-namespace sur = vmas::sur;
-
-using namespace vmas::sur;  // parameter offsets kOff*
-constexpr int kSurParams = vmas::sur::kParams;
-constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
-
-}  // namespace
-
-struct vmas_surrogate {
-  int device = 0;
-  int cap = 0;  // envs
-  int mode = VMAS_SUR_FUSED;
-  int n_sm = 0;
-  bool fused_ready = false;  // shared-memory opt-in of the fused kernel done
-  int adam_t = 0;
-  float *p32 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
-  bf16 *pbf = nullptr;
-  // forward
-  bf16 *node = nullptr, *edge = nullptr, *he = nullptr, *zin = nullptr, *h1 = nullptr,
-       *h2 = nullptr;
-  float *mask = nullptr, *ze2 = nullptr, *out = nullptr;
-  // training (allocated on first use)
-  float *ze1 = nullptr, *z1 = nullptr, *z2 = nullptr;
-  float *d_out = nullptr, *g128 = nullptr, *d_zin = nullptr, *ge = nullptr;
-  bf16 *d_outbf = nullptr, *g128bf = nullptr, *gebf = nullptr;
-  float *part = nullptr, *loss_part = nullptr, *save = nullptr, *target = nullptr;
-  int *list = nullptr, *list_len = nullptr;
-};
-
-namespace {
-
-void free_sur(vmas_surrogate *s) {
-  if (!s) return;
-  void *ptrs[] = {s->p32,   s->grad,  s->adam_m, s->adam_v, s->pbf,    s->node,   s->edge,
-                  s->he,    s->zin,   s->h1,     s->h2,     s->mask,   s->ze2,    s->out,
-                  s->ze1,   s->z1,    s->z2,     s->d_out,  s->g128,   s->d_zin,  s->ge,
-                  s->d_outbf, s->g128bf, s->gebf, s->part,  s->loss_part, s->save, s->target,
-                  s->list,  s->list_len};
-  for (void *q : ptrs) cudaFree(q);
-  delete s;
-}
-
-template <typename T>
-bool dalloc(T **ptr, size_t count) {
-  return cudaMalloc((void **)ptr, (count > 0 ? count : 1) * sizeof(T)) == cudaSuccess;
-}
-
-int ensure_training(vmas_surrogate *s) {
-  if (s->ze1) return VMAS_OK;
-  const size_t R = (size_t)s->cap * sur::kAgents, RK = R * sur::kK;
-  const bool ok = dalloc(&s->ze1, RK * 64) && dalloc(&s->z1, R * 128) && dalloc(&s->z2, R * 128) &&
-                  dalloc(&s->d_out, R * 8) && dalloc(&s->d_outbf, R * 8) &&
-                  dalloc(&s->g128, R * 128) && dalloc(&s->g128bf, R * 128) &&
-                  dalloc(&s->d_zin, R * 80) && dalloc(&s->ge, RK * 64) &&
-                  dalloc(&s->gebf, RK * 64) && dalloc(&s->save, R * 4) &&
-                  dalloc(&s->target, R * 4);
-  if (!ok) {
-    cudaGetLastError();
-    return fail(VMAS_ENOMEM, "cudaMalloc failed for the surrogate's training buffers");
-  }
-  return VMAS_OK;
-}
-
-unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
-
-// C = A B (+ bias, GELU) through gemm_bf16_kernel; `splits` > 1 sums K in
-// chunks into part, reduced into out_f32 (then no bias / bf16 output).
-int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, int lda,
-         const bf16 *B, int ldb, const float *bias, int act, float *out_f32, int ldc_f,
-         bf16 *out_bf, int ldc_b, float *part = nullptr, int splits = 1) {
-  if (M == 0 || N == 0) return VMAS_OK;
-  sur::GemmArgs g{};
-  g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
-  g.bias = bias; g.act = act;
-  g.ldc_f = ldc_f; g.out_bf = out_bf; g.ldc_b = ldc_b;
-  if (splits > 1 && K > 0) {
-    int chunk = (K + splits - 1) / splits;
-    chunk = (chunk + sur::kBK - 1) / sur::kBK * sur::kBK;
-    splits = (K + chunk - 1) / chunk;
-    g.kchunk = chunk;
-    g.out_f32 = part;
-    g.ldc_f = N;
-  } else {
-    splits = 1;
-    g.kchunk = K > 0 ? K : 1;
-    g.out_f32 = out_f32;
-  }
-  const dim3 grid(blocks_for((size_t)M, sur::kBM), blocks_for((size_t)N, sur::kBN), splits);
-  if (!ta && !tb) sur::gemm_bf16_kernel<false, false><<<grid, 128, 0, st>>>(g);
-  else if (!ta && tb) sur::gemm_bf16_kernel<false, true><<<grid, 128, 0, st>>>(g);
-  else if (ta && !tb) sur::gemm_bf16_kernel<true, false><<<grid, 128, 0, st>>>(g);
-  else sur::gemm_bf16_kernel<true, true><<<grid, 128, 0, st>>>(g);
-  VMAS_CUDA(cudaGetLastError());
-  if (g.out_f32 == part && part) {
-    const size_t MN = (size_t)M * N;
-    sur::sum_partials_kernel<<<blocks_for(MN, 256), 256, 0, st>>>(out_f32, part, splits, MN);
-    VMAS_CUDA(cudaGetLastError());
-  }
-  return VMAS_OK;
-}
-
-// Column sums of x [M][N] (N <= 128) into out [N]: up to 4,096 row chunks
-// summed in parallel, then the chunk sums per column (two stages).
-int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *part) {
-  const int chunks = std::max(1, std::min(4096, (M + 255) / 256));
-  const int chunk = (M + chunks - 1) / chunks;
-  sur::col_sum_kernel<<<chunks, 128, 0, st>>>(part, x, M, N, chunk > 0 ? chunk : 1);
-  VMAS_CUDA(cudaGetLastError());
-  // second stage: 64 groups of chunks, then the groups
-  const int groups = std::min(64, chunks), per = (chunks + groups - 1) / groups;
-  float *part2 = part + (size_t)chunks * N;
-  sur::col_sum_kernel<<<groups, 128, 0, st>>>(part2, part, chunks, N, per);
-  VMAS_CUDA(cudaGetLastError());
-  sur::sum_partials_kernel<<<1, 128, 0, st>>>(out, part2, groups, (size_t)N);
-  VMAS_CUDA(cudaGetLastError());
-  return VMAS_OK;
-}
-
-int sur_check(vmas_surrogate *s, vmas_world *w, const float *d_actions) {
-  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
-  if (!w) return fail(VMAS_EINVAL, "world is NULL");
-  if (!w->sur_ok)
-    return fail(VMAS_EINVAL, "world layout is not 16 actuated agent spheres then 4 fixed lines");
-  if (w->E > s->cap)
-    return fail(VMAS_EINVAL, "world has " + std::to_string(w->E) + " envs, surrogate capacity " +
-                                 std::to_string(s->cap));
-  if (w->E > 0 && !d_actions) return fail(VMAS_EINVAL, "d_actions is NULL");
-  return VMAS_OK;
-}
-
-// Features of the world's current state, then the network; train = true also
-// keeps the FP32 pre-activations the backward needs.
-int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool train,
-                cudaStream_t st) {
-  const int E = w->E;
-  const int R = E * sur::kAgents, RK = R * sur::kK;
-  if (E == 0) return VMAS_OK;
-  sur::FeatureArgs f{};
-  const size_t EN = (size_t)E * w->N;
-  f.E = E; f.N = w->N; f.A = w->A;
-  f.px = w->planes; f.py = w->planes + EN; f.vx = w->planes + 2 * EN; f.vy = w->planes + 3 * EN;
-  f.param = w->param; f.actions = d_actions;
-  f.node = s->node; f.edge = s->edge; f.mask = s->mask;
-  sur::features_kernel<<<blocks_for(R, 128), 128, 0, st>>>(f);
-  VMAS_CUDA(cudaGetLastError());
-  const bf16 *W = s->pbf;
-  const float *P = s->p32;
-  int rc;
-  // edge MLP
-  if ((rc = gemm(st, false, true, RK, 64, 16, s->edge, 16, W + kOffWe1, 16, P + kOffbe1, 1,
-                 train ? s->ze1 : nullptr, 64, s->he, 64)))
-    return rc;
-  if ((rc = gemm(st, false, true, RK, 64, 64, s->he, 64, W + kOffWe2, 64, P + kOffbe2, 0, s->ze2,
-                 64, nullptr, 0)))
-    return rc;
-  sur::aggregate_kernel<<<blocks_for((size_t)R * 80, 256), 256, 0, st>>>(R, s->ze2, s->mask,
-                                                                          s->node, s->zin);
-  VMAS_CUDA(cudaGetLastError());
-  // node MLP
-  if ((rc = gemm(st, false, true, R, 128, 80, s->zin, 80, W + kOffW1, 80, P + kOffb1, 1,
-                 train ? s->z1 : nullptr, 128, s->h1, 128)))
-    return rc;
-  if ((rc = gemm(st, false, true, R, 128, 128, s->h1, 128, W + kOffW2, 128, P + kOffb2, 1,
-                 train ? s->z2 : nullptr, 128, s->h2, 128)))
-    return rc;
-  return gemm(st, false, true, R, 8, 128, s->h2, 128, W + kOffW3, 128, P + kOffb3, 0, s->out, 8,
-              nullptr, 0);
-}
-
-// Loss against target [R][4] and the gradient into s->grad (after sur_forward
-// with train = true).
-int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, cudaStream_t st) {
-  const int R = E * sur::kAgents, RK = R * sur::kK;
-  float *G = s->grad;
-  const bf16 *W = s->pbf;
-  VMAS_CUDA(cudaMemsetAsync(G, 0, kSurParams * sizeof(float), st));
-  if (E == 0) {
-    if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
-    return VMAS_OK;
-  }
-  const int lb = (int)blocks_for((size_t)R * 8, 256);
-  sur::loss_kernel<<<lb, 256, 0, st>>>(R, s->out, target, s->d_out, s->d_outbf, s->loss_part);
-  VMAS_CUDA(cudaGetLastError());
-  if (d_loss) {
-    sur::finish_loss_kernel<<<1, 256, 0, st>>>(s->loss_part, lb, R, d_loss);
-    VMAS_CUDA(cudaGetLastError());
-  }
-  int rc;
-  const int sp = kSplitCap;
-  // output layer
-  if ((rc = gemm(st, true, false, 8, 128, R, s->d_outbf, 8, s->h2, 128, nullptr, 0, G + kOffW3,
-                 128, nullptr, 0, s->part, sp)))
-    return rc;
-  if ((rc = col_sum(st, G + kOffb3, s->d_out, R, 8, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 128, 8, s->d_outbf, 8, W + kOffW3, 128, nullptr, 0, s->g128,
-                 128, nullptr, 0)))
-    return rc;
-  // node layer 2
-  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
-                                                                           s->z2, s->g128, s->g128bf);
-  VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 128, 128, R, s->g128bf, 128, s->h1, 128, nullptr, 0, G + kOffW2,
-                 128, nullptr, 0, s->part, sp)))
-    return rc;
-  if ((rc = col_sum(st, G + kOffb2, s->g128, R, 128, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 128, 128, s->g128bf, 128, W + kOffW2, 128, nullptr, 0,
-                 s->g128, 128, nullptr, 0)))
-    return rc;
-  // node layer 1
-  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
-                                                                           s->z1, s->g128, s->g128bf);
-  VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 128, 80, R, s->g128bf, 128, s->zin, 80, nullptr, 0, G + kOffW1, 80,
-                 nullptr, 0, s->part, sp)))
-    return rc;
-  if ((rc = col_sum(st, G + kOffb1, s->g128, R, 128, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 80, 128, s->g128bf, 128, W + kOffW1, 80, nullptr, 0, s->d_zin,
-                 80, nullptr, 0)))
-    return rc;
-  // edge layer 2 (through the masked sum)
-  sur::edge_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>(R, s->d_zin, s->mask,
-                                                                           s->ze2, s->ge, s->gebf);
-  VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 64, 64, RK, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
-                 nullptr, 0, s->part, sp)))
-    return rc;
-  if ((rc = col_sum(st, G + kOffbe2, s->ge, RK, 64, s->part))) return rc;
-  if ((rc = gemm(st, false, false, RK, 64, 64, s->gebf, 64, W + kOffWe2, 64, nullptr, 0, s->ge, 64,
-                 nullptr, 0)))
-    return rc;
-  // edge layer 1
-  sur::gelu_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>((size_t)RK * 64, s->ge,
-                                                                          s->ze1, s->ge, s->gebf);
-  VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 64, 16, RK, s->gebf, 64, s->edge, 16, nullptr, 0, G + kOffWe1, 16,
-                 nullptr, 0, s->part, sp)))
-    return rc;
-  return col_sum(st, G + kOffbe1, s->ge, RK, 64, s->part);
-}
-
-int sur_adam(vmas_surrogate *s, float lr, cudaStream_t st) {
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  ++s->adam_t;
-  const float c1 = (float)(1.0 - std::pow((double)b1, s->adam_t));
-  const float c2 = (float)(1.0 - std::pow((double)b2, s->adam_t));
-  sur::adam_kernel<<<blocks_for(kSurParams, 256), 256, 0, st>>>(
-      kSurParams, s->p32, s->grad, s->adam_m, s->adam_v, s->pbf, lr, b1, b2, eps, c1, c2);
-  VMAS_CUDA(cudaGetLastError());
-  return VMAS_OK;
-}
-
-// The fused inference kernel over the world's envs: network output into
-// out (may be NULL); apply = true also applies the prediction and lists the
-// fallback envs.
-int sur_fused(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *out, bool apply,
-              float limit, cudaStream_t st) {
-  const int E = w->E;
-  if (E == 0) return VMAS_OK;
-  const size_t smem = sur::fused_smem_bytes();
-  if (!s->fused_ready) {  // > 48 KB of dynamic shared memory needs an opt-in
-    VMAS_CUDA(cudaFuncSetAttribute(sur::sur_fused_kernel,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    s->fused_ready = true;
-  }
-  sur::FusedArgs a{};
-  const size_t EN = (size_t)E * w->N;
-  a.E = E; a.N = w->N; a.A = w->A;
-  a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
-  a.param = w->param; a.actions = d_actions;
-  a.w = s->pbf; a.p = s->p32;
-  a.out = out; a.apply = apply ? 1 : 0; a.limit = limit;
-  a.list = s->list; a.list_len = s->list_len;
-  const int need = (E + sur::kFusedWarpsPerCta - 1) / sur::kFusedWarpsPerCta;
-  const int grid = std::max(1, std::min(need, s->n_sm));
-  sur::sur_fused_kernel<<<grid, sur::kFusedWarpsPerCta * 32, smem, st>>>(a);
-  VMAS_CUDA(cudaGetLastError());
-  return VMAS_OK;
-}
-
-__global__ void f32_to_bf16_kernel(const float *x, bf16 *y, int n) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) y[t] = __float2bfloat16_rn(x[t]);
-}
-
-}  // namespace
-
-extern "C" {
-
-int vmas_sur_param_count(void) { return kSurParams; }
-
-int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
-  if (!out) return fail(VMAS_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (max_envs < 0 || max_envs > (1 << 22))
-    return fail(VMAS_EINVAL, "max_envs must be 0.." + std::to_string(1 << 22));
-  vmas_surrogate *s = new vmas_surrogate();
-  cudaGetDevice(&s->device);
-  if (cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
-      s->n_sm < 1) {
-    cudaGetLastError();
-    s->n_sm = 1;
-  }
-  s->cap = max_envs;
-  const size_t R = (size_t)max_envs * sur::kAgents, RK = R * sur::kK;
-  const bool ok =
-      dalloc(&s->p32, kSurParams) && dalloc(&s->grad, kSurParams) && dalloc(&s->adam_m, kSurParams) &&
-      dalloc(&s->adam_v, kSurParams) && dalloc(&s->pbf, kSurParams) && dalloc(&s->node, R * 16) &&
-      dalloc(&s->edge, RK * 16) && dalloc(&s->he, RK * 64) && dalloc(&s->zin, R * 80) &&
-      dalloc(&s->h1, R * 128) && dalloc(&s->h2, R * 128) && dalloc(&s->mask, RK) &&
-      dalloc(&s->ze2, RK * 64) && dalloc(&s->out, R * 8) &&
-      dalloc(&s->part, (size_t)kSplitCap * 128 * 128) && dalloc(&s->loss_part, R * 8 / 256 + 1) &&
-      dalloc(&s->list, (size_t)max_envs) && dalloc(&s->list_len, 1);
-  if (!ok) {
-    cudaGetLastError();
-    free_sur(s);
-    return fail(VMAS_ENOMEM, "cudaMalloc failed while creating the surrogate");
-  }
-  cudaError_t e = cudaMemset(s->p32, 0, kSurParams * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->pbf, 0, kSurParams * sizeof(bf16));
-  if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, kSurParams * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, kSurParams * sizeof(float));
-  if (e != cudaSuccess) {
-    free_sur(s);
-    return cuda_fail(e, "surrogate init");
-  }
-  *out = s;
-  return VMAS_OK;
-}
-
-int vmas_sur_destroy(vmas_surrogate *s) {
-  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
-  free_sur(s);
-  return VMAS_OK;
-}
-
-int vmas_sur_set_params(vmas_surrogate *s, const float *h_params) {
-  if (!s || !h_params) return fail(VMAS_EINVAL, "surrogate or h_params is NULL");
-  for (int q = 0; q < kSurParams; ++q)
-    if (!std::isfinite(h_params[q])) return fail(VMAS_EINVAL, "a parameter is not finite");
-  VMAS_CUDA(cudaMemcpy(s->p32, h_params, kSurParams * sizeof(float), cudaMemcpyHostToDevice));
-  f32_to_bf16_kernel<<<blocks_for(kSurParams, 256), 256>>>(s->p32, s->pbf, kSurParams);
-  VMAS_CUDA(cudaGetLastError());
-  VMAS_CUDA(cudaMemset(s->adam_m, 0, kSurParams * sizeof(float)));
-  VMAS_CUDA(cudaMemset(s->adam_v, 0, kSurParams * sizeof(float)));
-  VMAS_CUDA(cudaDeviceSynchronize());
-  s->adam_t = 0;
-  return VMAS_OK;
-}
-
-int vmas_sur_get_params(vmas_surrogate *s, float *h_params) {
-  if (!s || !h_params) return fail(VMAS_EINVAL, "surrogate or h_params is NULL");
-  VMAS_CUDA(cudaDeviceSynchronize());
-  VMAS_CUDA(cudaMemcpy(h_params, s->p32, kSurParams * sizeof(float), cudaMemcpyDeviceToHost));
-  return VMAS_OK;
-}
-
-int vmas_sur_set_mode(vmas_surrogate *s, int32_t mode) {
-  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
-  if (mode != VMAS_SUR_FUSED && mode != VMAS_SUR_LAYERED) return fail(VMAS_EINVAL, "unknown mode");
-  s->mode = mode;
-  return VMAS_OK;
-}
-
-int vmas_sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_out,
-                     void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  cudaStream_t st = as_stream(stream);
-  if (s->mode == VMAS_SUR_FUSED)
-    return sur_fused(s, w, d_actions, d_out ? d_out : s->out, false, 0.f, st);
-  if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
-  if (d_out && w->E)
-    VMAS_CUDA(cudaMemcpyAsync(d_out, s->out, (size_t)w->E * sur::kAgents * 8 * sizeof(float),
-                              cudaMemcpyDeviceToDevice, st));
-  return VMAS_OK;
-}
-
-int vmas_sur_loss_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
-                       const float *d_target, float *d_loss, float *d_grad, void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  if (w->E > 0 && !d_target) return fail(VMAS_EINVAL, "d_target is NULL");
-  if ((rc = ensure_training(s))) return rc;
-  cudaStream_t st = as_stream(stream);
-  if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
-  if ((rc = sur_backward(s, w->E, d_target, d_loss, st))) return rc;
-  if (d_grad)
-    VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
-                              st));
-  return VMAS_OK;
-}
-
-int vmas_sur_adam(vmas_surrogate *s, float lr, const float *d_grad, void *stream) {
-  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
-  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
-  cudaStream_t st = as_stream(stream);
-  if (d_grad && d_grad != s->grad)
-    VMAS_CUDA(cudaMemcpyAsync(s->grad, d_grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
-                              st));
-  return sur_adam(s, lr, st);
-}
-
-// Forward on the world's current state, the plain step (the world advances)
-// as the target, loss and gradient into s->grad.
-static int sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
-                          float *d_loss, cudaStream_t st) {
-  int rc = ensure_training(s);
-  if (rc) return rc;
-  const int E = w->E, R = E * sur::kAgents;
-  if (E == 0) {
-    VMAS_CUDA(cudaMemsetAsync(s->grad, 0, kSurParams * sizeof(float), st));
-    if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
-    return VMAS_OK;
-  }
-  const size_t EN = (size_t)E * w->N;
-  float *px = w->planes, *py = px + EN, *vx = px + 2 * EN, *vy = px + 3 * EN;
-  if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
-  sur::save_agents_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save);
-  VMAS_CUDA(cudaGetLastError());
-  StepParams p = make_params(w);
-  p.actions = d_actions;
-  if ((rc = launch_step(p, st))) return rc;
-  sur::targets_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save,
-                                                           s->target);
-  VMAS_CUDA(cudaGetLastError());
-  return sur_backward(s, E, s->target, d_loss, st);
-}
-
-int vmas_sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_loss,
-                        float *d_grad, void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  cudaStream_t st = as_stream(stream);
-  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
-  if (d_grad)
-    VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
-                              st));
-  return VMAS_OK;
-}
-
-int vmas_sur_train_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float lr,
-                        float *d_loss, void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  if (!(lr >= 0) || !std::isfinite(lr)) return fail(VMAS_EINVAL, "lr must be >= 0");
-  cudaStream_t st = as_stream(stream);
-  if ((rc = sur_train_grad(s, w, d_actions, d_loss, st))) return rc;
-  if (w->E == 0) return VMAS_OK;
-  return sur_adam(s, lr, st);
-}
-
-int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, float limit,
-                  int32_t *d_n_fallback, void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  if (!(limit >= 0) || !std::isfinite(limit)) return fail(VMAS_EINVAL, "limit must be >= 0");
-  cudaStream_t st = as_stream(stream);
-  const int E = w->E;
-  if (E == 0) {
-    if (d_n_fallback) VMAS_CUDA(cudaMemsetAsync(d_n_fallback, 0, sizeof(int32_t), st));
-    return VMAS_OK;
-  }
-  VMAS_CUDA(cudaMemsetAsync(s->list_len, 0, sizeof(int), st));
-  if (s->mode == VMAS_SUR_FUSED) {
-    if ((rc = sur_fused(s, w, d_actions, nullptr, true, limit, st))) return rc;
-  } else {
-    if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
-    sur::PredictArgs a{};
-    const size_t EN = (size_t)E * w->N;
-    a.E = E; a.N = w->N;
-    a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
-    a.param = w->param; a.out = s->out; a.limit = limit;
-    a.list = s->list; a.list_len = s->list_len;
-    sur::predict_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
-    VMAS_CUDA(cudaGetLastError());
-  }
-  // the plain step for the listed envs (grid sized for all; blocks past the
-  // device-side count return at once)
-  StepParams p = make_params(w);
-  p.actions = d_actions;
-  p.env_list = s->list;
-  p.env_count = s->list_len;
-  if ((rc = launch_step(p, st))) return rc;
-  if (d_n_fallback)
-    VMAS_CUDA(cudaMemcpyAsync(d_n_fallback, s->list_len, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-  return VMAS_OK;
-}
-
-int vmas_sur_debug_features(vmas_surrogate *s, vmas_world *w, const float *d_actions,
-                            uint16_t *d_node, uint16_t *d_edge, float *d_mask, void *stream) {
-  int rc = sur_check(s, w, d_actions);
-  if (rc) return rc;
-  cudaStream_t st = as_stream(stream);
-  if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
-  const size_t R = (size_t)w->E * sur::kAgents, RK = R * sur::kK;
-  if (!R) return VMAS_OK;
-  if (d_node) VMAS_CUDA(cudaMemcpyAsync(d_node, s->node, R * 16 * 2, cudaMemcpyDeviceToDevice, st));
-  if (d_edge) VMAS_CUDA(cudaMemcpyAsync(d_edge, s->edge, RK * 16 * 2, cudaMemcpyDeviceToDevice, st));
-  if (d_mask) VMAS_CUDA(cudaMemcpyAsync(d_mask, s->mask, RK * 4, cudaMemcpyDeviceToDevice, st));
-  return VMAS_OK;
-}
-
-int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N, int32_t K,
-                         const uint16_t *d_a, int32_t lda, const uint16_t *d_b, int32_t ldb,
-                         const float *d_bias, int32_t gelu, float *d_out_f32, uint16_t *d_out_bf16,
-                         int32_t splits, void *stream) {
-  if (M < 0 || N < 0 || K < 0 || splits < 1 || splits > kSplitCap)
-    return fail(VMAS_EINVAL, "bad GEMM sizes");
-  if (splits > 1 && (d_bias || d_out_bf16 || gelu))
-    return fail(VMAS_EINVAL, "split-K GEMMs take no bias, GELU or bfloat16 output");
-  if ((size_t)M * N == 0) return VMAS_OK;
-  if ((K > 0 && (!d_a || !d_b)) || (!d_out_f32 && !d_out_bf16))
-    return fail(VMAS_EINVAL, "NULL buffer");
-  if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N))
-    return fail(VMAS_EINVAL, "leading dimension too small");
-  cudaStream_t st = as_stream(stream);
-  float *part = nullptr;
-  if (splits > 1) VMAS_CUDA(cudaMalloc(&part, (size_t)splits * M * N * sizeof(float)));
-  const int rc = gemm(st, trans_a, trans_b, M, N, K, reinterpret_cast<const bf16 *>(d_a), lda,
-                      reinterpret_cast<const bf16 *>(d_b), ldb, d_bias, gelu ? 1 : 0, d_out_f32, N,
-                      reinterpret_cast<bf16 *>(d_out_bf16), N, part, splits);
-  if (part) {
-    cudaStreamSynchronize(st);
-    cudaFree(part);
-  }
-  return rc;
 }
 
 }  // extern "C"
