@@ -64,11 +64,14 @@ enum {
   kStatCount = 16
 };
 
-// Per-environment shared memory: poses twice (the second copy lets the list
-// build read entity a + d without wrapping), body frames, contact records,
-// per-lane and compacted candidate lists.
+// Per-environment shared memory: poses, body frames, contact records (whose
+// area also holds the per-lane candidate lists while the list is built) and
+// the compacted candidate list.
+__host__ __device__ inline int fused_rec_bytes(int G) {
+  return kRecCap * 20 > align16(2 * G * kLaneCand) ? kRecCap * 20 : align16(2 * G * kLaneCand);
+}
 __host__ __device__ inline int fused_env_bytes(int N, int G) {
-  return 48 * N + kRecCap * 20 + 2 * align16(2 * G * kLaneCand);
+  return 32 * N + fused_rec_bytes(G) + align16(2 * G * kLaneCand);
 }
 __host__ __device__ inline int fused_cta_smem_bytes(int N, int P, int G) {
   return align16(2 * P) + kFusedWarps * (32 / G) * fused_env_bytes(N, G);
@@ -137,12 +140,15 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   const unsigned lt = (1u << lane) - 1u;
   unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(NL, G);
-  float4 *s_bp = reinterpret_cast<float4 *>(es);  // [2 NL] {x, y, inflated R, kind}
-  float4 *s_ng = s_bp + 2 * NL;                    // [NL] {cos, sin, ha, hb}
+  float4 *s_bp = reinterpret_cast<float4 *>(es);  // [NL] {x, y, inflated R, kind}
+  float4 *s_ng = s_bp + NL;                        // [NL] {cos, sin, ha, hb}
   float4 *s_rec = s_ng + NL;                       // {fx, fy, ti, tj}
   uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kRecCap);
-  uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rij + kRecCap);  // [G][kLaneCand]
-  uint16_t *s_cand = s_lc + align16(2 * G * kLaneCand) / 2;          // compact list
+  // per-lane lists [G][kLaneCand]: only live while the list is built, before
+  // any contact record of the substep is written
+  uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rec);
+  uint16_t *s_cand = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(s_rec) +
+                                                  fused_rec_bytes(G));  // compact list
   __syncthreads();
 
   // this group's environment: index, entity base and count, action rows
@@ -357,12 +363,6 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     }
 
     if (rebuild) {
-      // second copy of the poses, so partner a + d needs no wrap
-#pragma unroll
-      for (int s = 0; s < SLOTS; ++s) {
-        const int a = lg + G * s;
-        if (valid && a < N) s_bp[VIDX(a + N, 2 * NL, 30)] = s_bp[VIDX(a, N, 31)];
-      }
       __syncwarp();
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
       int n = 0;
@@ -383,13 +383,13 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
           const bool a_moves = (ka & (kMovable | kRotatable)) != 0u;
           const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
           auto test_partner = [&](int d) {
-            const float4 bb = s_bp[VIDX(a + d, 2 * NL, 8)];
+            const int b = a + d >= N ? a + d - N : a + d;
+            const float4 bb = s_bp[VIDX(b, N, 8)];
             const uint32_t kb = __float_as_uint(bb.w);
             if (!(kb & kCollidable) || !(a_moves || (kb & (kMovable | kRotatable)))) return;
             const float dx = ax_ - bb.x, dy = ay_ - bb.y;
             const float lim = ra + bb.z;
             if (dx * dx + dy * dy > lim * lim) return;
-            const int b = a + d >= N ? a + d - N : a + d;
             if ((kb & 3u) == kLine && !(kb & kRotatable)) {
               const float4 gb4 = s_ng[VIDX(b, N, 9)];
               if (fabsf(dx * gb4.y - dy * gb4.x) >
