@@ -64,14 +64,16 @@ enum {
   kStatCount = 16
 };
 
-// Per-environment shared memory: poses, body frames, contact records (whose
-// area also holds the per-lane candidate lists while the list is built) and
-// the compacted candidate list.
+// Per-environment shared memory: poses, body frames, the lane-private
+// constants of the step (inverse mass and inertia, bounding radius, base force
+// and torque: 24 B per entity, kept here rather than in registers), contact
+// records (whose area also holds the per-lane candidate lists while the list
+// is built) and the compacted candidate list.
 __host__ __device__ inline int fused_rec_bytes(int G) {
   return kRecCap * 20 > align16(2 * G * kLaneCand) ? kRecCap * 20 : align16(2 * G * kLaneCand);
 }
 __host__ __device__ inline int fused_env_bytes(int N, int G) {
-  return 32 * N + fused_rec_bytes(G) + align16(2 * G * kLaneCand);
+  return align16(56 * N) + fused_rec_bytes(G) + align16(2 * G * kLaneCand);
 }
 __host__ __device__ inline int fused_cta_smem_bytes(int N, int P, int G) {
   return align16(2 * P) + kFusedWarps * (32 / G) * fused_env_bytes(N, G);
@@ -142,7 +144,9 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(NL, G);
   float4 *s_bp = reinterpret_cast<float4 *>(es);  // [NL] {x, y, inflated R, kind}
   float4 *s_ng = s_bp + NL;                        // [NL] {cos, sin, ha, hb}
-  float4 *s_rec = s_ng + NL;                       // {fx, fy, ti, tj}
+  float4 *s_mi = s_ng + NL;                        // [NL] {1/m, 1/I, R, action torque}
+  float2 *s_fb = reinterpret_cast<float2 *>(s_mi + NL);  // [NL] action + gravity force
+  float4 *s_rec = reinterpret_cast<float4 *>(es + align16(56 * NL));  // {fx, fy, ti, tj}
   uint32_t *s_rij = reinterpret_cast<uint32_t *>(s_rec + kRecCap);
   // per-lane lists [G][kLaneCand]: only live while the list is built, before
   // any contact record of the substep is written
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   unsigned long long *const stats = p.stats;
 
   float x[SLOTS], y[SLOTS], vx[SLOTS], vy[SLOTS], th[SLOTS], om[SLOTS];
-  float fbx[SLOTS], fby[SLOTS], tau[SLOTS], im[SLOTS], iI[SLOTS], rb[SLOTS];
+  float fbx[SLOTS], fby[SLOTS], tau[SLOTS];  // live only until stored to s_fb / s_mi
   uint32_t kd[SLOTS];  // kind byte; bits 8.. hold 1 + the entity's action row (0: none)
   float4 prs[SLOTS];
   const int le = warp * EPW + grp;  // this env's index within the CTA
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   };
   // Eq. 1: action + gravity, constant over a step (only movable bodies
   // integrate, so only their mass matters); a staged step reads its actions
-  // from shared memory
+  // from shared memory.  store_fb moves them to the lane's own entries.
   auto load_actions = [&](int t) {
     const float *base = (bulk && t == 0)
                             ? reinterpret_cast<const float *>(stage + 6 * plane_b + param_b) +
@@ -275,6 +279,16 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       const float m = prs[s].x > 0.f ? 1.f / prs[s].x : 0.f;
       fbx[s] = fax + m * p.gx;
       fby[s] = fay + m * p.gy;
+    }
+  };
+  auto store_fb = [&]() {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int a = lg + G * s;
+      if (valid && a < N) {
+        s_fb[a] = make_float2(fbx[s], fby[s]);
+        s_mi[a].w = tau[s];
+      }
     }
   };
   if constexpr (!RAW) {
@@ -315,23 +329,23 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     } else {
       pr = prs[s];
     }
-    im[s] = pr.x;
-    iI[s] = pr.y;
     const uint32_t sh = kd[s] & 3u;
-    rb[s] = sh == kBox ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
+    const float rb = sh == kBox ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
     if (ok) {
       float c = 1.f, sn = 0.f;
       if (sh != kSphere) body_axes(th[s], c, sn);
       s_ng[VIDX(a, N, 2)] = make_float4(c, sn, pr.z, pr.w);  // {cos, sin, ha, hb}
       // immovable bodies are published once here
-      const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
+      const float infl = rb + 1e-5f * (rb + fabsf(x[s]) + fabsf(y[s]));
       s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
+      s_mi[VIDX(a, N, 6)] = make_float4(pr.x, pr.y, rb, 0.f);
     }
   }
   if constexpr (RAW) {
     assign_rows();
     load_actions(0);
   }
+  store_fb();  // after the frames: the torque shares their float4
 
   const float move_limit = 0.499f * p.skin;
   bool full = false;    // group scans all pairs (list overflow)
@@ -341,7 +355,10 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
 
   const int tile = TILED ? p.tile : 1;
   for (int t = 0; t < tile; ++t) {
-  if (t > 0) load_actions(t);
+  if (t > 0) {
+    load_actions(t);
+    store_fb();
+  }
   for (int sub = 0; sub < p.S; ++sub) {
     // publish the substep-start pose of bodies that move or turn
     if (t > 0 || sub > 0) {
@@ -355,7 +372,8 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
             *reinterpret_cast<float2 *>(&s_ng[VIDX(a, N, 4)]) = make_float2(c, sn);
           }
           if (kd[s] & kMovable) {
-            const float infl = rb[s] + 1e-5f * (rb[s] + fabsf(x[s]) + fabsf(y[s]));
+            const float rb = s_mi[VIDX(a, N, 3)].z;
+            const float infl = rb + 1e-5f * (rb + fabsf(x[s]) + fabsf(y[s]));
             s_bp[VIDX(a, N, 5)] = make_float4(x[s], y[s], infl, __uint_as_float(kd[s]));
           }
         }
@@ -376,7 +394,8 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
           const uint32_t ka = kd[s];
           if (!(ka & kCollidable)) continue;
           const float ax_ = x[s], ay_ = y[s];
-          const float infl_a = rb[s] + 1e-5f * (rb[s] + fabsf(ax_) + fabsf(ay_));
+          const float rb = s_mi[VIDX(a, N, 11)].z;
+          const float infl_a = rb + 1e-5f * (rb + fabsf(ax_) + fabsf(ay_));
           const float ra = infl_a + p.skin;  // grown by the skin on both sides
           const bool a_line = (ka & 3u) == kLine && !(ka & kRotatable);
           const float4 ga = s_ng[VIDX(a, N, 7)];
@@ -443,9 +462,12 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     float Fx[SLOTS], Fy[SLOTS], T[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      Fx[s] = fbx[s];
-      Fy[s] = fby[s];
-      T[s] = tau[s];
+      const int a = lg + G * s;
+      const bool ok = valid && a < N;
+      const float2 f0 = ok ? s_fb[VIDX(a, N, 13)] : make_float2(0.f, 0.f);
+      Fx[s] = f0.x;
+      Fy[s] = f0.y;
+      T[s] = ok ? s_mi[VIDX(a, N, 14)].w : 0.f;
     }
     auto drain = [&](int n) {
       const int nmax = (int)__reduce_max_sync(FULL, (unsigned)n);
@@ -513,9 +535,15 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     float fastest = 0.f;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
+      float im = 0.f, iI = 0.f;  // kind bits are set only for this env's entities
+      if (kd[s] & (kMovable | kRotatable)) {
+        const float4 mi = s_mi[VIDX(lg + G * s, N, 18)];
+        im = mi.x;
+        iI = mi.y;
+      }
       if (kd[s] & kMovable) {
-        vx[s] = p.damp * vx[s] + Fx[s] * im[s] * p.h;
-        vy[s] = p.damp * vy[s] + Fy[s] * im[s] * p.h;
+        vx[s] = p.damp * vx[s] + Fx[s] * im * p.h;
+        vy[s] = p.damp * vy[s] + Fy[s] * im * p.h;
         if (p.vmax > 0.f) {
           const float sp = sqrtf(vx[s] * vx[s] + vy[s] * vy[s]);
           if (sp > p.vmax) {
@@ -529,7 +557,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
         fastest = fmaxf(fastest, fabsf(vx[s]) + fabsf(vy[s]));
       }
       if (kd[s] & kRotatable) {
-        om[s] = p.damp * om[s] + T[s] * iI[s] * p.h;
+        om[s] = p.damp * om[s] + T[s] * iI * p.h;
         th[s] += om[s] * p.h;
       }
     }
