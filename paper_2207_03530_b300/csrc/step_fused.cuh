@@ -385,7 +385,69 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
       int n = 0;
       bool over = false;
-      if (valid) {
+      // kernels compiled for a fixed entity count test every (slot, offset)
+      // without branches first; the generic kernel walks the offsets
+      constexpr bool kMask = NC > 0 && SLOTS * (NC / 2) <= 64;
+      if (kMask && valid) {
+        // pass 1: the bounding-circle test of every (slot, offset), without
+        // branches, into a bit mask in (slot, offset) order
+        constexpr int D = NC > 0 ? NC / 2 : 1;
+        const int dmax = (N - 1) / 2;
+        unsigned long long m = 0ull;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int a = lg + G * s;
+          const uint32_t ka = kd[s];
+          if (a >= N || !(ka & kCollidable)) continue;
+          const float ax_ = x[s], ay_ = y[s];
+          const float rb = s_mi[VIDX(a, N, 11)].z;
+          const float infl_a = rb + 1e-5f * (rb + fabsf(ax_) + fabsf(ay_));
+          const float ra = infl_a + p.skin;
+          const bool a_moves = (ka & (kMovable | kRotatable)) != 0u;
+          const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
+#pragma unroll
+          for (int d = 1; d <= D; ++d) {
+            const int b = a + d >= N ? a + d - N : a + d;
+            const float4 bb = s_bp[VIDX(b, N, 8)];
+            const uint32_t kb = __float_as_uint(bb.w);
+            const float dx = ax_ - bb.x, dy = ay_ - bb.y;
+            const float lim = ra + bb.z;
+            const bool pass = d <= dlast && (kb & kCollidable) &&
+                              (a_moves || (kb & (kMovable | kRotatable))) &&
+                              !(dx * dx + dy * dy > lim * lim);
+            m |= (unsigned long long)pass << (s * D + d - 1);
+          }
+        }
+        // pass 2: the exact line tests and the appends, in mask order; the
+        // published pose of a is its current position and inflated radius
+        while (m) {
+          const int bit = __ffsll((long long)m) - 1;
+          m &= m - 1ull;
+          const int s = bit / D, d = bit - s * D + 1;
+          const int a = lg + G * s;
+          const int b = a + d >= N ? a + d - N : a + d;
+          const float4 ba = s_bp[VIDX(a, N, 27)], bb = s_bp[VIDX(b, N, 28)];
+          const uint32_t ka = __float_as_uint(ba.w), kb = __float_as_uint(bb.w);
+          const float dx = ba.x - bb.x, dy = ba.y - bb.y;
+          if ((kb & 3u) == kLine && !(kb & kRotatable)) {
+            const float4 gb4 = s_ng[VIDX(b, N, 9)];
+            if (fabsf(dx * gb4.y - dy * gb4.x) > ba.z + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
+              continue;
+          }
+          if ((ka & 3u) == kLine && !(ka & kRotatable)) {
+            const float4 ga = s_ng[VIDX(a, N, 7)];
+            if (fabsf(dx * ga.y - dy * ga.x) > bb.z + p.skin + 1e-5f * (fabsf(ba.x) + fabsf(ba.y)))
+              continue;
+          }
+          if (n < kLaneCand) {
+            const int lo = a < b ? a : b, hi = a < b ? b : a;
+            s_lc[VIDX(lg * kLaneCand + n, LC, 10)] = (uint16_t)(lo | (hi << 8));
+          } else {
+            over = true;
+          }
+          ++n;
+        }
+      } else if (valid) {
         const int dmax = (N - 1) / 2;
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
