@@ -1,13 +1,16 @@
 """ctypes declarations of the C ABI in include/vmas.h (argument marshalling only).
 
 Loading fails loudly when libvmas.so is missing: there is no CPU fallback.
+With VMAS_CHECKED=1 in the environment the bounds-checked build
+libvmas_checked.so is loaded instead (see build.py).
 """
 from __future__ import annotations
 
 import ctypes
 import os
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvmas.so")
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libvmas_checked.so" if os.environ.get("VMAS_CHECKED") == "1" else "libvmas.so")
 
 VMAS_OK, VMAS_EINVAL, VMAS_ENOMEM, VMAS_ECUDA, VMAS_EDEVICE = 0, -1, -2, -3, -4
 MAX_ENTITIES = 128
@@ -92,8 +95,9 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libvmas.so is not built (expected at %s); build it with "
-                          "paper_2207_03530_b300.build.build()" % LIB_PATH)
+        raise ImportError("%s is not built (expected at %s); build it with "
+                          "paper_2207_03530_b300.build.build()"
+                          % (os.path.basename(LIB_PATH), LIB_PATH))
     L = ctypes.CDLL(LIB_PATH)
     vp, i32, P = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
     sig = {

@@ -3,6 +3,14 @@
 The host code is three translation units (the world and its step, the
 packed ragged worlds, the surrogate); each compiles to an object in its own
 nvcc process, in parallel, and one nvcc call links them.
+
+With VMAS_CHECKED=1 in the environment the same sources build
+libvmas_checked.so instead, with -DVMAS_CHECKED: every shared- and
+global-memory index of the step kernels is checked on the device; an index
+out of range is not used, sets bit 2 of the device error word (reported by
+vmas_check as VMAS_EDEVICE) and records where it happened.  The binding
+loads that library when the same variable is set, so
+``VMAS_CHECKED=1 python -m pytest tests -m gpu`` runs the GPU suite on it.
 """
 from __future__ import annotations
 
@@ -12,10 +20,11 @@ import subprocess
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-LIB = os.path.join(PKG, "libvmas.so")
+CHECKED = os.environ.get("VMAS_CHECKED") == "1"
+LIB = os.path.join(PKG, "libvmas_checked.so" if CHECKED else "libvmas.so")
 SOURCES = [os.path.join(PKG, "csrc", f) for f in ("vmas.cu", "ragged.cu", "surrogate_host.cu")]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-              "-Xcompiler", "-fPIC"]
+              "-Xcompiler", "-fPIC"] + (["-DVMAS_CHECKED"] if CHECKED else [])
 
 
 def _inputs():
@@ -31,7 +40,8 @@ def stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libvmas.so unless it is up to date; returns its path."""
+    """Compile the library (libvmas.so, or libvmas_checked.so with
+    VMAS_CHECKED=1) unless it is up to date; returns its path."""
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
