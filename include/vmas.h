@@ -64,6 +64,9 @@ enum {
 /* Bits of the device error word reported through VMAS_EDEVICE. */
 enum {
   VMAS_DEVERR_NONFINITE = 1, /* a state value became NaN or Inf */
+  VMAS_DEVERR_INDEX = 2,     /* bounds-checked builds (-DVMAS_CHECKED) only: an index was out
+                                of range and was not used; vmas_last_error() names the first
+                                one (site code, index, bound) */
   VMAS_DEVERR_BAD_ENTITY = 4, /* vmas_step_noalloc met an invalid entity and left it inert */
   VMAS_DEVERR_TIMEOUT = 8     /* a step's staging copies did not arrive in time; its CTA
                                  left its envs unchanged */
@@ -233,6 +236,8 @@ int vmas_ragged_rollout(vmas_ragged *world, const float *d_actions, int32_t n_st
 /* State [total][6] in the caller's entity order (see vmas_state). */
 int vmas_ragged_state(vmas_ragged *world, float *out, int32_t out_is_device, void *stream);
 int vmas_ragged_set_state(vmas_ragged *world, const float *d_state, void *stream);
+/* As vmas_check, for a ragged world's device error word. */
+int vmas_ragged_check(vmas_ragged *world, void *stream, int32_t *bits);
 /* lanes [5] per size class (NULL keeps them); steps_per_launch 1..1024. */
 int vmas_ragged_set_tuning(vmas_ragged *world, const int32_t *lanes, int32_t steps_per_launch);
 int vmas_ragged_get_tuning(const vmas_ragged *world, int32_t *lanes, int32_t *steps_per_launch);

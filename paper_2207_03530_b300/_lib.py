@@ -27,6 +27,7 @@ SYMBOLS = (
     "vmas_lidar", "vmas_world_set_rollout_tile",
     "vmas_ragged_create", "vmas_ragged_destroy", "vmas_ragged_info", "vmas_ragged_action_offsets",
     "vmas_ragged_step", "vmas_ragged_rollout", "vmas_ragged_state", "vmas_ragged_set_state",
+    "vmas_ragged_check",
     "vmas_ragged_set_tuning", "vmas_ragged_get_tuning", "vmas_ragged_autotune",
     "vmas_sur_param_count", "vmas_sur_create", "vmas_sur_destroy", "vmas_sur_set_params",
     "vmas_sur_get_params", "vmas_sur_set_mode", "vmas_sur_forward", "vmas_sur_loss_grad", "vmas_sur_adam",
@@ -133,6 +134,7 @@ def load():
         "vmas_ragged_step": ([vp, vp, vp], ctypes.c_int),
         "vmas_ragged_rollout": ([vp, vp, i32, vp], ctypes.c_int),
         "vmas_ragged_state": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_ragged_check": ([vp, vp, P(i32)], ctypes.c_int),
         "vmas_ragged_set_state": ([vp, vp, vp], ctypes.c_int),
         "vmas_ragged_set_tuning": ([vp, vp, i32], ctypes.c_int),
         "vmas_ragged_get_tuning": ([vp, vp, vp], ctypes.c_int),

@@ -354,6 +354,35 @@ int vmas_ragged_rollout(vmas_ragged *r, const float *d_actions, int32_t n_steps,
   return VMAS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Wait for `st`, then report (and clear) the device error word.
+int ragged_read_err(vmas_ragged *r, cudaStream_t st, int32_t *bits) {
+  int h[3] = {0, 0, 0};  // bits; bounds-checked builds: site << 20 | index, bound
+  VMAS_CUDA(cudaMemcpyAsync(h, r->err, sizeof(h), cudaMemcpyDeviceToHost, st));
+  VMAS_CUDA(cudaStreamSynchronize(st));
+  if (bits) *bits = h[0];
+  if (h[0]) {
+    VMAS_CUDA(cudaMemsetAsync(r->err, 0, sizeof(h), st));
+    VMAS_CUDA(cudaStreamSynchronize(st));
+    std::string msg = "device error word set (bits " + std::to_string(h[0]) + ")";
+    if (h[0] & VMAS_DEVERR_INDEX)
+      msg += "; first index out of range: site " + std::to_string(h[1] >> 20) + ", index " +
+             std::to_string(h[1] & 0xfffff) + ", bound " + std::to_string(h[2]);
+    return fail(VMAS_EDEVICE, msg);
+  }
+  return VMAS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int vmas_ragged_check(vmas_ragged *r, void *stream, int32_t *bits) {
+  if (!r) return fail(VMAS_EINVAL, "world is NULL");
+  return ragged_read_err(r, as_stream(stream), bits);
+}
+
 int vmas_ragged_state(vmas_ragged *r, float *out, int32_t out_is_device, void *stream) {
   if (!r) return fail(VMAS_EINVAL, "world is NULL");
   if (!r->total) return VMAS_OK;
@@ -369,13 +398,7 @@ int vmas_ragged_state(vmas_ragged *r, float *out, int32_t out_is_device, void *s
   VMAS_CUDA(cudaGetLastError());
   if (!out_is_device) {
     VMAS_CUDA(cudaMemcpyAsync(out, r->stage, r->total * 6 * sizeof(float), cudaMemcpyDeviceToHost, st));
-    int h = 0;
-    VMAS_CUDA(cudaMemcpyAsync(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VMAS_CUDA(cudaStreamSynchronize(st));
-    if (h) {
-      cudaMemset(r->err, 0, sizeof(int));
-      return fail(VMAS_EDEVICE, "device error word set (bits " + std::to_string(h) + ")");
-    }
+    return ragged_read_err(r, st, nullptr);
   }
   return VMAS_OK;
 }

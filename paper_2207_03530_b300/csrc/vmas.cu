@@ -240,14 +240,18 @@ int ensure_stage(vmas_world *w) {
 }
 
 int read_err(vmas_world *w, cudaStream_t st, int32_t *bits) {
-  int h = 0;
-  VMAS_CUDA(cudaMemcpyAsync(&h, w->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int h[3] = {0, 0, 0};  // bits; bounds-checked builds: site << 20 | index, bound
+  VMAS_CUDA(cudaMemcpyAsync(h, w->err, sizeof(h), cudaMemcpyDeviceToHost, st));
   VMAS_CUDA(cudaStreamSynchronize(st));
-  if (bits) *bits = h;
-  if (h) {
-    VMAS_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+  if (bits) *bits = h[0];
+  if (h[0]) {
+    VMAS_CUDA(cudaMemsetAsync(w->err, 0, sizeof(h), st));
     VMAS_CUDA(cudaStreamSynchronize(st));
-    return fail(VMAS_EDEVICE, "device error word set (bits " + std::to_string(h) + ")");
+    std::string msg = "device error word set (bits " + std::to_string(h[0]) + ")";
+    if (h[0] & VMAS_DEVERR_INDEX)
+      msg += "; first index out of range: site " + std::to_string(h[1] >> 20) + ", index " +
+             std::to_string(h[1] & 0xfffff) + ", bound " + std::to_string(h[2]);
+    return fail(VMAS_EDEVICE, msg);
   }
   return VMAS_OK;
 }
@@ -284,6 +288,10 @@ int noalloc_scratch(unsigned char **out) {
 }
 
 // Canonical pair list (i < j, row-major) for N entities.
+#ifdef VMAS_CHECKED
+__global__ void or_status_kernel(int *dst, const int *src) { atomicOr(dst, src[0]); }
+#endif
+
 __global__ void fill_pairs_kernel(uint16_t *pairs, int N) {
   for (int i = blockIdx.x; i < N - 1; i += gridDim.x) {
     const int row = i * N - i * (i + 1) / 2;
@@ -348,8 +356,8 @@ int vmas_step_noalloc(const vmas_step_noalloc_args *a, void *stream) {
   const int N = a->n_entities;
   uint16_t *pairs = reinterpret_cast<uint16_t *>(scratch);
   int *status = reinterpret_cast<int *>(scratch + kNoallocStatusOffset);
-  // the status word must start each call at zero; the pair table is rewritten
-  VMAS_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  // the status words must start each call at zero; the pair table is rewritten
+  VMAS_CUDA(cudaMemsetAsync(status, 0, 3 * sizeof(int), st));
   if (N > 1) {
     fill_pairs_kernel<<<N - 1, 64, 0, st>>>(pairs, N);
     VMAS_CUDA(cudaGetLastError());
@@ -374,7 +382,13 @@ int vmas_step_noalloc(const vmas_step_noalloc_args *a, void *stream) {
   p.EN = EN;
   p.pairs = pairs;
   p.actions = a->actions;
+#ifdef VMAS_CHECKED
+  // a bounds-checked kernel also writes the two words after the bits, so it
+  // gets the library's own three; their bits are ORed into the caller's word
+  p.err = status;
+#else
   p.err = a->status ? a->status : status;
+#endif
   p.aos_state = a->state;
   p.r_shape = a->shape;
   p.r_flags = a->flags;
@@ -383,11 +397,18 @@ int vmas_step_noalloc(const vmas_step_noalloc_args *a, void *stream) {
   p.r_mass = a->mass;
   p.r_inertia = a->inertia;
   switch (group_lanes(N)) {
-    case 4: return launch_raw_g<4>(p, st);
-    case 8: return launch_raw_g<8>(p, st);
-    case 16: return launch_raw_g<16>(p, st);
-    default: return launch_raw_g<32>(p, st);
+    case 4: rc = launch_raw_g<4>(p, st); break;
+    case 8: rc = launch_raw_g<8>(p, st); break;
+    case 16: rc = launch_raw_g<16>(p, st); break;
+    default: rc = launch_raw_g<32>(p, st); break;
   }
+#ifdef VMAS_CHECKED
+  if (rc == VMAS_OK && a->status) {
+    or_status_kernel<<<1, 1, 0, st>>>(a->status, status);
+    VMAS_CUDA(cudaGetLastError());
+  }
+#endif
+  return rc;
 }
 
 
@@ -795,14 +816,6 @@ int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
   return VMAS_OK;
 }
 
-#ifdef VMAS_CHECKED
-// Self-checking build only: the error words {bits, first bad index, limit}.
-int vmas_debug_err_words(vmas_world *w, int32_t *out) {
-  if (!w || !out) return VMAS_EINVAL;
-  cudaDeviceSynchronize();
-  return cudaMemcpy(out, w->err, 3 * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : VMAS_ECUDA;
-}
-#endif
 
 // Lanes per env of the differentiable rollout kernels: the smallest power
 // of two that holds the env's entities.

@@ -65,6 +65,15 @@ class RaggedWorld:
     def set_state(self, state: torch.Tensor) -> None:
         _lib.check(self._L.vmas_ragged_set_state(self._h, state.contiguous().data_ptr(), _stream()))
 
+    def check(self) -> int:
+        """Wait for the stream; raise if a kernel set the device error word."""
+        bits = ctypes.c_int32(0)
+        rc = self._L.vmas_ragged_check(self._h, _stream(), ctypes.byref(bits))
+        if rc == _lib.VMAS_EDEVICE:
+            raise _lib.VmasError(rc, "device error bits %d" % bits.value)
+        _lib.check(rc)
+        return bits.value
+
     def tuning(self):
         lanes = np.zeros(5, np.int32)
         tile = ctypes.c_int32()

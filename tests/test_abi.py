@@ -112,6 +112,8 @@ def test_null_arguments(L):
     assert L.vmas_world_destroy(None) == _lib.VMAS_OK
     assert "NULL" in L.vmas_last_error().decode()
     assert L.vmas_rollout_host(None, None, 1, None, None) == _lib.VMAS_EINVAL
+    assert L.vmas_check(None, None, None) == _lib.VMAS_EINVAL
+    assert L.vmas_ragged_check(None, None, None) == _lib.VMAS_EINVAL
 
 
 def test_surrogate_null_and_bad_arguments(L):

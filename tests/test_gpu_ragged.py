@@ -47,6 +47,7 @@ def test_ragged_matches_oracle(vmas_lib, orc, seed):
     got, sel = _unpack_state(rw.state().cpu().numpy(), counts, sc.n_entities)
     ref = orc.step(sc, sc.init_state, act, threads=8)
     assert normwise_err(got[sel], ref[sel]).max() <= TOL
+    rw.check()
     rw.close()
 
 
@@ -67,6 +68,7 @@ def test_ragged_matches_padded_world(vmas_lib):
     assert normwise_err(got[sel], ref[sel]).max() <= TOL
     # padding entities of the regular world never move
     assert np.array_equal(ref[~sel], sc.init_state[~sel])
+    rw.check()
     rw.close()
     w.close()
 
@@ -82,6 +84,7 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     for t in range(24):
         base.step(pact[t])
     ref = base.state().cpu().numpy()
+    base.check()
     base.close()
     for tile in (1, 4, 7):
         rw = _ragged(sc, counts)
@@ -89,6 +92,7 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
         rw.rollout(pact)
         assert np.array_equal(rw.state().cpu().numpy(), ref), tile
         rw.rollout(pact[:0])  # zero steps is a no-op
+        rw.check()
         rw.close()
     rw = _ragged(sc, counts)
     before = rw.state().cpu().numpy()
@@ -99,6 +103,7 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     rw.rollout(pact)
     rw.rollout(pact)  # graph replay
     got = rw.state().cpu().numpy()
+    rw.check()
     rw.close()
     rw2 = _ragged(sc, counts)
     rw2.rollout(pact)
@@ -106,6 +111,7 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     # another lane layout sums contacts in another order: after 48 steps of
     # contact dynamics the two agree to rounding growth, not bitwise
     assert normwise_err(got, rw2.state().cpu().numpy()).max() <= 1e-4
+    rw2.check()
     rw2.close()
 
 
@@ -142,6 +148,7 @@ def test_extreme_env_sizes(vmas_lib, orc):
     refp = np.concatenate([ref[0, :1], ref[1]])
     per_env_ok = normwise_err(got[1:], refp[1:]).max() <= 1e-3  # 128 overlapping bodies: near ties allowed
     assert normwise_err(got[:1], refp[:1]).max() <= TOL and per_env_ok
+    rw.check()
     rw.close()
 
 
@@ -184,5 +191,7 @@ def test_full_config_sampled_envs(vmas_lib, orc):
     for t in range(T):
         rw2.step(pact[t])
     assert np.array_equal(rw.state().cpu().numpy(), rw2.state().cpu().numpy())
+    rw.check()
     rw.close()
+    rw2.check()
     rw2.close()
