@@ -70,6 +70,27 @@ def _hbm_roofline(bytes_per_env_step, env_steps_per_s, note):
             "note": note}
 
 
+# FP32 operations of one ray against one body, counted from the closed-form
+# entry distances of the LIDAR kernel as written (sqrt and divide count one,
+# comparisons that feed a branch are not counted), plus one for the running
+# minimum; and of one ray direction (angle, sin/cos by the library's own
+# reduction and series)
+LIDAR_OPS = {"sphere": 12, "box": 28, "line": 13, "ray": 22}
+
+
+def _alu_roofline(ops_per_unit, units_per_s, note):
+    """FP32 ALU roofline: one operation per lane per cycle on every FP32 lane
+    (SMs x 128 lanes x the maximum SM clock, 2,032 MHz on B300)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2.032e9 / 1e12
+    achieved = ops_per_unit * units_per_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "peak_source": "%d SMs x 128 FP32 lanes x 2.032 GHz" % sms,
+            "ops_per_unit": ops_per_unit, "note": note}
+
+
 # the sources the plain step kernel is compiled from
 STEP_KERNEL_SOURCES = ("contact.cuh", "params.cuh", "step.cuh", "step_fused.cuh")
 
@@ -866,8 +887,21 @@ def run_lidar(args):
     ms = a.elapsed_time(b) / args.steps
     rays = args.envs * sc.n_actuated * 32
     w.close()
-    print(json.dumps({"form": "lidar", "metric": "rays/s", "value": rays / (ms / 1e3),
+    # bodies each ray is tested against: every other collidable entity (the
+    # casters are spheres)
+    coll = (np.asarray(sc.flags[0]) & scenes.COLLIDABLE) != 0
+    shape = np.asarray(sc.shape[0])
+    ops = (LIDAR_OPS["ray"] + LIDAR_OPS["sphere"] * (int((coll & (shape == 0)).sum()) - 1)
+           + LIDAR_OPS["box"] * int((coll & (shape == 1)).sum())
+           + LIDAR_OPS["line"] * int((coll & (shape == 2)).sum()))
+    value = rays / (ms / 1e3)
+    print(json.dumps({"form": "lidar", "metric": "rays/s", "value": value,
                       "unit": "rays/s", "ms_per_call": ms, "env_scans_per_s": args.envs / (ms / 1e3),
+                      "roofline": _alu_roofline(ops, value, "instruction-issue-bound: 88 % of "
+                                                "issue slots, ALU pipe 68 %, 32 warp "
+                                                "instructions per ray "
+                                                "(profiles/lidar_kernel_30k.md)"),
+                      "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "%d envs x 20 agents x 32 rays vs 24 bodies"
                                              % args.envs}}), flush=True)
     return 0

@@ -934,7 +934,7 @@ int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, voi
   p.param = w->param;
   p.kind = w->kind;
   p.out = d_out;
-  const size_t smem = (size_t)w->N * (16 + 8 + 1) + 16;
+  const size_t smem = (size_t)vmas::lidar_smem_bytes(w->N);
   vmas::lidar_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
