@@ -54,7 +54,11 @@ __device__ __forceinline__ bool sphere_force(float xi, float yi, float xj, float
                                              const DiffParams &p, float &fx, float &fy,
                                              float *J) {
   const float dx = xi - xj, dy = yi - yj;
-  const float s = sqrtf(dx * dx + dy * dy);
+  const float d2 = dx * dx + dy * dy;
+  // most pairs are apart: d2 > 1.0001 rsum^2 gives RN(sqrt(d2)) > rsum, so
+  // the exact test below would reject them too (results do not change)
+  if (d2 > 1.0001f * (rsum * rsum)) return false;
+  const float s = sqrtf(d2);
   const float g = s - rsum;
   if (!(g <= 0.f) || !(s > 0.f)) return false;
   const float inv = 1.f / s;
