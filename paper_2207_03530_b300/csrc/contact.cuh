@@ -141,8 +141,10 @@ __device__ __forceinline__ void poly_edge(const Poly &p, int k, float &ax, float
   }
 }
 
-// Box/line i against box/line j.
-__device__ __noinline__ bool hit_poly_poly(const Poly A, const Poly B, Hit &h) {
+// Box/line i against box/line j.  Inlined: as an out-of-line call its
+// by-value arguments went through the stack and the call site cost the step
+// kernel its spill-free register allocation (4 % of the step).
+__device__ __forceinline__ bool hit_poly_poly(const Poly A, const Poly B, Hit &h) {
   // candidate axes: A's (box e1, e2 | line e2), then B's, then for two
   // exactly parallel lines A's e1 (their normals coincide)
   float ax[5], ay[5];
