@@ -36,12 +36,30 @@ enum : int {
   kParams = kOffb3 + 8
 };
 
+// 1 + erf(x) by the rational approximation of Abramowitz & Stegun,
+// Handbook of Mathematical Functions, 7.1.26 (Hastings): for x >= 0,
+// erf(x) = 1 - q(x), q = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^{-x^2},
+// t = 1 / (1 + p x), |error| <= 1.5e-7; erf is odd, so 1 + erf(x) = q(|x|)
+// for x < 0 (no cancellation in the tail).  About half the instructions of
+// erff, and far below the bfloat16 rounding every GELU output meets.
+__device__ __forceinline__ float one_plus_erf(float x) {
+  const float ax = fabsf(x);
+  const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+  float poly = fmaf(1.061405429f, t, -1.453152027f);
+  poly = fmaf(poly, t, 1.421413741f);
+  poly = fmaf(poly, t, -0.284496736f);
+  poly = fmaf(poly, t, 0.254829592f);
+  const float q = poly * t * __expf(-ax * ax);
+  return x < 0.f ? q : 2.f - q;
+}
+// gelu(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative
+// (1 + erf(z / sqrt 2)) / 2 + z phi(z).
 __device__ __forceinline__ float gelu(float z) {
-  return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+  return 0.5f * z * one_plus_erf(z * 0.70710678118654752f);
 }
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) +
-         z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return 0.5f * one_plus_erf(z * 0.70710678118654752f) +
+         z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 // --------------------------------------------------------------- GEMM

@@ -99,7 +99,7 @@ __device__ __forceinline__ void load_b1k2(uint32_t (&b)[4], const bf16 *W, int l
   ldsm_x4(b, W + (lane & 7) * ld + 16 * (kk + (m >> 1)) + (m & 1) * 8);
 }
 
-// GELU of four values, out of line (one copy of the erf code in the kernel).
+// GELU of four values, out of line (one copy of the GELU code in the kernel).
 __device__ __noinline__ float4 gelu4(float4 z) {
   return make_float4(gelu(z.x), gelu(z.y), gelu(z.z), gelu(z.w));
 }

@@ -59,6 +59,33 @@ def test_gemm_matches_fp64(vmas_lib, ta, tb, M, N, K):
     assert np.all(np.abs(g - gr) <= 2.0 ** -7 * np.abs(gr) + 1e-6)
 
 
+def test_gelu_dense_grid(vmas_lib):
+    """The device GELU (1 + erf by Abramowitz & Stegun 7.1.26) against the
+    FP64 GELU on every bfloat16 value in [-8, 8]: an identity GEMM passes the
+    values through exactly, and its GELU epilogue rounds to bfloat16.  The
+    roundings agree except where the two values straddle a rounding
+    boundary, and never differ by more than one bfloat16 step or 2e-7."""
+    from paper_2207_03530_b300.surrogate import gemm_bf16
+
+    bits = np.arange(0, 1 << 16, dtype=np.uint32) << 16
+    v = bits.view(np.float32)
+    v = np.unique(v[np.isfinite(v) & (np.abs(v) <= 8.0)]).astype(np.float64)
+    K = 64
+    n = -(-len(v) // K)
+    B = np.zeros(K * n)
+    B[:len(v)] = v
+    B = B.reshape(n, K).T.copy()  # value i at row i % K, column i // K
+    eye = torch.eye(K, dtype=torch.bfloat16, device="cuda")
+    out, obf = gemm_bf16(eye, torch.tensor(B, dtype=torch.bfloat16, device="cuda"), gelu=True)
+    assert np.array_equal(out.cpu().numpy(), B.astype(np.float32))
+    g = obf.float().cpu().numpy().T.reshape(-1)[:len(v)].astype(np.float64)
+    ref = _gelu64(v)
+    ref_bf = _bf(ref)
+    step = np.abs(ref_bf) * 2.0 ** -7
+    assert np.all(np.abs(g - ref_bf) <= np.maximum(step, 2e-7))
+    assert np.mean(g == ref_bf) >= 0.99
+
+
 @pytest.mark.parametrize("splits", [2, 7, 64])
 def test_gemm_split_k(vmas_lib, splits):
     from paper_2207_03530_b300.surrogate import gemm_bf16
