@@ -40,8 +40,8 @@ enum : int {
 // Handbook of Mathematical Functions, 7.1.26 (Hastings): for x >= 0,
 // erf(x) = 1 - q(x), q = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^{-x^2},
 // t = 1 / (1 + p x), |error| <= 1.5e-7; erf is odd, so 1 + erf(x) = q(|x|)
-// for x < 0 (no cancellation in the tail).  About half the instructions of
-// erff, and far below the bfloat16 rounding every GELU output meets.
+// for x < 0 (no cancellation in the tail).  Fewer instructions than erff,
+// and an error far below the bfloat16 rounding every GELU output meets.
 __device__ __forceinline__ float one_plus_erf(float x) {
   const float ax = fabsf(x);
   const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
