@@ -95,11 +95,21 @@ def _alu_roofline(ops_per_unit, units_per_s, note):
 STEP_KERNEL_SOURCES = ("contact.cuh", "params.cuh", "step.cuh", "step_fused.cuh")
 
 
+def _code_text(text):
+    """C++ source without comments and with whitespace collapsed, so that a
+    comment edit does not make a profile of unchanged code look stale."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def _kernel_digest():
     h = hashlib.sha256()
     for name in STEP_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2207_03530_b300", "csrc", name)) as f:
+            h.update(_code_text(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,7 +5,12 @@
 // memory between substeps and touches HBM once on the way in and once on the
 // way out.  32 / G environments share a warp.
 //
-//   entities   entity a lives in lane a % G of its group, slot a / G
+//   entities   entity a lives in lane a % G of its group, slot a / G; its
+//              pose and velocity in registers, its inverse mass and inertia,
+//              bounding radius and the step's action + gravity force and
+//              torque in the lane's own shared-memory entries (read once per
+//              substep: cheaper there than in registers the narrow phase
+//              needs)
 //   candidates once per step (and again only if some body may have moved
 //              more than half the skin since: a per-lane bound adds
 //              (|vx| + |vy|) h of its fastest body every substep) every lane
@@ -18,7 +23,8 @@
 //              environment.  A pair left out is farther apart than its
 //              bounding circles for the rest of the list's life, so the list
 //              never changes results, and the list order does not depend on
-//              the skin.
+//              the skin.  Kernels compiled for a fixed entity count run
+//              the bounding tests without branches into a bit mask first.
 //   contacts   per substep the group walks its list G pairs at a time through
 //              the exact narrow phase; hits are appended to a per-env buffer
 //              in list order (ballot + popc) and every lane adds the records
