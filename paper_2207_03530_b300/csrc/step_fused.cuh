@@ -82,7 +82,8 @@ __host__ __device__ inline int fused_env_bytes(int N, int G) {
   return align16(56 * N) + fused_rec_bytes(G) + align16(2 * G * kLaneCand);
 }
 __host__ __device__ inline int fused_cta_smem_bytes(int N, int P, int G) {
-  return align16(2 * P) + kFusedWarps * (32 / G) * fused_env_bytes(N, G);
+  (void)P;  // the pair table stays in global memory (read only by full scans)
+  return kFusedWarps * (32 / G) * fused_env_bytes(N, G);
 }
 
 // Shape-pair class of two shape ids: SS 0, SB 1, SL 2, BB 3, BL 4, LL 5.
@@ -114,7 +115,6 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     // (uniform over the block, before its first barrier)
     if (p.env_list && (int)(blockIdx.x * kFusedWarps * EPW) >= *p.env_count) return;
   }
-  uint16_t *s_pairs = reinterpret_cast<uint16_t *>(smem);
   // Bulk staging (one-step plain kernels, full CTAs): the CTA's envs are
   // contiguous in every plane, so one thread issues a bulk copy per plane,
   // for the parameters, the actions and the kinds into the per-env area
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   bool bulk = false;
   if constexpr (!RAW && !RAGGED && !TILED)
     bulk = p.bulk && !p.env_list && (blockIdx.x + 1) * CE <= p.E;
-  unsigned char *stage = smem + align16(2 * P);
+  unsigned char *stage = smem;
   const uint32_t plane_b = (uint32_t)(CE * NL * 4), param_b = 4 * plane_b;
   const uint32_t act_b = (uint32_t)(CE * p.A * 12), kind_b = (uint32_t)(CE * NL);
   if (bulk && threadIdx.x == 0) {
@@ -140,14 +140,13 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
                p.actions + (size_t)blockIdx.x * CE * p.A * 3, act_b, bar);
     bulk_g2s(smem_u32(stage + 6 * plane_b + param_b + act_b), p.kind + e0, kind_b, bar);
   }
-  for (int q = threadIdx.x; q < P; q += blockDim.x) s_pairs[q] = p.pairs[q];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / G, lg = lane % G;
   const int LC = G * kLaneCand;  // candidate capacity per env
   (void)LC;
   const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   const unsigned lt = (1u << lane) - 1u;
-  unsigned char *es = smem + align16(2 * P) + (warp * EPW + grp) * fused_env_bytes(NL, G);
+  unsigned char *es = smem + (warp * EPW + grp) * fused_env_bytes(NL, G);
   float4 *s_bp = reinterpret_cast<float4 *>(es);  // [NL] {x, y, inflated R, kind}
   float4 *s_ng = s_bp + NL;                        // [NL] {cos, sin, ha, hb}
   float4 *s_mi = s_ng + NL;                        // [NL] {1/m, 1/I, R, action torque}
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rec);
   uint16_t *s_cand = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(s_rec) +
                                                   fused_rec_bytes(G));  // compact list
-  __syncthreads();
+  __syncthreads();  // the staging mbarrier is initialised before any thread waits on it
 
   // this group's environment: index, entity base and count, action rows
   int e, N, A_e;
@@ -563,7 +562,9 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       Hit hh;
       int i = 0, j = 0;
       if (c < ncand) {
-        const uint32_t ij = full ? s_pairs[VIDX(c, P, 21)] : s_cand[VIDX(c, LC, 20)];
+        // a full scan (after a list overflow, rare) reads the canonical
+        // pair table from global memory, where it stays L2-resident
+        const uint32_t ij = full ? p.pairs[VIDX(c, P, 21)] : s_cand[VIDX(c, LC, 20)];
         i = VIDX((int)(ij & 0xffu), NL, 22);
         j = VIDX((int)(ij >> 8), NL, 23);
         const bool in_env = !RAGGED || j < N;  // a full scan covers the layout capacity
