@@ -23,8 +23,8 @@
 //              environment.  A pair left out is farther apart than its
 //              bounding circles for the rest of the list's life, so the list
 //              never changes results, and the list order does not depend on
-//              the skin.  Kernels compiled for a fixed entity count run
-//              the bounding tests without branches into a bit mask first.
+//              the skin.  Where a lane's (slot, offset) pairs fit 64 bits,
+//              the bounding tests run without branches into a bit mask first.
 //   contacts   per substep the group walks its list G pairs at a time through
 //              the exact narrow phase; hits are appended to a per-env buffer
 //              in list order (ballot + popc) and every lane adds the records
@@ -390,13 +390,15 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
       int n = 0;
       bool over = false;
-      // kernels compiled for a fixed entity count test every (slot, offset)
-      // without branches first; the generic kernel walks the offsets
-      constexpr bool kMask = NC > 0 && SLOTS * (NC / 2) <= 64;
+      // Lanes whose (slot, offset) pairs fit a 64-bit mask run the bounding
+      // tests without branches first (offsets up to N / 2: N is the
+      // compiled count, else at most the layout's G * SLOTS); the others
+      // walk the offsets
+      constexpr int D = NC > 0 ? NC / 2 : (G * SLOTS) / 2;
+      constexpr bool kMask = SLOTS * D <= 64;
       if (kMask && valid) {
-        // pass 1: the bounding-circle test of every (slot, offset), without
-        // branches, into a bit mask in (slot, offset) order
-        constexpr int D = NC > 0 ? NC / 2 : 1;
+        // pass 1: the bounding-circle test of every (slot, offset), into a
+        // bit mask in (slot, offset) order
         const int dmax = (N - 1) / 2;
         unsigned long long m = 0ull;
 #pragma unroll
@@ -410,17 +412,23 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
           const float ra = infl_a + p.skin;
           const bool a_moves = (ka & (kMovable | kRotatable)) != 0u;
           const int dlast = dmax + ((N % 2 == 0 && a < N / 2) ? 1 : 0);
-#pragma unroll
-          for (int d = 1; d <= D; ++d) {
+          auto circle = [&](int d) {
             const int b = a + d >= N ? a + d - N : a + d;
             const float4 bb = s_bp[VIDX(b, N, 8)];
             const uint32_t kb = __float_as_uint(bb.w);
             const float dx = ax_ - bb.x, dy = ay_ - bb.y;
             const float lim = ra + bb.z;
-            const bool pass = d <= dlast && (kb & kCollidable) &&
-                              (a_moves || (kb & (kMovable | kRotatable))) &&
-                              !(dx * dx + dy * dy > lim * lim);
-            m |= (unsigned long long)pass << (s * D + d - 1);
+            return (kb & kCollidable) && (a_moves || (kb & (kMovable | kRotatable))) &&
+                   !(dx * dx + dy * dy > lim * lim);
+          };
+          if constexpr (NC > 0) {
+#pragma unroll
+            for (int d = 1; d <= D; ++d)
+              m |= (unsigned long long)(d <= dlast && circle(d)) << (s * D + d - 1);
+          } else {
+#pragma unroll 4
+            for (int d = 1; d <= dlast; ++d)
+              m |= (unsigned long long)circle(d) << (s * D + d - 1);
           }
         }
         // pass 2: the exact line tests and the appends, in mask order; the
