@@ -28,6 +28,9 @@
  *    before the call returns unless stated.
  *  - All floating-point data is FP32, little-endian, C order.
  *  - A world is not thread-safe: serialise calls on one world.
+ *  - A world lives on the device that is current when it is created; make
+ *    that device current for every later call on it, and pass streams of
+ *    that device (the Python binding creates its tensors there).
  */
 #ifndef VMAS_H_
 #define VMAS_H_
