@@ -47,3 +47,29 @@ def test_lidar_full_config_sampled(vmas_lib, orc):
     sub = sc.subset(pick)
     ref = orc.lidar(sub, sub.init_state, 16, 1.0)
     assert (np.abs(got[pick] - ref) > 2e-5).mean() <= 5e-4
+
+
+def test_lidar_rays_parallel_to_box_faces_and_walls(vmas_lib, orc):
+    """Ray 0 of a caster with heading 0 is exactly (1, 0): against a box with
+    angle 0 it is parallel to two faces (the slab between them bounds it
+    only if it starts inside), and against a wall with angle 0 it never
+    crosses the segment.  Hand-worked: from (0, 0) the box face x = 0.4 is
+    hit at 0.4; from (0, 0.3), outside the box's y-slab |y| <= 0.2, the ray
+    misses everything and reads the range."""
+    from conftest import make_scene
+    from paper_2207_03530_b300 import World
+
+    act = scenes.MOVABLE | scenes.COLLIDABLE | scenes.ACTUATED
+    sc = make_scene([
+        dict(shape=scenes.SPHERE, x=0.0, y=0.0, a=0.05, flags=act),
+        dict(shape=scenes.SPHERE, x=0.0, y=0.3, a=0.05, flags=act),
+        dict(shape=scenes.BOX, x=0.5, y=0.0, a=0.2, b=0.4, m=5.0, flags=scenes.COLLIDABLE),
+        dict(shape=scenes.LINE, x=0.0, y=-0.5, a=1.0, flags=scenes.COLLIDABLE),
+    ], n_envs=3)
+    w = World(sc)
+    got = w.lidar(4, 2.0).cpu().numpy()
+    w.close()
+    ref = orc.lidar(sc, sc.init_state, 4, 2.0)
+    assert np.abs(got - ref).max() <= 2e-5
+    assert abs(got[0, 0, 0] - 0.4) <= 1e-6 and abs(ref[0, 0, 0] - 0.4) <= 1e-6
+    assert got[0, 1, 0] == 2.0 and ref[0, 1, 0] == 2.0
