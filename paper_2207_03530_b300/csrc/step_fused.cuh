@@ -390,22 +390,23 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
       // candidate list: pairs {a, a + d mod N}, each unordered pair once
       int n = 0;
       bool over = false;
-      // Lanes whose (slot, offset) pairs fit a 64-bit mask run the bounding
-      // tests without branches first (offsets up to N / 2: N is the
-      // compiled count, else at most the layout's G * SLOTS); the others
-      // walk the offsets
-      constexpr int D = NC > 0 ? NC / 2 : (G * SLOTS) / 2;
-      constexpr bool kMask = SLOTS * D <= 64;
+      // The bounding tests run without branches into 64-bit masks of
+      // (slot, offset) pairs -- offsets up to N / 2, where N is the compiled
+      // count or at most the layout's G * SLOTS -- whose set bits are then
+      // walked in (slot, offset) order.  One mask holds all slots where they
+      // fit; ragged kernels (whose envs hold no padding) use one mask per
+      // slot otherwise; the remaining kernels walk the offsets with a branch
+      // per test, which leaves a padded world's many inert partners early.
+      constexpr int D = NC > 0 ? NC / 2 : (G * SLOTS) / 2;  // at most 64
+      constexpr bool kOneMask = SLOTS * D <= 64;
+      constexpr bool kMask = kOneMask || RAGGED;
       if (kMask && valid) {
-        // pass 1: the bounding-circle test of every (slot, offset), into a
-        // bit mask in (slot, offset) order
         const int dmax = (N - 1) / 2;
-        unsigned long long m = 0ull;
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
+        auto pass1 = [&](int s) {
+          unsigned long long m = 0ull;
           const int a = lg + G * s;
           const uint32_t ka = kd[s];
-          if (a >= N || !(ka & kCollidable)) continue;
+          if (a >= N || !(ka & kCollidable)) return m;
           const float ax_ = x[s], ay_ = y[s];
           const float rb = s_mi[VIDX(a, N, 11)].z;
           const float infl_a = rb + 1e-5f * (rb + fabsf(ax_) + fabsf(ay_));
@@ -424,41 +425,55 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
           if constexpr (NC > 0) {
 #pragma unroll
             for (int d = 1; d <= D; ++d)
-              m |= (unsigned long long)(d <= dlast && circle(d)) << (s * D + d - 1);
+              m |= (unsigned long long)(d <= dlast && circle(d)) << (d - 1);
           } else {
 #pragma unroll 4
-            for (int d = 1; d <= dlast; ++d)
-              m |= (unsigned long long)circle(d) << (s * D + d - 1);
+            for (int d = 1; d <= dlast; ++d) m |= (unsigned long long)circle(d) << (d - 1);
           }
-        }
-        // pass 2: the exact line tests and the appends, in mask order; the
-        // published pose of a is its current position and inflated radius
-        while (m) {
-          const int bit = __ffsll((long long)m) - 1;
-          m &= m - 1ull;
-          const int s = bit / D, d = bit - s * D + 1;
-          const int a = lg + G * s;
-          const int b = a + d >= N ? a + d - N : a + d;
-          const float4 ba = s_bp[VIDX(a, N, 27)], bb = s_bp[VIDX(b, N, 28)];
-          const uint32_t ka = __float_as_uint(ba.w), kb = __float_as_uint(bb.w);
-          const float dx = ba.x - bb.x, dy = ba.y - bb.y;
-          if ((kb & 3u) == kLine && !(kb & kRotatable)) {
-            const float4 gb4 = s_ng[VIDX(b, N, 9)];
-            if (fabsf(dx * gb4.y - dy * gb4.x) > ba.z + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
-              continue;
+          return m;
+        };
+        // the exact line tests and the appends, in mask order; the published
+        // pose of a is its current position and inflated radius
+        auto walk = [&](unsigned long long m, int s0) {
+          while (m) {
+            const int bit = __ffsll((long long)m) - 1;
+            m &= m - 1ull;
+            const int s = kOneMask ? bit / D : s0;
+            const int d = kOneMask ? bit - s * D + 1 : bit + 1;
+            const int a = lg + G * s;
+            const int b = a + d >= N ? a + d - N : a + d;
+            const float4 ba = s_bp[VIDX(a, N, 27)], bb = s_bp[VIDX(b, N, 28)];
+            const uint32_t ka = __float_as_uint(ba.w), kb = __float_as_uint(bb.w);
+            const float dx = ba.x - bb.x, dy = ba.y - bb.y;
+            if ((kb & 3u) == kLine && !(kb & kRotatable)) {
+              const float4 gb4 = s_ng[VIDX(b, N, 9)];
+              if (fabsf(dx * gb4.y - dy * gb4.x) >
+                  ba.z + p.skin + 1e-5f * (fabsf(bb.x) + fabsf(bb.y)))
+                continue;
+            }
+            if ((ka & 3u) == kLine && !(ka & kRotatable)) {
+              const float4 ga = s_ng[VIDX(a, N, 7)];
+              if (fabsf(dx * ga.y - dy * ga.x) >
+                  bb.z + p.skin + 1e-5f * (fabsf(ba.x) + fabsf(ba.y)))
+                continue;
+            }
+            if (n < kLaneCand) {
+              const int lo = a < b ? a : b, hi = a < b ? b : a;
+              s_lc[VIDX(lg * kLaneCand + n, LC, 10)] = (uint16_t)(lo | (hi << 8));
+            } else {
+              over = true;
+            }
+            ++n;
           }
-          if ((ka & 3u) == kLine && !(ka & kRotatable)) {
-            const float4 ga = s_ng[VIDX(a, N, 7)];
-            if (fabsf(dx * ga.y - dy * ga.x) > bb.z + p.skin + 1e-5f * (fabsf(ba.x) + fabsf(ba.y)))
-              continue;
-          }
-          if (n < kLaneCand) {
-            const int lo = a < b ? a : b, hi = a < b ? b : a;
-            s_lc[VIDX(lg * kLaneCand + n, LC, 10)] = (uint16_t)(lo | (hi << 8));
-          } else {
-            over = true;
-          }
-          ++n;
+        };
+        if constexpr (kOneMask) {
+          unsigned long long m = 0ull;
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) m |= pass1(s) << (s * D);
+          walk(m, 0);
+        } else {
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) walk(pass1(s), s);
         }
       } else if (valid) {
         const int dmax = (N - 1) / 2;
