@@ -1,8 +1,7 @@
 // Closest points and penetration of one entity pair, FP32, device side.
 //
-// VMAS section 3, Eq. 2: the contact force acts along x_ij, "the relative
-// position between the closest points on the shapes of the two entities",
-// when |x_ij| <= d_min.  Each routine returns the signed gap
+// VMAS section 3, Eq. 2: the contact force acts along x_ij, the offset that
+// joins the two entities' closest surface points, when |x_ij| <= d_min.  Each routine returns the signed gap
 // g = |x_ij| - d_min, the unit normal n pointing from j towards i and the
 // lever terms ti = (p_i - x_i) x n, tj = (p_j - x_j) x n of the contact
 // points p_i, p_j (Eq. 3 torque, read as the signed 2D cross product).
