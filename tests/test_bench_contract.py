@@ -45,3 +45,29 @@ def test_native_arm_line(vmas_lib):
     assert d["gpu_launches"] == 5
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
+
+
+def _bench_module():
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_kernel_digest_ignores_comments_and_layout():
+    b = _bench_module()
+    code = "int f(int x) {\n  return x + 1;  // one more\n}\n"
+    same = "/* header */\nint f(int x) { return x + 1; }\n"
+    other = "int f(int x) { return x + 2; }\n"
+    assert b._code_text(code) == b._code_text(same)
+    assert b._code_text(code) != b._code_text(other)
+
+
+def test_step_kernel_profile_matches_the_code():
+    """The committed ncu summary of the step kernel was taken on the current
+    kernel code, so the bench reports its DRAM traffic (a changed kernel needs
+    a new capture)."""
+    traffic, figures = _bench_module()._recorded_profile()
+    assert traffic is not None and traffic > 0
+    assert figures["issue_active_pct"] > 0 and figures["warps_per_sm"] > 0
