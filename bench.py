@@ -810,6 +810,68 @@ def run_sweep(args):
     return 0
 
 
+def run_rollout(args):
+    """Open-loop rollout of the paper-scale workload (every step's actions
+    known ahead): args.steps world steps through vmas_rollout with 1, 2, 4, 8
+    and 16 steps per launch, the L2 flushed before each rollout.  The state
+    and the candidate lists stay on chip between the steps of a launch, so
+    the state crosses HBM once per launch; the final states are checked
+    bitwise equal across the tilings."""
+    import torch
+
+    from paper_2207_03530_b300 import World, build, scenes
+
+    build.build()
+    torch.cuda.set_device(0)
+    sc = scenes.paper_scene(args.envs, args.seed, substeps=args.substeps)
+    E, A = sc.n_envs, sc.n_actuated
+    T = max(args.steps, 16)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1000 + args.seed)
+    act = torch.rand((T, E, A, 3), device="cuda", generator=gen) * 2 - 1
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 126 << 20) or (126 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows, ref = [], None
+    for tile in (1, 2, 4, 8, 16):
+        w = World(sc)
+        w.set_rollout_tile(tile)
+        w.rollout(act[:tile])  # lazy kernel loading, off the clock
+        w.set_state(sc.init_state)
+        flush.zero_()
+        flush.sum()
+        torch.cuda.synchronize()
+        a.record()
+        w.rollout(act)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        st = w.state().cpu().numpy()
+        w.check()
+        w.close()
+        ref = st if ref is None else ref
+        rows.append({"steps_per_launch": tile, "us_per_step": 1e3 * ms / T,
+                     "env_steps_per_s": E * T / (ms / 1e3),
+                     "bitwise_equal_one_step_launches": bool(np.array_equal(
+                         st.view(np.uint32), ref.view(np.uint32)))})
+    best = max(rows, key=lambda r: r["env_steps_per_s"])
+    # per env-step: the useful action floats every step, the state read and
+    # written once per launch
+    state_b = 2 * ENTITIES * 6 * 4
+    b_env = B_ALG_PER_ENV - state_b + state_b / best["steps_per_launch"]
+    print(json.dumps({
+        "form": "rollout", "metric": "env-steps/s, open-loop rollout (world steps per launch)",
+        "value": best["env_steps_per_s"], "unit": UNIT, "steps_per_launch": best["steps_per_launch"],
+        "tilings": rows, "rollout_steps": T,
+        "roofline": _hbm_roofline(b_env, best["env_steps_per_s"],
+                                  "latency-bound like the one-step launch; the state "
+                                  "crosses HBM once per launch"),
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%d envs x (16 agent spheres + 4 boxes + 4 walls), %d substeps, "
+                               "%d-step rollout" % (E, args.substeps, T)}}), flush=True)
+    return 0
+
+
 def run_small(args):
     """Small workload: 32 envs x (4 agents + 2 landmarks),
     1 substep, 100 steps: latency per step, launched one by one and replayed
@@ -924,7 +986,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--form", choices=["plain", "adjoint", "lidar", "ragged", "surrogate",
-                                       "sweep", "small"],
+                                       "sweep", "small", "rollout"],
                     default="plain",
                     help="plain: the fused world step (the headline); adjoint: "
                          "differentiable rollout forward + backward")
@@ -957,6 +1019,8 @@ def main(argv=None):
         return run_sweep(args)
     if args.form == "small":
         return run_small(args)
+    if args.form == "rollout":
+        return run_rollout(args)
     return run_native(args)
 
 

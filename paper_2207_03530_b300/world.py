@@ -107,6 +107,12 @@ class World:
         _lib.check(self._L.vmas_rollout(self._handle(), _ptr(a) if a.numel() else None, T,
                                         _stream_handle(stream)))
 
+    def set_rollout_tile(self, steps_per_launch: int) -> None:
+        """World steps per kernel launch in rollout() (1..1024): state and
+        candidate lists stay on chip between them; results are bitwise the
+        same for any value."""
+        _lib.check(self._L.vmas_world_set_rollout_tile(self._handle(), int(steps_per_launch)))
+
     def rollout_host(self, actions, states_out=None, stream=None) -> torch.Tensor:
         """len(actions) steps between host buffers: actions [T, E, A, 3] (host;
         pinned keeps the uploads asynchronous), every step's state into
