@@ -874,8 +874,9 @@ def run_rollout(args):
 
 def run_small(args):
     """Small workload: 32 envs x (4 agents + 2 landmarks),
-    1 substep, 100 steps: latency per step, launched one by one and replayed
-    from a CUDA graph captured around the same 100 launches.  A roofline
+    1 substep, 100 steps: latency per step, launched one by one, replayed
+    from a CUDA graph captured around the same 100 launches, and (when the
+    actions are known ahead) all 100 steps in one launch.  A roofline
     fraction at 4.6 KB of state is meaningless; it is reported, labelled
     latency-bound."""
     import torch
@@ -918,6 +919,17 @@ def run_small(args):
     b.record()
     torch.cuda.synchronize()
     graph_us = a.elapsed_time(b) * 1e3 / (reps * T)
+    # the same 100 steps as one launch (an open-loop rollout: every step's
+    # actions known ahead)
+    w.set_rollout_tile(T)
+    w.rollout(act)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        w.rollout(act)
+    b.record()
+    torch.cuda.synchronize()
+    one_launch_us = a.elapsed_time(b) * 1e3 / (reps * T)
     w.check()
     w.close()
     peak, peak_kind = _peaks()
@@ -927,6 +939,7 @@ def run_small(args):
         "form": "small", "metric": "us per step (latency), 100-step rollout",
         "value": graph_us, "unit": "us/step", "higher_is_better": False,
         "eager_us_per_step": eager_us, "graph_us_per_step": graph_us,
+        "one_launch_rollout_us_per_step": one_launch_us,
         "env_steps_per_s_graph": 32 / (graph_us / 1e6),
         "roofline": {"bound": "latency", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "bytes_per_env_step": b_env,
