@@ -260,9 +260,16 @@ def cpu_baseline(n_envs, substeps, seed, budget_s=20.0):
     t0 = time.perf_counter()
     oracle.step(sample, sample.init_state, act, threads=cores)
     dt = time.perf_counter() - t0
+    # one thread, on the probe sample
+    act1 = scenes.make_actions(probe, 1, seed)
+    t1 = time.perf_counter()
+    oracle.step(probe, probe.init_state, act1, threads=1)
+    single = probe.n_envs / (time.perf_counter() - t1)
     return {"value": E_s * T_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d of %d envs x %d steps of the same workload, FP64, %.1f s"
-                      % (E_s, n_envs, T_s, dt)}
+                      % (E_s, n_envs, T_s, dt),
+            "single_thread_value": single,
+            "single_thread_sample": "first %d envs x 1 step, 1 thread" % probe.n_envs}
 
 
 def run_reference(args):
