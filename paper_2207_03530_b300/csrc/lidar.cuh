@@ -87,12 +87,16 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
   float2 *s_half = reinterpret_cast<float2 *>(s_pose + p.N);   // [N] by list slot
   uint8_t *s_kind = reinterpret_cast<uint8_t *>(s_half + p.N);  // [N] by entity
   __shared__ int s_ent[VMAS_LIDAR_MAX_ENTITIES];    // entity of each list slot
+  __shared__ int s_slot[VMAS_LIDAR_MAX_ENTITIES];   // list slot of each entity (-1: none)
   __shared__ int s_agent[VMAS_LIDAR_MAX_ENTITIES];  // k-th actuated entity
   __shared__ int s_start[4];                        // list starts: spheres, boxes, lines, end
   __shared__ int s_nact;
   const int e = blockIdx.x;
   const size_t eb = (size_t)e * p.N;
-  for (int i = threadIdx.x; i < p.N; i += blockDim.x) s_kind[i] = p.kind[eb + i];
+  for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+    s_kind[i] = p.kind[eb + i];
+    s_slot[i] = -1;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
     // the collidable bodies, grouped by shape (each group in entity order),
@@ -107,7 +111,10 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
         const uint32_t kd = i < p.N ? s_kind[i] : 0u;
         const bool in = i < p.N && (kd & 3u) == (uint32_t)sh && (kd & kCollidable);
         const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) s_ent[n + __popc(m & lt)] = i;
+        if (in) {
+          s_ent[n + __popc(m & lt)] = i;
+          s_slot[i] = n + __popc(m & lt);
+        }
         n += __popc(m);
       }
     }
@@ -132,9 +139,8 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
     float c = 1.f, s = 0.f;
     if ((s_kind[i] & 3u) != kSphere) body_axes(p.th[eb + i], c, s);
     const bool sphere = (s_kind[i] & 3u) == kSphere;
-    // a sphere's slot holds {x, y, r, entity}: one load per test
-    s_pose[q] = make_float4(p.px[eb + i], p.py[eb + i], sphere ? pr.z : c,
-                            sphere ? __int_as_float(i) : s);
+    // a sphere's slot holds {x, y, r, -}: one load per test
+    s_pose[q] = make_float4(p.px[eb + i], p.py[eb + i], sphere ? pr.z : c, sphere ? 0.f : s);
     s_half[q] = make_float2(pr.z, pr.w);
   }
   __syncthreads();
@@ -146,6 +152,7 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
     float best = p.range;
     if (k < nact) {
       const int i = s_agent[k];
+      const int self = s_slot[i];  // the caster's own slot is skipped
       const float ox = p.px[eb + i], oy = p.py[eb + i];
       float dx, dy;
       body_axes(p.th[eb + i] + step * (float)r, dx, dy);
@@ -153,17 +160,17 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
       for (int q = 0; q < b0; ++q) {
         const float4 b = s_pose[q];
         const float t = ray_sphere(ox, oy, dx, dy, b);
-        best = fminf(best, __float_as_int(b.w) == i ? inf : t);  // not the caster itself
+        best = fminf(best, q == self ? inf : t);
       }
 #pragma unroll 2
       for (int q = b0; q < l0; ++q) {
         const float t = ray_box(ox, oy, dx, dy, s_pose[q], s_half[q]);
-        best = fminf(best, s_ent[q] == i ? inf : t);
+        best = fminf(best, q == self ? inf : t);
       }
 #pragma unroll 2
       for (int q = l0; q < end; ++q) {
         const float t = ray_line(ox, oy, dx, dy, s_pose[q], s_half[q].x);
-        best = fminf(best, s_ent[q] == i ? inf : t);
+        best = fminf(best, q == self ? inf : t);
       }
     }
     p.out[((size_t)e * p.A + k) * p.R + r] = best;
