@@ -51,6 +51,27 @@ def test_ragged_matches_oracle(vmas_lib, orc, seed):
     rw.close()
 
 
+@pytest.mark.parametrize("lanes", [[4, 4, 8, 16, 32], [8, 8, 16, 32, 32], [8, 16, 32, 32, 32]])
+def test_every_lane_choice_matches_oracle(vmas_lib, orc, lanes):
+    """Every (lanes, entities per lane) kernel a size class can run -- the
+    three tunings cover them all: 4 or 8 lanes for the 8-entity class, 4, 8
+    or 16 for 16, 8, 16 or 32 for 32, 16 or 32 for 64, 32 for 128 -- against
+    the FP64 oracle."""
+    sc, counts = scenes.ragged_scene(300, 4)
+    rw = _ragged(sc, counts)
+    assert (rw.class_envs > 0).all()
+    rw.set_tuning(lanes, 1)
+    act = scenes.make_actions(sc, 2, 4)
+    pact = torch.from_numpy(_packed_actions(rw, sc, act)).cuda()
+    for t in range(2):
+        rw.step(pact[t])
+    got, sel = _unpack_state(rw.state().cpu().numpy(), counts, sc.n_entities)
+    ref = orc.step(sc, sc.init_state, act, threads=8)
+    assert normwise_err(got[sel], ref[sel]).max() <= TOL
+    rw.check()
+    rw.close()
+
+
 def test_ragged_matches_padded_world(vmas_lib):
     from paper_2207_03530_b300 import World
 
