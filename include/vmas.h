@@ -253,7 +253,10 @@ int vmas_ragged_autotune(vmas_ragged *world, const float *d_actions, int32_t n_s
  * [n_rays] (device) receives the distance to the first entry into a sphere,
  * box or line segment, 0 when the ray starts inside one, max_range when it
  * meets none (also for action rows an env does not use).  A ray exactly
- * parallel to a segment misses it.  Enqueues one kernel on `stream`. */
+ * parallel to a segment misses it.  Distances are FP32 within about 1e-7 of
+ * a unit range (fast reciprocal and reciprocal square root); a ray that
+ * grazes a body within that margin may read hit or miss.  Enqueues one
+ * kernel on `stream`. */
 int vmas_lidar(vmas_world *world, int32_t n_rays, float max_range, float *d_out, void *stream);
 
 /* ---- Differentiable rollout (sphere worlds) -----------------------------
