@@ -21,6 +21,7 @@ method) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import math
@@ -76,6 +77,30 @@ def _hbm_roofline(bytes_per_env_step, env_steps_per_s, note):
 # minimum; and of one ray direction (angle, sin/cos by the library's own
 # reduction and series)
 LIDAR_OPS = {"sphere": 12, "box": 28, "line": 13, "ray": 22}
+
+
+def _issue_roofline(figures, avg_ms, clocks):
+    """The instruction-issue bound beside the HBM one: the launch's warp
+    instructions (ncu, recorded for these kernel sources) over the SMs' issue
+    rate (4 schedulers per SM, one warp instruction per cycle each, at the
+    median SM clock sampled during the timed region), against the measured
+    mean launch time."""
+    if not figures or not figures.get("warp_inst_per_launch"):
+        return None
+    try:
+        import torch
+
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if not mhz:
+        return None
+    inst = figures["warp_inst_per_launch"]
+    floor_us = inst / (sms * 4 * mhz * 1e6) * 1e6
+    return {"warp_inst_per_launch": inst, "sms": sms, "sm_mhz": mhz,
+            "issue_floor_us": floor_us, "measured_us": avg_ms * 1e3,
+            "frac": floor_us / (avg_ms * 1e3)}
 
 
 def _alu_roofline(ops_per_unit, units_per_s, note):
@@ -145,6 +170,8 @@ def _recorded_profile():
         "issue_active_pct": pct("smsp__issue_active", r"([\d.]+) %"),
         "fma_pipe_pct": pct("pipes (of active)", r"FMA ([\d.]+) %"),
         "warps_per_sm": pct("sm__warps_active", r"([\d.]+) warps"),
+        "warp_inst_per_launch": (lambda v: v * 1e6 if v is not None else None)(
+            pct("smsp__issue_active", r"smsp__inst_executed: ([\d.]+) M")),
         "binds": "latency: neither HBM nor the FP32 pipes are saturated",
     }
     return traffic, figures
@@ -212,7 +239,10 @@ class ClockSampler:
             time.sleep(self.period)
 
     def __enter__(self):
+        # re-entrant: each `with` block adds its samples to the same record,
+        # so a form can sample only its timed loops
         if self.ok:
+            self._stop = threading.Event()
             self._t = threading.Thread(target=self._run, daemon=True)
             self._t.start()
         return self
@@ -221,6 +251,7 @@ class ClockSampler:
         if self._t:
             self._stop.set()
             self._t.join()
+            self._t = None
 
     def summary(self):
         if not self.ok:
@@ -454,8 +485,12 @@ def run_native(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
+                         "traffic_source": ("ncu capture of these kernel sources, read from the "
+                                            "committed summary (not measured in this run)"
+                                            if traffic is not None else None),
                          "bytes_per_env_step": B_ALG_PER_ENV, "kernel": "world_step_kernel",
-                         "ncu": ncu_figures},
+                         "ncu": ncu_figures,
+                         "issue": _issue_roofline(ncu_figures, avg_ms, clocks)},
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
@@ -498,12 +533,14 @@ def run_adjoint(args):
     for _ in range(args.warmup):
         fwd_bwd()
     torch.cuda.synchronize()
+    cs = ClockSampler(torch.device("cuda", 0))
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(args.steps):
-        grad = fwd_bwd()
-    t1.record()
-    torch.cuda.synchronize()
+    with cs:
+        t0.record()
+        for _ in range(args.steps):
+            grad = fwd_bwd()
+        t1.record()
+        torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / args.steps
     # the same forward + backward captured once into a CUDA graph (autograd
     # included) and replayed: no host work per iteration
@@ -525,11 +562,12 @@ def run_adjoint(args):
         torch.cuda.synchronize()
         if not torch.equal(static_a.grad, grad):
             raise RuntimeError("graphed gradient differs")
-        t0.record()
-        for _ in range(args.steps):
-            g.replay()
-        t1.record()
-        torch.cuda.synchronize()
+        with cs:
+            t0.record()
+            for _ in range(args.steps):
+                g.replay()
+            t1.record()
+            torch.cuda.synchronize()
         graph_ms = t0.elapsed_time(t1) / args.steps
     except Exception as exc:  # capture is an optional extra measurement
         print("graph capture of the adjoint skipped: %s" % exc, file=sys.stderr)
@@ -564,9 +602,10 @@ def run_adjoint(args):
         "graphed_value": E * T / (graph_ms / 1e3) if graph_ms else None,
         "graphed_ms_per_rollout": graph_ms,
         "roofline": _hbm_roofline(b_env, E * T / (ms / 1e3),
-                                  "latency-bound (profiles/diff_backward_kernel_4k.md)"),
+                                  "latency-bound (ncu: diff_backward_kernel)"),
         "plain_step_value": E * T / (plain_ms / 1e3), "rollout_steps": T, "ckpt_every": K,
-        "grad_rel_err_vs_fp64_oracle": err, "dtype": "f32", "data": "synthetic",
+        "grad_rel_err_vs_fp64_oracle": err, "clocks": cs.summary(),
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": "%d envs x (8 agent spheres + 2 landmarks), 3 substeps, %d steps"
                                % (E, T)}}), flush=True)
     return 0
@@ -599,11 +638,13 @@ def run_ragged(args):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, args.steps // 100)
-    a.record()
-    for _ in range(reps):
-        rw.rollout(act)
-    b.record()
-    torch.cuda.synchronize()
+    cs = ClockSampler(torch.device("cuda", 0))
+    with cs:
+        a.record()
+        for _ in range(reps):
+            rw.rollout(act)
+        b.record()
+        torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
     value = E * T / (ms / 1e3)
     rw.close()
@@ -629,16 +670,17 @@ def run_ragged(args):
         "form": "ragged", "metric": "env-steps/s, ragged rollout (CUDA graph, autotuned)",
         "value": value, "unit": UNIT, "ms_per_rollout": ms, "rollout_steps": T,
         "roofline": _hbm_roofline(b_env, value, "latency-bound size classes "
-                                  "(profiles/world_step_ragged_class128_8k.md)"),
+                                  "(ncu: the 128-entity class)"),
         "entities": int(counts.sum()), "envs": E, "lanes_per_class": [int(x) for x in lanes],
-        "steps_per_launch": tile, "padded_regular_world_value": padded, "dtype": "f32",
+        "steps_per_launch": tile, "padded_regular_world_value": padded, "clocks": cs.summary(),
+        "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "%d envs x (2-64 agents + 0-8 boxes + 0-4 walls), 5 substeps, "
                                "%d-step graph rollout" % (E, T)}}), flush=True)
     return 0
 
 
-def _sur_rollouts(sur, sc, act, runs, World):
+def _sur_rollouts(sur, sc, act, runs, World, cs=None):
     """The same 50-step rollout from sc's start with the plain step and with
     the surrogate in each inference mode; per-step CUDA events (median after
     3 steps), agent positions kept for the error."""
@@ -653,15 +695,16 @@ def _sur_rollouts(sur, sc, act, runs, World):
         nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
         pos = torch.empty((T, E, 16, 2), device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T)]
-        for t in range(T):
-            ev[2 * t].record()
-            if mode:
-                sur.step(w, act[t], n_fallback=nfb[t:t + 1])
-            else:
-                w.step(act[t])
-            ev[2 * t + 1].record()
-            pos[t] = w.state()[:, :16, :2]
-        torch.cuda.synchronize()
+        with (cs if cs is not None else contextlib.nullcontext()):
+            for t in range(T):
+                ev[2 * t].record()
+                if mode:
+                    sur.step(w, act[t], n_fallback=nfb[t:t + 1])
+                else:
+                    w.step(act[t])
+                ev[2 * t + 1].record()
+                pos[t] = w.state()[:, :16, :2]
+            torch.cuda.synchronize()
         ms = [ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(T)]
         out[name] = dict(pos=pos, ms=statistics.median(ms[3:]), nfb=nfb.cpu().numpy(),
                          value=E / (statistics.median(ms[3:]) / 1e3))
@@ -700,6 +743,7 @@ def run_surrogate(args):
     gen.manual_seed(args.seed + 5)
     act = torch.rand((T, E, 16, 3), device="cuda", generator=gen) * 2 - 1
     res = {}
+    cs = ClockSampler(torch.device("cuda", 0))
     for S, sc in ((5, sc5), (1, sc1)):
         sur = Surrogate(max(E, E_train), seed=args.seed)
         train = train_on_plain_step(sur, E_train, args.train_steps, args.lr, args.seed + 1000,
@@ -707,9 +751,9 @@ def run_surrogate(args):
         runs = [("plain", False), ("surrogate", "fused"), ("surrogate_layered", "layered")]
         if S == 5:
             runs.append(("plain_s1", None))
-        out = _sur_rollouts(sur, sc, act, [r for r in runs if r[1] is not None], World)
+        out = _sur_rollouts(sur, sc, act, [r for r in runs if r[1] is not None], World, cs)
         if S == 5:
-            out.update(_sur_rollouts(sur, sc1, act, [("plain_s1", False)], World))
+            out.update(_sur_rollouts(sur, sc1, act, [("plain_s1", False)], World, cs))
         sur.close()
         ref = out["plain"]["pos"]
         e, e_end = _pos_err(out["surrogate"]["pos"], ref)
@@ -741,7 +785,7 @@ def run_surrogate(args):
             "frac": tflops / tpeak, "peak_source": "%s bf16_tflops (burst)" % tkind,
             "flop_per_env": flop_env, "edges_per_env": edges,
             "note": "instruction-issue-bound on the GELUs, not on the tensor pipe "
-                    "(profiles/sur_fused_kernel_16k.md)"}
+                    "(ncu: sur_fused_kernel)"}
     print(json.dumps({
         "form": "surrogate",
         "metric": "env-steps/s, learned surrogate step (with plain-step fallback)",
@@ -754,7 +798,7 @@ def run_surrogate(args):
         "plain_s1_mean_pos_err_50": r5["plain_s1_mean_pos_err_50"],
         "plain_s1_pos_err_at_50": r5["plain_s1_pos_err_at_50"],
         "fallback_envs_per_step": r5["fallback_envs_per_step"], "train": r5["train"],
-        "substeps_1": {k: v for k, v in res[1].items()},
+        "substeps_1": {k: v for k, v in res[1].items()}, "clocks": cs.summary(),
         "dtype": "bf16 network / f32 fallback", "data": "synthetic",
         "config": {"workload": "%d envs x (16 agent spheres + 4 walls), 5 (and 1) substeps, "
                                "%d steps" % (E, T)}}), flush=True)
@@ -784,6 +828,7 @@ def run_sweep(args):
     peak, peak_kind = _peaks()
     points = []
     steps = min(args.steps, 50)
+    cs = ClockSampler(dev)
     for E in (1000, 4000, 16000, 30000, 131072, 262144):
         sc = scenes.paper_scene(E, args.seed, substeps=args.substeps)
         w = World(sc)
@@ -791,15 +836,16 @@ def run_sweep(args):
         gen.manual_seed(1000 + args.seed)
         act = torch.rand((3 + steps, E, sc.n_actuated, 3), device=dev, generator=gen) * 2 - 1
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
-        for t in range(3 + steps):
-            flush.zero_()
-            flush.sum()
-            if t >= 3:
-                ev[2 * (t - 3)].record()
-            w.step(act[t])
-            if t >= 3:
-                ev[2 * (t - 3) + 1].record()
-        torch.cuda.synchronize()
+        with cs:
+            for t in range(3 + steps):
+                flush.zero_()
+                flush.sum()
+                if t >= 3:
+                    ev[2 * (t - 3)].record()
+                w.step(act[t])
+                if t >= 3:
+                    ev[2 * (t - 3) + 1].record()
+            torch.cuda.synchronize()
         w.check()
         ms = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps))
         gbs = B_ALG_PER_ENV * E / (ms / 1e3) / 1e9
@@ -810,7 +856,7 @@ def run_sweep(args):
         del act
     print(json.dumps({"form": "sweep", "metric": "env-steps/s vs env count, plain step",
                       "unit": UNIT, "peak_gbs": peak, "peak_source": peak_kind,
-                      "l2_mb": l2 / 1e6, "points": points,
+                      "l2_mb": l2 / 1e6, "points": points, "clocks": cs.summary(),
                       "config": {"workload": "paper-scale scene (16 spheres + 4 boxes + 4 walls), "
                                              "5 substeps, L2 flushed before every step"}}),
           flush=True)
@@ -840,6 +886,7 @@ def run_rollout(args):
     flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device="cuda")
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows, ref = [], None
+    cs = ClockSampler(torch.device("cuda", 0))
     for tile in (1, 2, 4, 8, 16):
         w = World(sc)
         w.set_rollout_tile(tile)
@@ -848,10 +895,11 @@ def run_rollout(args):
         flush.zero_()
         flush.sum()
         torch.cuda.synchronize()
-        a.record()
-        w.rollout(act)
-        b.record()
-        torch.cuda.synchronize()
+        with cs:
+            a.record()
+            w.rollout(act)
+            b.record()
+            torch.cuda.synchronize()
         ms = a.elapsed_time(b)
         st = w.state().cpu().numpy()
         w.check()
@@ -869,7 +917,7 @@ def run_rollout(args):
     print(json.dumps({
         "form": "rollout", "metric": "env-steps/s, open-loop rollout (world steps per launch)",
         "value": best["env_steps_per_s"], "unit": UNIT, "steps_per_launch": best["steps_per_launch"],
-        "tilings": rows, "rollout_steps": T,
+        "tilings": rows, "rollout_steps": T, "clocks": cs.summary(),
         "roofline": _hbm_roofline(b_env, best["env_steps_per_s"],
                                   "latency-bound like the one-step launch; the state "
                                   "crosses HBM once per launch"),
@@ -907,12 +955,14 @@ def run_small(args):
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 10
-    a.record()
-    for _ in range(reps):
-        for t in range(T):
-            w.step(act[t])
-    b.record()
-    torch.cuda.synchronize()
+    cs = ClockSampler(torch.device("cuda", 0))
+    with cs:
+        a.record()
+        for _ in range(reps):
+            for t in range(T):
+                w.step(act[t])
+        b.record()
+        torch.cuda.synchronize()
     eager_us = a.elapsed_time(b) * 1e3 / (reps * T)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
@@ -920,22 +970,24 @@ def run_small(args):
             w.step(act[t])
     g.replay()
     torch.cuda.synchronize()
-    a.record()
-    for _ in range(reps):
-        g.replay()
-    b.record()
-    torch.cuda.synchronize()
+    with cs:
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
     graph_us = a.elapsed_time(b) * 1e3 / (reps * T)
     # the same 100 steps as one launch (an open-loop rollout: every step's
     # actions known ahead)
     w.set_rollout_tile(T)
     w.rollout(act)
     torch.cuda.synchronize()
-    a.record()
-    for _ in range(reps):
-        w.rollout(act)
-    b.record()
-    torch.cuda.synchronize()
+    with cs:
+        a.record()
+        for _ in range(reps):
+            w.rollout(act)
+        b.record()
+        torch.cuda.synchronize()
     one_launch_us = a.elapsed_time(b) * 1e3 / (reps * T)
     w.check()
     w.close()
@@ -947,7 +999,7 @@ def run_small(args):
         "value": graph_us, "unit": "us/step", "higher_is_better": False,
         "eager_us_per_step": eager_us, "graph_us_per_step": graph_us,
         "one_launch_rollout_us_per_step": one_launch_us,
-        "env_steps_per_s_graph": 32 / (graph_us / 1e6),
+        "env_steps_per_s_graph": 32 / (graph_us / 1e6), "clocks": cs.summary(),
         "roofline": {"bound": "latency", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "bytes_per_env_step": b_env,
                      "note": "4.6 KB of state: launch- and latency-bound"},
@@ -971,11 +1023,13 @@ def run_lidar(args):
         w.lidar(32, 1.0)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        w.lidar(32, 1.0)
-    b.record()
-    torch.cuda.synchronize()
+    cs = ClockSampler(torch.device("cuda", 0))
+    with cs:
+        a.record()
+        for _ in range(args.steps):
+            w.lidar(32, 1.0)
+        b.record()
+        torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
     rays = args.envs * sc.n_actuated * 32
     w.close()
@@ -991,9 +1045,8 @@ def run_lidar(args):
                       "unit": "rays/s", "ms_per_call": ms, "env_scans_per_s": args.envs / (ms / 1e3),
                       "roofline": _alu_roofline(ops, value, "instruction-issue-bound: 88 % of "
                                                 "issue slots, ALU pipe 68 %, 32 warp "
-                                                "instructions per ray "
-                                                "(profiles/lidar_kernel_30k.md)"),
-                      "dtype": "f32", "data": "synthetic",
+                                                "instructions per ray (ncu: lidar_kernel)"),
+                      "clocks": cs.summary(), "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "%d envs x 20 agents x 32 rays vs 24 bodies"
                                              % args.envs}}), flush=True)
     return 0

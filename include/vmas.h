@@ -106,9 +106,13 @@ typedef struct {
   const float *init_state;/* [n_envs][n_entities][6]: x y vx vy theta omega */
 } vmas_world_desc;
 
-/* Create a world on the current CUDA device: validates the description,
- * allocates the device state and parameter planes and copies them in
- * (synchronously).  On failure *out is NULL and nothing is leaked. */
+/* Create a world on the current CUDA device (the scenario's make_world of
+ * section 3, "Scenario": it creates the entities and spawns them; the
+ * entity attributes are those of section 3, "Core": shape, mass, movable /
+ * rotatable / collidable, maximum speed, and the world's delta t, damping
+ * zeta and gravity g).  Validates the description, allocates the device
+ * state and parameter planes and copies them in (synchronously).  On failure
+ * *out is NULL and nothing is leaked. */
 int vmas_world_create(const vmas_world_desc *desc, vmas_world **out);
 
 /* Free a world and its device memory (waits for the device).  NULL is a
@@ -172,7 +176,10 @@ int vmas_rollout_host(vmas_world *world, const float *h_actions, int32_t n_steps
                       void *stream);
 
 /* Read the state into caller memory as [n_envs][n_entities][6]
- * (x y vx vy theta omega).  out_is_device != 0: `out` is device memory and
+ * (x y vx vy theta omega): the vectorized state (x_i, xdot_i, theta_i,
+ * thetadot_i) of every entity in every environment (section 3, "Core"),
+ * returned as one batched tensor as section 3's "Interface" returns its
+ * outputs for all environments.  out_is_device != 0: `out` is device memory and
  * the copy is enqueued on `stream`.  out_is_device == 0: `out` is host
  * memory; the call waits for `stream` and then returns VMAS_EDEVICE if a
  * kernel has raised the device error word since the last check. */
@@ -186,13 +193,17 @@ int vmas_state(vmas_world *world, float *out, int32_t out_is_device, void *strea
 int vmas_set_state(vmas_world *world, const float *state, int32_t state_is_device,
                    const uint8_t *env_mask, void *stream);
 
-/* First-substep contact mask of the current state: d_mask is device uint8
- * [n_envs][n_pairs], pairs (i < j) in row-major order; 1 where the pair is
- * active (both collidable, one movable or rotatable) and gap <= 0 with a
- * defined normal.  Does not change the state. */
+/* First-substep contact mask of the current state: the case split of Eq. 2
+ * (section 3), i.e. which pairs have |x_ij| <= d_min and so a non-zero
+ * environmental force f^e_ij.  d_mask is device uint8 [n_envs][n_pairs],
+ * pairs (i < j) in row-major order; 1 where the pair is active (both
+ * collidable, one movable or rotatable) and gap <= 0 with a defined normal.
+ * Does not change the state. */
 int vmas_debug_pairs(vmas_world *world, uint8_t *d_mask, void *stream);
 
-/* The canonical pair list into host arrays of n_pairs elements. */
+/* The canonical pair list into host arrays of n_pairs elements: the pairs
+ * (i, j), i < j, row-major, over which Eq. 1's sum over j in N \ {i} runs
+ * (each unordered pair once, its force applied to both with opposite signs). */
 int vmas_pair_table(const vmas_world *world, int32_t *pair_i, int32_t *pair_j);
 
 /* Wait for `stream` and return VMAS_EDEVICE (clearing the word) if a kernel
@@ -304,10 +315,10 @@ int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void
  * calls are not allowed.  vmas_step_noalloc is one world step (the same
  * kernel as vmas_step) over buffers the caller owns; it allocates nothing.
  *
- * Its only scratch is a fixed 16 KiB array in the library's device memory
- * (the pair table for up to VMAS_NOALLOC_MAX_ENTITIES entities plus a status
- * word), present on every device that loads the library until the process
- * exits.  The first call on a device looks up that array's device address
+ * Its only scratch is a fixed 16,640-byte array in the library's device
+ * memory (a 16,384-byte pair table for up to VMAS_NOALLOC_MAX_ENTITIES
+ * entities plus a 256-byte status block), present on every device that
+ * loads the library until the process exits.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the array and rewrites it, so calls that can overlap on
  * the GPU (on different streams) race: serialise them.
@@ -320,7 +331,8 @@ int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void
  * status (optional, device int32): the call ORs VMAS_DEVERR_* bits into it;
  * the caller clears it.  Entities are checked on the device: an invalid one
  * is left inert and raises VMAS_DEVERR_BAD_ENTITY.  Returns VMAS_EINVAL
- * (before enqueuing anything) when n_entities > VMAS_NOALLOC_MAX_ENTITIES. */
+ * (before enqueuing anything) when n_entities > VMAS_NOALLOC_MAX_ENTITIES or a
+ * world parameter is out of range or not finite. */
 #define VMAS_NOALLOC_MAX_ENTITIES 128
 typedef struct {
   int32_t n_envs, n_entities, n_actuated, substeps;

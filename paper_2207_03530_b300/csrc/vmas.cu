@@ -344,6 +344,10 @@ int vmas_step_noalloc(const vmas_step_noalloc_args *a, void *stream) {
       !(a->contact_force >= 0) || !(a->max_speed >= 0) || !(a->skin >= 0) ||
       !std::isfinite(a->skin))
     return fail(VMAS_EINVAL, "dt, contact_margin must be > 0; contact_force, max_speed, skin >= 0");
+  if (!std::isfinite(a->drag) || !std::isfinite(a->gx) || !std::isfinite(a->gy) ||
+      !std::isfinite(a->contact_margin) || !std::isfinite(a->contact_force) ||
+      !std::isfinite(a->max_speed))
+    return fail(VMAS_EINVAL, "drag, gravity and the contact and speed parameters must be finite");
   const size_t EN = (size_t)a->n_envs * a->n_entities;
   if (EN && (!a->state || !a->shape || !a->flags || !a->size_a || !a->size_b || !a->mass ||
              !a->inertia))

@@ -166,3 +166,17 @@ def test_no_conditionally_skipped_warp_votes():
             if pat.search(line.split("//")[0]):
                 bad.append("%s:%d: %s" % (os.path.basename(f), n, line.strip()))
     assert not bad, bad
+
+
+@pytest.mark.parametrize("field", ["drag", "gx", "gy", "contact_force", "max_speed"])
+@pytest.mark.parametrize("value", [float("nan"), float("inf")])
+def test_noalloc_step_rejects_non_finite_parameters(L, field, value):
+    """vmas_step_noalloc checks its world parameters on the host, as
+    vmas_world_create does, before it enqueues anything (no GPU needed)."""
+    a = _lib.StepNoallocArgs()
+    a.n_envs, a.n_entities, a.n_actuated, a.substeps = 4, 6, 0, 1
+    a.dt, a.contact_margin, a.contact_force = 0.1, 1e-3, 100.0
+    setattr(a, field, value)
+    rc = L.vmas_step_noalloc(ctypes.byref(a), None)
+    assert rc == _lib.VMAS_EINVAL
+    assert "finite" in L.vmas_last_error().decode() or field in L.vmas_last_error().decode()

@@ -40,9 +40,31 @@ def _args(sc, skin, state, actions, status, keep):
         state.data_ptr(), actions.data_ptr(), status.data_ptr())
 
 
+def _padded_ragged(n_envs, seed, n_total, max_agents):
+    """A mixed scene of spheres, boxes and walls (the ragged generator's), every
+    env padded with inert entities to exactly n_total entities."""
+    sc, _ = scenes.ragged_scene(n_envs, seed, max_agents=max_agents)
+    pad = n_total - sc.n_entities
+    assert pad >= 0
+    kw = {}
+    for key, fill in (("shape", 0), ("flags", 0), ("size_a", 0.05), ("size_b", 0.0),
+                      ("mass", 1.0), ("inertia", 0.0)):
+        a = getattr(sc, key)
+        kw[key] = np.ascontiguousarray(np.concatenate(
+            [a, np.full((sc.n_envs, pad), fill, a.dtype)], axis=1))
+    kw["init_state"] = np.ascontiguousarray(np.concatenate(
+        [sc.init_state, np.zeros((sc.n_envs, pad, 6), np.float32)], axis=1))
+    import dataclasses
+
+    return dataclasses.replace(sc, n_entities=n_total, **kw)
+
+
 @pytest.mark.parametrize("make", [lambda: scenes.paper_scene(203, 5, dense=True),
-                                  lambda: scenes.small_scene(37, 2, dense=True)],
-                         ids=["paper-203envs", "small-37envs"])
+                                  lambda: scenes.small_scene(37, 2, dense=True),
+                                  lambda: _padded_ragged(45, 11, 48, 36),
+                                  lambda: _padded_ragged(21, 12, 128, 116)],
+                         ids=["paper-203envs", "small-37envs", "mixed-48ent-45envs",
+                              "mixed-128ent-21envs"])
 def test_noalloc_step_matches_regular_step_twice(vmas_lib, make):
     from paper_2207_03530_b300 import World
 
