@@ -21,8 +21,16 @@ y = +-1).  It is a per-agent message-passing network:
   prediction: x' = x + 0.01 out0..1, v' = v + 0.1 out2..3.
 
 bf() rounds to bfloat16 (nearest even); weights are held in bfloat16, biases
-in FP32; gelu(z) = z (1 + erf(z / sqrt 2)) / 2.  The rounding points mirror
-the CUDA kernels so the two agree to accumulation order.
+in FP32; gelu(z) = z (1 + erf(z / sqrt 2)) / 2 = z Phi(z).  The rounding
+points are part of the network's definition (bfloat16 weights and
+activations feeding every matrix product, FP32-or-better accumulation); any
+implementation of the network rounds at them, and this reference evaluates
+everything else in FP64.
+
+Pins (tests/test_oracle_surrogate.py): the forward pass against a network
+worked by hand from the normal table and the bfloat16 grid; gelu against
+table values and a library normal CDF; the backward against central
+differences of the unrounded loss; features against hand-computed values.
 
 Training loss: mean over agents and the 4 outputs of (out - target)^2, the
 target being the true step's deltas divided by (0.01, 0.01, 0.1, 0.1).
