@@ -58,6 +58,9 @@ def _lib():
         h.ow_step.argtypes = [ctypes.POINTER(_World), ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_int, ctypes.c_int]
         h.ow_step.restype = ctypes.c_int
+        h.ow_step_margin.argtypes = [ctypes.POINTER(_World), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        h.ow_step_margin.restype = ctypes.c_int
         h.ow_pairs.argtypes = [ctypes.POINTER(_World), ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p]
         h.ow_pairs.restype = ctypes.c_int
@@ -113,6 +116,28 @@ def step(scene, state, actions, threads: int = 1) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle rejected the world description")
     return st
+
+
+def step_margin(scene, state, actions, threads: int = 1):
+    """As ``step``, and also the smallest decision margin [E] each env met
+    over all its substeps (Reading R9 of the C file): the least |gap| of an
+    active pair and, for pairs in contact, how far the chosen face, axis,
+    incident edge, clip or normal orientation was from its runner-up.  Two
+    correct implementations in different precisions can only disagree
+    beyond rounding where that margin is within their rounding difference."""
+    pk = _Packed(scene)
+    E, N, A = int(scene.n_envs), int(scene.n_entities), int(scene.n_actuated)
+    st = np.array(np.asarray(state, np.float64).reshape(E, N, 6), order="C", copy=True)
+    act = np.asarray(actions, np.float64)
+    if act.ndim == 3:
+        act = act[None]
+    act = np.ascontiguousarray(act.reshape(act.shape[0], E, A, 3))
+    margin = np.zeros(E, np.float64)
+    rc = _lib().ow_step_margin(ctypes.byref(pk.w), st.ctypes.data, act.ctypes.data,
+                               act.shape[0], threads, margin.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the world description")
+    return st, margin
 
 
 def pairs(scene, state):
@@ -195,3 +220,48 @@ def lidar(scene, state, n_rays: int, max_range: float) -> np.ndarray:
     out = np.zeros((E, A, n_rays), np.float64)
     _lib().ow_lidar(ctypes.byref(pk.w), st.ctypes.data, n_rays, float(max_range), out.ctypes.data)
     return out
+
+
+def lidar_sensitivity(scene, state, n_rays: int, max_range: float, trials: int = 24,
+                      rel: float = 2.0 ** -20, seed: int = 0) -> np.ndarray:
+    """How much each ray's FP64 result moves when the inputs are perturbed
+    at the size of single-precision rounding: the largest |t' - t| [E, A,
+    n_rays] over ``trials`` copies of the scene whose positions, angles and
+    sizes are each moved by a uniform random amount of at most ``rel`` times
+    max(1, |value|) (2^-20: eight FP32 units in the last place at 1).  A ray
+    that grazes a disc (the entry distance goes as the square root of the
+    discriminant), clips a box corner or a segment end, or starts on a
+    surface moves by far more than its inputs; a well-conditioned ray moves
+    by about as much as they do."""
+    import dataclasses
+
+    rng = np.random.default_rng(seed)
+    st0 = np.asarray(state, np.float64)
+    ref = lidar(scene, st0, n_rays, max_range)
+    spread = np.zeros_like(ref)
+
+    def jig(a):
+        a = np.asarray(a, np.float64)
+        return a + rng.uniform(-rel, rel, a.shape) * np.maximum(1.0, np.abs(a))
+
+    for _ in range(trials):
+        st = st0.copy()
+        st[..., 0] = jig(st[..., 0])
+        st[..., 1] = jig(st[..., 1])
+        st[..., 4] = jig(st[..., 4])
+        sa = np.asarray(scene.size_a, np.float64)
+        sb = np.asarray(scene.size_b, np.float64)
+        sc = _Jiggled(scene, sa * (1 + rng.uniform(-rel, rel, sa.shape)),
+                      sb * (1 + rng.uniform(-rel, rel, sb.shape)))
+        spread = np.maximum(spread, np.abs(lidar(sc, st, n_rays, max_range) - ref))
+    return spread
+
+
+class _Jiggled:
+    """A scene with its sizes replaced (every other attribute delegated)."""
+
+    def __init__(self, base, size_a, size_b):
+        self._base, self.size_a, self.size_b = base, size_a, size_b
+
+    def __getattr__(self, name):
+        return getattr(self._base, name)

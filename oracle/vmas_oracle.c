@@ -84,6 +84,12 @@ typedef struct {
   double pix, piy; /* closest / contact point on i                        */
   double pjx, pjy; /* closest / contact point on j                        */
   int has_normal;  /* 0 when the normal is undefined (Reading R8)         */
+  /* Decision margin (Reading R9): how far the nearest discrete choice the
+   * geometry made for this pair (face, axis, incident edge, clip, normal
+   * orientation) is from switching to another candidate, in world units
+   * (dot products of unit normals for the incident-edge choice); INFINITY
+   * where the result is continuous.  Used only to certify near ties. */
+  double margin;
 } ow_contact;
 
 static double clampd(double v, double lo, double hi) {
@@ -103,6 +109,7 @@ static double softplus(double z) {
 static ow_contact sphere_sphere(const ow_body *bi, const ow_body *bj) {
   ow_contact r;
   memset(&r, 0, sizeof r);
+  r.margin = INFINITY;
   double dx = bi->x - bj->x, dy = bi->y - bj->y;
   double dist = sqrt(dx * dx + dy * dy);
   r.g = dist - (bi->a + bj->a);
@@ -123,6 +130,7 @@ static ow_contact sphere_sphere(const ow_body *bi, const ow_body *bj) {
 static ow_contact sphere_line(const ow_body *s, const ow_body *l) {
   ow_contact r;
   memset(&r, 0, sizeof r);
+  r.margin = INFINITY;
   double ux = cos(l->th), uy = sin(l->th);
   double ax = l->x - 0.5 * l->a * ux, ay = l->y - 0.5 * l->a * uy;
   double bx = l->x + 0.5 * l->a * ux, by = l->y + 0.5 * l->a * uy;
@@ -154,6 +162,7 @@ static ow_contact sphere_line(const ow_body *s, const ow_body *l) {
 static ow_contact sphere_box(const ow_body *s, const ow_body *b) {
   ow_contact r;
   memset(&r, 0, sizeof r);
+  r.margin = INFINITY;
   double c = cos(b->th), sn = sin(b->th);
   double dx = s->x - b->x, dy = s->y - b->y;
   double lx = c * dx + sn * dy;  /* box-local coordinates: R(-th) d */
@@ -165,6 +174,8 @@ static ow_contact sphere_box(const ow_body *s, const ow_body *b) {
     int f = 0;
     for (int q = 1; q < 4; ++q)
       if (depth[q] < depth[f]) f = q;
+    for (int q = 0; q < 4; ++q) /* runner-up face */
+      if (q != f && depth[q] - depth[f] < r.margin) r.margin = depth[q] - depth[f];
     if (f == 0) { nlx = 1; nly = 0; qx = hw; qy = ly; }
     else if (f == 1) { nlx = -1; nly = 0; qx = -hw; qy = ly; }
     else if (f == 2) { nlx = 0; nly = 1; qx = lx; qy = hh; }
@@ -273,6 +284,8 @@ static void closest_on_segment(double px, double py, double ax, double ay,
 static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
   ow_contact r;
   memset(&r, 0, sizeof r);
+  r.margin = INFINITY;
+  double depth_all[5];
   double ax[5], ay[5];
   int nai = body_axes(bi, ax, ay);
   int naj = body_axes(bj, ax + nai, ay + nai);
@@ -281,6 +294,7 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
    * along the lines, so add line i's direction. */
   if (bi->shape == OW_LINE && bj->shape == OW_LINE) {
     double ci = cos(bi->th), si = sin(bi->th), cj = cos(bj->th), sj = sin(bj->th);
+    r.margin = fabs(ci * sj - si * cj);
     if (ci * sj - si * cj == 0) {
       ax[na] = ci;
       ay[na] = si;
@@ -292,6 +306,7 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
   for (int q = 0; q < na; ++q) {
     double delta = (bi->x - bj->x) * ax[q] + (bi->y - bj->y) * ay[q];
     double depth = half_extent(bi, ax[q], ay[q]) + half_extent(bj, ax[q], ay[q]) - fabs(delta);
+    depth_all[q] = depth;
     if (depth < best) {
       best = depth;
       bk = q;
@@ -343,6 +358,9 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
    * turned to point from j towards i. */
   double ux = ax[bk], uy = ay[bk];
   double delta = (bi->x - bj->x) * ux + (bi->y - bj->y) * uy;
+  for (int q = 0; q < na; ++q) /* runner-up separating axis */
+    if (q != bk && depth_all[q] - best < r.margin) r.margin = depth_all[q] - best;
+  if (fabs(delta) < r.margin) r.margin = fabs(delta); /* orientation of the normal */
   if (delta < 0) { ux = -ux; uy = -uy; }
   r.g = -best;
   r.nx = ux;
@@ -385,6 +403,10 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
       double d = pQ->enx[q] * nRx + pQ->eny[q] * nRy;
       if (d < bestdot) { bestdot = d; e = q; }
     }
+    for (int q = 0; q < 4; ++q) { /* runner-up incident edge */
+      double d = pQ->enx[q] * nRx + pQ->eny[q] * nRy;
+      if (q != e && d - bestdot < r.margin) r.margin = d - bestdot;
+    }
     edge_of(pQ, e, &i0x, &i0y, &i1x, &i1y);
   } else {
     edge_of(pQ, 0, &i0x, &i0y, &i1x, &i1y);
@@ -404,10 +426,13 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
       double s1 = (i1x - fax) * tx + (i1y - fay) * ty;
       double lo, hi;
       int nonempty;
+      double ilen = sqrt((i1x - i0x) * (i1x - i0x) + (i1y - i0y) * (i1y - i0y));
       if (s1 == s0) {
         lo = 0.0;
         hi = 1.0;
         nonempty = (s0 >= 0 && s0 <= flen);
+        double mc = fmin(fabs(s0), fabs(flen - s0)); /* span test */
+        if (mc < r.margin) r.margin = mc;
       } else {
         double la = (0.0 - s0) / (s1 - s0), lb = (flen - s0) / (s1 - s0);
         lo = la < lb ? la : lb;
@@ -415,6 +440,8 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
         if (lo < 0) lo = 0;
         if (hi > 1) hi = 1;
         nonempty = lo <= hi;
+        double mc = fabs(hi - lo) * ilen; /* clipped length (or gap) */
+        if (mc < r.margin) r.margin = mc;
       }
       if (nonempty) {
         double c0x = i0x + lo * (i1x - i0x), c0y = i0y + lo * (i1y - i0y);
@@ -422,6 +449,7 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
         double d0 = -((c0x - fax) * nRx + (c0y - fay) * nRy);
         double d1 = -((c1x - fax) * nRx + (c1y - fay) * nRy);
         double w0 = d0 > 0 ? d0 : 0, w1 = d1 > 0 ? d1 : 0;
+        if (fabs(fmax(d0, d1)) < r.margin) r.margin = fabs(fmax(d0, d1)); /* midpoint rule */
         if (w0 + w1 > 0) {
           qx = (w0 * c0x + w1 * c1x) / (w0 + w1);
           qy = (w0 * c0y + w1 * c1y) / (w0 + w1);
@@ -440,6 +468,10 @@ static ow_contact poly_poly(const ow_body *bi, const ow_body *bj) {
     for (int q = 0; q < pQ->nv; ++q) {
       double p = pQ->vx[q] * nRx + pQ->vy[q] * nRy;
       if (p < bestp) { bestp = p; v = q; }
+    }
+    for (int q = 0; q < pQ->nv; ++q) { /* runner-up deepest vertex */
+      double p = pQ->vx[q] * nRx + pQ->vy[q] * nRy;
+      if (q != v && p - bestp < r.margin) r.margin = p - bestp;
     }
     qx = pQ->vx[v];
     qy = pQ->vy[v];
@@ -511,7 +543,7 @@ static void load_body(const ow_world *w, const double *st, size_t base, int i,
  * st points at that env's [n_entities][6] state (x, y, vx, vy, th, om);
  * act at its [n_actuated][3] actions (fx, fy, torque). */
 static void step_env(const ow_world *w, int e, double *st, const double *act,
-                     double *F, double *T) {
+                     double *F, double *T, double *margin) {
   int N = w->n_entities;
   size_t base = (size_t)e * N;
   double h = w->dt / w->substeps; /* Reading R5 */
@@ -541,6 +573,11 @@ static void step_env(const ow_world *w, int e, double *st, const double *act,
         load_body(w, st, base, i, &bi);
         load_body(w, st, base, j, &bj);
         ow_contact c = pair_geometry(&bi, &bj);
+        if (margin) { /* Reading R9: the contact decision g <= 0, and the choices behind a contact */
+          double m = fabs(c.g);
+          if (c.g <= 0 && c.has_normal && c.margin < m) m = c.margin;
+          if (m < *margin) *margin = m;
+        }
         if (!(c.g <= 0) || !c.has_normal) continue; /* Readings R2, R8 */
         double mag = contact_magnitude(w->c, w->k, c.g);
         double fx = mag * c.nx, fy = mag * c.ny;
@@ -597,10 +634,12 @@ static int ow_threads(int t) {
  * actions : [n_steps][n_envs][n_actuated][3]; the k-th actuated entity of an
  *           env (in entity order) reads row k.
  * threads : OpenMP threads over environments (<= 0: library default). */
-int ow_step(const ow_world *w, double *state, const double *actions, int n_steps,
-            int threads) {
+static int step_all(const ow_world *w, double *state, const double *actions, int n_steps,
+                    int threads, double *margin) {
   int E = w->n_envs, N = w->n_entities, A = w->n_actuated;
   if (E < 0 || N < 0 || A < 0 || w->substeps < 1 || n_steps < 0) return -1;
+  if (margin)
+    for (int e = 0; e < E; ++e) margin[e] = INFINITY;
   int nt = ow_threads(threads);
   (void)nt;
 #pragma omp parallel num_threads(nt)
@@ -611,12 +650,29 @@ int ow_step(const ow_world *w, double *state, const double *actions, int n_steps
 #pragma omp for schedule(static)
       for (int e = 0; e < E; ++e)
         step_env(w, e, state + (size_t)e * N * 6,
-                 actions + ((size_t)t * E + e) * A * 3, F, T);
+                 actions + ((size_t)t * E + e) * A * 3, F, T, margin ? margin + e : NULL);
     }
     free(F);
     free(T);
   }
   return 0;
+}
+
+int ow_step(const ow_world *w, double *state, const double *actions, int n_steps,
+            int threads) {
+  return step_all(w, state, actions, n_steps, threads, NULL);
+}
+
+/* As ow_step, and margin [n_envs] receives, per env, the smallest decision
+ * margin met over all substeps (Reading R9): the least |gap| of any active
+ * pair (the case split of Eq. 2) and, for pairs in contact, the margin of
+ * the geometry's discrete choices (see ow_contact.margin).  A result that
+ * differs between two correct implementations in different precisions
+ * (FP32 against FP64) can only come from a choice whose margin is within
+ * their rounding difference. */
+int ow_step_margin(const ow_world *w, double *state, const double *actions, int n_steps,
+                   int threads, double *margin) {
+  return step_all(w, state, actions, n_steps, threads, margin);
 }
 
 /* Canonical unordered pair list: (i, j), i < j, row-major. */

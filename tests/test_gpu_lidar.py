@@ -1,7 +1,15 @@
 """LIDAR ray casts on the GPU against the FP64 oracle, element by element.
-Rays that graze a disc or pass within rounding of a box corner or segment
-end flip between hit and miss in FP32 vs FP64; they are counted (at most
-0.05 % of rays) and the rest must agree to 2e-5 world units."""
+
+Every ray must agree to 2e-5 world units, or to twice the oracle's own
+sensitivity to single-precision rounding, whichever is larger: the oracle
+recomputes every ray on copies of the scene whose positions, angles and
+sizes are moved by up to eight FP32 units in the last place
+(``oracle.lidar_sensitivity``), decided before the GPU result is looked at.
+A ray that grazes a disc (its entry distance goes as the square root of the
+discriminant), clips a box corner or a segment end, or starts on a surface
+moves by far more than its inputs and may differ between FP32 and FP64;
+a well-conditioned ray may not.  The rays the allowance covers are
+counted and reported."""
 import numpy as np
 import pytest
 import torch
@@ -11,17 +19,31 @@ from paper_2207_03530_b300 import scenes
 pytestmark = pytest.mark.gpu
 
 
-def _compare(orc, sc, n_rays, rng_max):
+TOL = 2e-5
+
+
+def _certified(orc, sc, got, n_rays, rng_max, label):
+    ref = orc.lidar(sc, sc.init_state, n_rays, rng_max)
+    sens = orc.lidar_sensitivity(sc, sc.init_state, n_rays, rng_max)
+    diff = np.abs(got - ref)
+    allow = np.maximum(TOL, 2.0 * sens)
+    assert (diff <= allow).all(), (label, diff[diff > allow][:8], sens[diff > allow][:8])
+    cov = diff > TOL
+    print("\n[ill-conditioned rays] %s: %d of %d rays beyond %.0e, each within twice the "
+          "oracle's sensitivity (largest difference %.2e); %d rays have sensitivity > %.0e"
+          % (label, int(cov.sum()), diff.size, TOL, float(diff.max()), int((sens > TOL / 2).sum()),
+             TOL / 2))
+    return ref, int(cov.sum())
+
+
+def _compare(orc, sc, n_rays, rng_max, label=""):
     from paper_2207_03530_b300 import World
 
     w = World(sc)
     got = w.lidar(n_rays, rng_max).cpu().numpy()
     w.close()
-    ref = orc.lidar(sc, sc.init_state, n_rays, rng_max)
-    diff = np.abs(got - ref)
-    bad = diff > 2e-5
-    assert bad.mean() <= 5e-4, (bad.sum(), bad.size, diff.max())
-    return got, ref, int(bad.sum())
+    ref, nbad = _certified(orc, sc, got, n_rays, rng_max, label)
+    return got, ref, nbad
 
 
 @pytest.mark.parametrize("make,n_rays,rng", [
@@ -29,13 +51,15 @@ def _compare(orc, sc, n_rays, rng_max):
     (lambda: scenes.mixed_scene(200, 3), 24, 0.8),
     (lambda: scenes.small_scene(64, 1), 12, 2.0),
 ])
-def test_lidar_matches_oracle(vmas_lib, orc, make, n_rays, rng):
-    got, ref, nbad = _compare(orc, make(), n_rays, rng)
+def test_lidar_matches_oracle(vmas_lib, orc, make, n_rays, rng, capsys):
+    sc = make()
+    with capsys.disabled():
+        got, ref, nbad = _compare(orc, sc, n_rays, rng, label=sc.name)
     assert (ref < rng).mean() > 0.05  # the rays do hit things
     assert (got == 0).sum() == (ref == 0).sum()  # inside-origin readings agree
 
 
-def test_lidar_full_config_sampled(vmas_lib, orc):
+def test_lidar_full_config_sampled(vmas_lib, orc, capsys):
     """30,000 envs, 16 rays: 64 sampled envs compared."""
     from paper_2207_03530_b300 import World
 
@@ -45,8 +69,8 @@ def test_lidar_full_config_sampled(vmas_lib, orc):
     w.close()
     pick = np.random.default_rng(0).choice(30000, 64, replace=False)
     sub = sc.subset(pick)
-    ref = orc.lidar(sub, sub.init_state, 16, 1.0)
-    assert (np.abs(got[pick] - ref) > 2e-5).mean() <= 5e-4
+    with capsys.disabled():
+        _certified(orc, sub, got[pick], 16, 1.0, "30,000 envs, 64 sampled")
 
 
 def test_lidar_rays_parallel_to_box_faces_and_walls(vmas_lib, orc):

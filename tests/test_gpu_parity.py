@@ -6,6 +6,20 @@ Gate (max relative state error after one step): for every state field
 bit-exactly (scenes keep every active pair's gap outside +-1e-4, so FP32 and
 FP64 take the same decision).  Multi-step trajectory errors are reported,
 not gated: contact dynamics is chaotic.
+
+Near ties (Reading R9).  Where bodies overlap at random, two contact
+features can lie within rounding of each other, and FP32 and FP64 may then
+choose differently.  Such envs are named by the oracle alone, before the GPU
+result is looked at: its decision margin (the least |gap| of an active pair
+and, for contacts, the distance of the chosen face, separating axis,
+incident edge, clip or normal orientation from its runner-up, over all
+substeps) must be below MARGIN_BOUND.  Every other env meets the 1e-5 gate.
+MARGIN_BOUND = 1e-5: before a choice flips, the two implementations' states
+differ by FP32 rounding (about 1e-7 of the positions and angles within one
+step), and a margin moves at most about 4 times as much as the state does
+(a corner moves by its position change plus half its diagonal times the
+angle change), so a flip needs a margin below about 1e-6; the bound leaves
+a factor of 10.
 """
 import os
 
@@ -18,6 +32,7 @@ from paper_2207_03530_b300 import scenes
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
+MARGIN_BOUND = 1e-5
 S_, B_, L_ = scenes.SPHERE, scenes.BOX, scenes.LINE
 MOV, ROT, COL, ACT = scenes.MOVABLE, scenes.ROTATABLE, scenes.COLLIDABLE, scenes.ACTUATED
 THREADS = os.cpu_count() or 1
@@ -40,6 +55,29 @@ def _one_step(vmas_lib, orc, sc, seed=0, steps=1):
     ref = orc.step(sc, sc.init_state, act, threads=THREADS)
     w.close()
     return got, ref
+
+
+def _one_step_certified(vmas_lib, orc, sc, seed, steps=1, label=""):
+    """GPU and oracle after `steps` steps; envs whose oracle decision margin is
+    below MARGIN_BOUND are reported, every other env must meet TOL."""
+    act = scenes.make_actions(sc, steps, seed)
+    w = _world(sc)
+    d_act = torch.from_numpy(act).cuda()
+    for t in range(steps):
+        w.step(d_act[t])
+    got = w.state().cpu().numpy()
+    w.check()
+    w.close()
+    ref, margin = orc.step_margin(sc, sc.init_state, act, threads=THREADS)
+    tie = margin < MARGIN_BOUND
+    err = normwise_err(got[~tie], ref[~tie])
+    assert err.max() <= TOL, (label, err)
+    ties = [(int(e), float(margin[e]), float(normwise_err(got[e:e + 1], ref[e:e + 1]).max()))
+            for e in np.nonzero(tie)[0]]
+    print("\n[near ties] %s: %d of %d envs below margin %.0e (env, margin, error): %s"
+          % (label, len(ties), sc.n_envs, MARGIN_BOUND,
+             ", ".join("(%d, %.2e, %.2e)" % t for t in ties)))
+    return got, ref, margin
 
 
 def _mask_compare(vmas_lib, orc, sc):
@@ -93,19 +131,14 @@ def test_paper_config_one_step(vmas_lib, orc, dense, n_envs):
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_mixed_scene_all_pair_types(vmas_lib, orc, seed):
+def test_mixed_scene_all_pair_types(vmas_lib, orc, seed, capsys):
     """Every pair type in contact (sphere/box/line, movable lines, gravity,
-    3 substeps); near-tie envs (several contact features within FP32
-    rounding) are counted and excluded."""
+    3 substeps); envs the oracle certifies as near ties (decision margin
+    below MARGIN_BOUND) are reported, every other env meets TOL."""
     sc = scenes.mixed_scene(256, seed)
-    got, ref = _one_step(vmas_lib, orc, sc, seed)
-    per_env = np.stack([normwise_err(got[e:e + 1], ref[e:e + 1]) for e in range(sc.n_envs)])
-    err = normwise_err(got, ref)
-    bad = np.nonzero(per_env.max(1) > 1e-3)[0]
-    assert len(bad) <= 2, (bad, per_env[bad])
-    keep = np.setdiff1d(np.arange(sc.n_envs), bad)
-    err = normwise_err(got[keep], ref[keep])
-    assert err.max() <= TOL, err
+    with capsys.disabled():
+        got, ref, margin = _one_step_certified(vmas_lib, orc, sc, seed, label="mixed seed %d" % seed)
+    assert (margin < MARGIN_BOUND).sum() < sc.n_envs // 10  # the scene still tests contacts
     mask, omask, nguard = _mask_compare(vmas_lib, orc, sc)
     pi, pj = orc.pair_list(sc.n_entities)
     kinds = {(int(sc.shape[0, pi[p]]), int(sc.shape[0, pj[p]])) for p in np.nonzero(omask.any(0))[0]}
@@ -128,7 +161,7 @@ def test_paper_config_full_size_dense_masks(vmas_lib, orc):
 
 
 @pytest.mark.parametrize("N", [1, 2, 31, 32, 33, 64, 65, 100, 128])
-def test_entity_counts_span_slots(vmas_lib, orc, N):
+def test_entity_counts_span_slots(vmas_lib, orc, N, capsys):
     """Entity counts around the lane / slot boundaries (1..4 slots)."""
     rng = np.random.default_rng(N)
     bodies = []
@@ -143,11 +176,8 @@ def test_entity_counts_span_slots(vmas_lib, orc, N):
     sc = make_scene(bodies, substeps=2, drag=0.1, n_envs=11)
     # give each env its own layout
     sc.init_state[:, :, :2] += np.random.default_rng(1).uniform(-0.05, 0.05, (11, N, 2)).astype(np.float32)
-    got, ref = _one_step(vmas_lib, orc, sc, 5)
-    per_env = np.stack([normwise_err(got[e:e + 1], ref[e:e + 1]) for e in range(sc.n_envs)])
-    assert (per_env.max(1) > 1e-3).sum() <= 1
-    good = per_env.max(1) <= 1e-3
-    assert normwise_err(got[good], ref[good]).max() <= TOL
+    with capsys.disabled():
+        _one_step_certified(vmas_lib, orc, sc, 5, label="N=%d" % N)
 
 
 def test_gravity_max_speed_and_inert_padding(vmas_lib, orc):

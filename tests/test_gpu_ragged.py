@@ -165,10 +165,14 @@ def test_extreme_env_sizes(vmas_lib, orc):
     sc.shape[1], sc.flags[1], sc.size_a[1], sc.size_b[1] = shape[1:], flags[1:], size_a[1:], size_b[1:]
     sc.init_state[1] = st[1:]
     sc.size_a[0, 1:] = 0.05
-    ref = orc.step(sc, sc.init_state, np.zeros((1, 2, n_big, 3)))
+    ref, margin = orc.step_margin(sc, sc.init_state, np.zeros((1, 2, n_big, 3)))
     refp = np.concatenate([ref[0, :1], ref[1]])
-    per_env_ok = normwise_err(got[1:], refp[1:]).max() <= 1e-3  # 128 overlapping bodies: near ties allowed
-    assert normwise_err(got[:1], refp[:1]).max() <= TOL and per_env_ok
+    assert normwise_err(got[:1], refp[:1]).max() <= TOL
+    # 128 overlapping bodies: held to TOL unless the oracle certifies a near
+    # tie (decision margin below 1e-5, as in the regular world's parity tests)
+    err_big = normwise_err(got[1:], refp[1:]).max()
+    print("\n[near ties] 128-entity env: margin %.2e, error %.2e" % (margin[1], err_big))
+    assert err_big <= TOL or margin[1] < 1e-5, (err_big, margin[1])
     rw.check()
     rw.close()
 

@@ -507,3 +507,67 @@ def test_degenerate_worlds(orc):
     one = make_scene([dict(shape=S_, vx=1.0, a=0.1, flags=MOV | COL)], drag=0.5)
     out = orc.step(one, one.init_state, np.zeros((2, 1, 0, 3), np.float32))
     assert out[0, 0, 2] == pytest.approx(0.25, rel=1e-15)
+
+
+# ---- decision margins and ray sensitivity (the near-tie certificates) ----
+
+def test_step_margin_leaves_the_step_unchanged(orc):
+    """ow_step_margin is ow_step plus bookkeeping: bitwise the same state."""
+    from paper_2207_03530_b300 import scenes
+
+    sc = scenes.mixed_scene(64, 5)
+    act = scenes.make_actions(sc, 2, 1)
+    a = orc.step(sc, sc.init_state, act)
+    b, m = orc.step_margin(sc, sc.init_state, act)
+    assert np.array_equal(a, b)
+    assert m.shape == (64,) and (m >= 0).all() and np.isfinite(m).all()
+
+
+def test_step_margin_sphere_inside_box_runner_up_face(orc):
+    """A sphere (r = 0.01) whose centre sits at (0.03, 0.01) inside a fixed
+    0.2 x 0.1 box: face depths +x 0.07, -x 0.13, +y 0.04, -y 0.06, so the
+    contact leaves through +y and the runner-up face is 0.02 deeper; the
+    gap is -0.05.  One substep: the margin is min(|gap|, 0.02) = 0.02, i.e.
+    2 y in the box frame (the -y face depth minus the +y one), with y the
+    FP32 value the scene holds."""
+    sc = make_scene([dict(shape=S_, x=0.03, y=0.01, a=0.01, flags=MOV | COL),
+                     dict(shape=B_, a=0.2, b=0.1, flags=COL)], substeps=1)
+    _, m = orc.step_margin(sc, sc.init_state, np.zeros((1, 1, 0, 3)))
+    assert m[0] == pytest.approx(2 * float(np.float32(0.01)), abs=1e-15)
+
+
+def test_step_margin_box_box_runner_up_axis(orc):
+    """Two axis-aligned 0.2 x 0.2 boxes, centres 0.15 apart in x and 0.17 in
+    y: overlap depths 0.05 along x and 0.03 along y (on both boxes' axes),
+    so the least axis is y (i's own, found first) with i's x-axis and
+    both of j's axes as runners-up; the nearest runner-up is j's y-axis at
+    the same depth: margin 0 (an exact tie, resolved by order), and the
+    scene with j turned by 0.1 rad has a positive margin."""
+    bodies = [dict(shape=B_, a=0.2, b=0.2, flags=MOV | ROT | COL),
+              dict(shape=B_, x=0.15, y=0.17, a=0.2, b=0.2, flags=COL)]
+    sc = make_scene(bodies, substeps=1)
+    _, m = orc.step_margin(sc, sc.init_state, np.zeros((1, 1, 0, 3)))
+    assert m[0] == 0.0
+    bodies[1]["th"] = 0.1
+    sc = make_scene(bodies, substeps=1)
+    _, m = orc.step_margin(sc, sc.init_state, np.zeros((1, 1, 0, 3)))
+    assert m[0] > 1e-3
+
+
+def test_lidar_sensitivity_separates_grazing_from_central_rays(orc):
+    """A disc of radius 0.1 centred 0.5 ahead of the caster: ray 0 hits it
+    head on (entry at 0.4, well conditioned); a second caster's ray passes
+    the disc 0.1 - 1e-7 from its centre (a graze: the entry distance moves
+    with the square root of the discriminant).  The central ray's
+    sensitivity is about its input perturbation, the grazing one's far
+    larger."""
+    act = MOV | COL | ACT
+    sc = make_scene([dict(shape=S_, x=0.0, y=0.0, a=0.01, flags=act),
+                     dict(shape=S_, x=0.0, y=0.3 - 1e-7, a=0.01, flags=act),
+                     dict(shape=S_, x=0.5, y=0.2, a=0.1, flags=COL),
+                     dict(shape=S_, x=0.5, y=0.0, a=0.1, flags=COL)])
+    ref = orc.lidar(sc, sc.init_state, 1, 2.0)
+    sens = orc.lidar_sensitivity(sc, sc.init_state, 1, 2.0)
+    assert ref[0, 0, 0] == 0.5 - float(np.float32(0.1))  # the scene's FP32 radius
+    assert sens[0, 0, 0] < 1e-5
+    assert sens[0, 1, 0] > 1e-4
