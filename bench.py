@@ -632,21 +632,40 @@ def run_ragged(args):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(args.seed + 3)
     act = torch.rand((T, rw.n_action_rows, 3), device="cuda", generator=gen) * 2 - 1
-    rw.autotune(act[:8])
+    rw.autotune(act[:64])
     lanes, tile = rw.tuning()
-    rw.rollout(act)  # captures the graph
-    torch.cuda.synchronize()
+    persistent = rw.persistent
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, args.steps // 100)
     cs = ClockSampler(torch.device("cuda", 0))
-    with cs:
-        a.record()
-        for _ in range(reps):
-            rw.rollout(act)
-        b.record()
+    start = rw.state()
+
+    def timed_rollout():
+        rw.set_state(start)
+        rw.rollout(act)  # captures the graph on first use
         torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / reps
+        with cs:
+            a.record()
+            for _ in range(reps):
+                rw.rollout(act)
+            b.record()
+            torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms = timed_rollout()
     value = E * T / (ms / 1e3)
+    # A/B of the two schedules: one launch per size class (autotuned lanes)
+    # against one persistent launch over every class (atomic work queue), at
+    # several steps per launch
+    ab = []
+    for sched in (False, True):
+        for t in sorted({tile, 8, 16, 32}):
+            rw.persistent = sched
+            rw.set_tuning(lanes, t)
+            ab.append({"schedule": "persistent" if sched else "per-class", "steps_per_launch": t,
+                       "env_steps_per_s": E * T / (timed_rollout() / 1e3)})
+    rw.persistent = persistent
+    rw.set_tuning(lanes, tile)
     rw.close()
     del act
     # the same scene padded to the largest env, regular world, one step at a time
@@ -672,7 +691,8 @@ def run_ragged(args):
         "roofline": _hbm_roofline(b_env, value, "latency-bound size classes "
                                   "(ncu: the 128-entity class)"),
         "entities": int(counts.sum()), "envs": E, "lanes_per_class": [int(x) for x in lanes],
-        "steps_per_launch": tile, "padded_regular_world_value": padded, "clocks": cs.summary(),
+        "steps_per_launch": tile, "schedule": "persistent" if persistent else "per-class",
+        "schedules_ab": ab, "padded_regular_world_value": padded, "clocks": cs.summary(),
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "%d envs x (2-64 agents + 0-8 boxes + 0-4 walls), 5 substeps, "

@@ -222,12 +222,22 @@ int vmas_check(vmas_world *world, void *stream, int32_t *bits);
  * aoff[e] + k).
  *
  * The library sorts the envs into size classes of capacity 8, 16, 32, 64
- * and 128 entities and steps each class with the fused kernel compiled for
- * its choice of lanes per environment (4, 8, 16 or 32); rollouts run
- * steps_per_launch world steps per launch and are captured once into a CUDA
- * graph per (actions buffer, n_steps, tuning), then replayed.
- * vmas_ragged_autotune times the choices on the caller's actions (the world
- * state is restored afterwards) and keeps the fastest. */
+ * and 128 entities (Table 1 of the paper lists VMAS for "< 100 agents" per
+ * world; section 3's vectorized interface steps any number of worlds in one
+ * batch).  Two schedules step them:
+ *  - per class (schedule 0): each class by the fused kernel compiled for its
+ *    choice of lanes per environment (4, 8, 16 or 32), the classes' launches
+ *    side by side;
+ *  - persistent (schedule 1): every class in ONE launch, whose warps take
+ *    one warp's worth of envs at a time from an atomic work queue, largest
+ *    class first, with fixed lanes per class (8, 8, 16, 32, 32).  No warp
+ *    ever waits on another: a warp takes its next item with one atomic add.
+ * Rollouts run steps_per_launch world steps per launch and are captured once
+ * into a CUDA graph per (actions buffer, n_steps, tuning, schedule), then
+ * replayed.  vmas_ragged_autotune times the lanes per class, then every
+ * steps_per_launch under both schedules, on the caller's actions (the world
+ * state is restored afterwards), and keeps the fastest.  Both schedules give
+ * bitwise the same result for the same lanes per class. */
 typedef struct vmas_ragged vmas_ragged;
 typedef struct {
   int32_t n_envs, substeps;
@@ -256,6 +266,10 @@ int vmas_ragged_check(vmas_ragged *world, void *stream, int32_t *bits);
 int vmas_ragged_set_tuning(vmas_ragged *world, const int32_t *lanes, int32_t steps_per_launch);
 int vmas_ragged_get_tuning(const vmas_ragged *world, int32_t *lanes, int32_t *steps_per_launch);
 int vmas_ragged_autotune(vmas_ragged *world, const float *d_actions, int32_t n_steps, void *stream);
+/* Schedule: 0 = per-class launches (default at create), 1 = one persistent
+ * launch with an atomic work queue.  VMAS_EINVAL for other values. */
+int vmas_ragged_set_schedule(vmas_ragged *world, int32_t persistent);
+int vmas_ragged_get_schedule(const vmas_ragged *world, int32_t *persistent);
 
 /* LIDAR (section 3: agents can carry LIDAR sensors).  Every actuated
  * entity of every env casts n_rays rays from its centre at angles

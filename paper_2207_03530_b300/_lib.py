@@ -29,6 +29,7 @@ SYMBOLS = (
     "vmas_ragged_step", "vmas_ragged_rollout", "vmas_ragged_state", "vmas_ragged_set_state",
     "vmas_ragged_check",
     "vmas_ragged_set_tuning", "vmas_ragged_get_tuning", "vmas_ragged_autotune",
+    "vmas_ragged_set_schedule", "vmas_ragged_get_schedule",
     "vmas_sur_param_count", "vmas_sur_create", "vmas_sur_destroy", "vmas_sur_set_params",
     "vmas_sur_get_params", "vmas_sur_set_mode", "vmas_sur_forward", "vmas_sur_loss_grad", "vmas_sur_adam",
     "vmas_sur_train_grad", "vmas_sur_train_step", "vmas_sur_step", "vmas_sur_debug_features", "vmas_debug_gemm_bf16",
@@ -139,6 +140,8 @@ def load():
         "vmas_ragged_set_tuning": ([vp, vp, i32], ctypes.c_int),
         "vmas_ragged_get_tuning": ([vp, vp, vp], ctypes.c_int),
         "vmas_ragged_autotune": ([vp, vp, i32, vp], ctypes.c_int),
+        "vmas_ragged_set_schedule": ([vp, i32], ctypes.c_int),
+        "vmas_ragged_get_schedule": ([vp, vp], ctypes.c_int),
         "vmas_sur_param_count": ([], ctypes.c_int),
         "vmas_sur_create": ([i32, P(vp)], ctypes.c_int),
         "vmas_sur_destroy": ([vp], ctypes.c_int),

@@ -64,6 +64,9 @@ int group_lanes(int N);
 int launch_step(const StepParams &p, cudaStream_t st, bool tiled = false);
 // One launch of the step kernel over a ragged world's size class.
 int launch_ragged_class(const StepParams &p, int G, int slots, int n_envs, cudaStream_t st);
+// One persistent launch over every size class of a ragged world (q.slab is
+// filled in here); the caller zeroes *q.queue on `st` first.
+int launch_ragged_persistent(vmas::RaggedQueueParams q, cudaStream_t st);
 
 }  // namespace vmas_host
 

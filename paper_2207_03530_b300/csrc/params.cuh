@@ -51,4 +51,26 @@ struct StepParams {
   const float *r_size_a, *r_size_b, *r_mass, *r_inertia;  // [E * N]
 };
 
+// A packed ragged world stepped in one persistent launch: every size class
+// (capacities 8, 16, 32, 64, 128) from one atomic work queue.  Lanes per env
+// and entities per lane of each class are fixed for this form.
+constexpr int kPersistLanes[5] = {8, 8, 16, 32, 32};
+constexpr int kPersistSlots[5] = {1, 2, 2, 2, 4};
+
+struct RaggedQueueParams {
+  StepParams p[5];  // one per size class: capacity, pair table, env range, actions, tile
+  // work items (one warp's envs each) run largest class first: class c owns
+  // items [item_end[c + 1], item_end[c]), with item_end[5] = 0 implied
+  int item_end[5];
+  int n_items;
+  int *queue;       // the dequeue counter; must be 0 when the launch starts
+  int slab;         // shared-memory bytes per warp
+};
+
+// Work items of a class of n_envs envs in the persistent form.
+inline int persist_items(int n_envs, int c) {
+  const int epw = 32 / kPersistLanes[c];
+  return (n_envs + epw - 1) / epw;
+}
+
 }  // namespace vmas

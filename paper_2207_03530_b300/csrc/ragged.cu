@@ -7,8 +7,12 @@
 // per env, entities per lane) choice, which the autotuner picks by timing, as
 // it picks the number of world steps per launch of a rollout.  Rollouts are
 // captured into a CUDA graph (one node per class per tile of steps) and
-// replayed.  The step kernels themselves are instantiated in vmas.cu and
-// reached through launch_ragged_class.
+// replayed.  The persistent schedule instead steps every class in one launch
+// per tile: warps take one warp's worth of envs at a time from an atomic
+// work queue, largest class first, with fixed lanes per class.  The
+// autotuner times both schedules.  The step kernels themselves are
+// instantiated in vmas.cu and reached through launch_ragged_class and
+// launch_ragged_persistent.
 
 #include "host.h"
 
@@ -26,6 +30,9 @@ struct vmas_ragged {
   int lanes[kClasses] = {};          // chosen lanes per env
   int slots[kClasses] = {};          // chosen entities per lane
   int tile = 1;                      // steps per launch in rollouts
+  int persistent = 0;                // 1: one persistent launch per tile for all classes
+  int *queue = nullptr;              // work-queue counters, one per launch of a rollout
+  int queue_cap = 0;
   float *planes = nullptr;           // 6 planes x total, sorted order
   float4 *param = nullptr;
   uint8_t *kind = nullptr;
@@ -60,6 +67,7 @@ void free_ragged(vmas_ragged *r) {
   cudaFree(r->err);
   cudaFree(r->stage);
   cudaFree(r->backup);
+  cudaFree(r->queue);
   delete r;
 }
 
@@ -100,9 +108,44 @@ StepParams ragged_params(const vmas_ragged *r, int c) {
   return p;
 }
 
+// At least n work-queue counters.
+int ragged_queue_reserve(vmas_ragged *r, int n) {
+  if (r->queue_cap >= n) return VMAS_OK;
+  cudaFree(r->queue);
+  r->queue = nullptr;
+  r->queue_cap = 0;
+  VMAS_CUDA(cudaMalloc(&r->queue, (size_t)n * sizeof(int)));
+  r->queue_cap = n;
+  return VMAS_OK;
+}
+
+// The persistent launch of one tile: every class, counter `counter` (zeroed
+// by the caller on the same stream).
+int ragged_persist_tile(vmas_ragged *r, const float *d_actions, int tile, int *counter,
+                        cudaStream_t st) {
+  vmas::RaggedQueueParams q{};
+  int end = 0;
+  for (int c = vmas_ragged::kClasses - 1; c >= 0; --c) {
+    q.p[c] = ragged_params(r, c);
+    q.p[c].actions = d_actions;
+    q.p[c].tile = tile;
+    end += vmas::persist_items(r->cls_begin[c + 1] - r->cls_begin[c], c);
+    q.item_end[c] = end;
+  }
+  q.n_items = end;
+  q.queue = counter;
+  return launch_ragged_persistent(q, st);
+}
+
 // One tile of `tile` steps for every class, actions of the tile's first step
 // at d_actions.
 int ragged_launch_tile(vmas_ragged *r, const float *d_actions, int tile, cudaStream_t st) {
+  if (r->persistent) {
+    int rc = ragged_queue_reserve(r, 1);
+    if (rc) return rc;
+    VMAS_CUDA(cudaMemsetAsync(r->queue, 0, sizeof(int), st));
+    return ragged_persist_tile(r, d_actions, tile, r->queue, st);
+  }
   for (int c = 0; c < vmas_ragged::kClasses; ++c) {
     const int n = r->cls_begin[c + 1] - r->cls_begin[c];
     if (n == 0) continue;
@@ -316,8 +359,23 @@ int vmas_ragged_rollout(vmas_ragged *r, const float *d_actions, int32_t n_steps,
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     int rc = VMAS_OK;
+    const int n_tiles = (n_steps + r->tile - 1) / r->tile;
+    if (r->persistent) {
+      rc = ragged_queue_reserve(r, n_tiles);
+      if (rc) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && r->persistent) {
+      // one memset of every tile's counter, then the tiles in order
+      e = cudaMemsetAsync(r->queue, 0, (size_t)n_tiles * sizeof(int), cap);
+      for (int k = 0; k < n_tiles && rc == VMAS_OK && e == cudaSuccess; ++k) {
+        const int t = k * r->tile;
+        rc = ragged_persist_tile(r, d_actions + (size_t)t * r->total_act * 3,
+                                 std::min(r->tile, n_steps - t), r->queue + k, cap);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(cap, &r->graph);
+      if (e == cudaSuccess) e = e2;
+    } else if (e == cudaSuccess) {
       e = cudaEventRecord(fork, cap);
       for (int c = 0; c < C && e == cudaSuccess; ++c) {
         const int n = r->cls_begin[c + 1] - r->cls_begin[c];
@@ -434,6 +492,20 @@ int vmas_ragged_set_tuning(vmas_ragged *r, const int32_t *lanes, int32_t steps_p
   return VMAS_OK;
 }
 
+int vmas_ragged_set_schedule(vmas_ragged *r, int32_t persistent) {
+  if (!r) return fail(VMAS_EINVAL, "world is NULL");
+  if (persistent != 0 && persistent != 1) return fail(VMAS_EINVAL, "persistent must be 0 or 1");
+  r->persistent = persistent;
+  ++r->version;
+  return VMAS_OK;
+}
+
+int vmas_ragged_get_schedule(const vmas_ragged *r, int32_t *persistent) {
+  if (!r || !persistent) return fail(VMAS_EINVAL, "NULL argument");
+  *persistent = r->persistent;
+  return VMAS_OK;
+}
+
 int vmas_ragged_get_tuning(const vmas_ragged *r, int32_t *lanes, int32_t *steps_per_launch) {
   if (!r) return fail(VMAS_EINVAL, "world is NULL");
   if (lanes)
@@ -453,7 +525,8 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
   cudaEvent_t a, b;
   VMAS_CUDA(cudaEventCreate(&a));
   VMAS_CUDA(cudaEventCreate(&b));
-  const int tiles[] = {1, 2, 4, 8, 16};
+  const int tiles[] = {1, 2, 4, 8, 16, 32, 64};
+  constexpr int kTiles = (int)(sizeof(tiles) / sizeof(tiles[0]));
   int rc = VMAS_OK;
   for (int c = 0; c < vmas_ragged::kClasses && rc == VMAS_OK; ++c) {
     const int n = r->cls_begin[c + 1] - r->cls_begin[c];
@@ -480,25 +553,30 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
     r->lanes[c] = best_g;
     r->slots[c] = r->cap[c] / best_g;
   }
-  // steps per launch, all classes together
+  // steps per launch, all classes together, under either schedule (the
+  // per-class launches with the lanes just chosen, or one persistent launch)
   float best = 3.4e38f;
-  int best_tile = 1;
-  for (int ti = 0; ti < 5 && rc == VMAS_OK; ++ti) {
-    const int tile = tiles[ti];
-    if (tile > n_steps) break;
-    float ms = 0;
-    for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {
-      cudaEventRecord(a, st);
-      for (int t = 0; t + tile <= n_steps && rc == VMAS_OK; t += tile)
-        rc = ragged_launch_tile(r, d_actions + (size_t)t * r->total_act * 3, tile, st);
-      cudaEventRecord(b, st);
-      cudaEventSynchronize(b);
-      cudaEventElapsedTime(&ms, a, b);
+  int best_tile = 1, best_sched = 0;
+  for (int sched = 0; sched < 2 && rc == VMAS_OK; ++sched) {
+    r->persistent = sched;
+    for (int ti = 0; ti < kTiles && rc == VMAS_OK; ++ti) {
+      const int tile = tiles[ti];
+      if (tile > n_steps) break;
+      float ms = 0;
+      for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {
+        cudaEventRecord(a, st);
+        for (int t = 0; t + tile <= n_steps && rc == VMAS_OK; t += tile)
+          rc = ragged_launch_tile(r, d_actions + (size_t)t * r->total_act * 3, tile, st);
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+      }
+      const float per_step = ms / (float)((n_steps / tile) * tile);
+      if (per_step < best) { best = per_step; best_tile = tile; best_sched = sched; }
     }
-    const float per_step = ms / (float)((n_steps / tile) * tile);
-    if (per_step < best) { best = per_step; best_tile = tile; }
   }
   r->tile = best_tile;
+  r->persistent = best_sched;
   ++r->version;
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -102,27 +102,30 @@ __device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
 // entity count (at most p.N, the layout capacity) at its own offset.  TILED
 // kernels run p.tile consecutive world steps per launch (others run one);
 // the state and the candidate list stay on chip between them.
-template <int G, int SLOTS, int NC, bool RAW = false, bool RAGGED = false, bool TILED = false>
-__global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
-    world_step_kernel(const StepParams p) {
+//
+// The body steps the 32 / G environments of one warp: env slots slot0 +
+// group (of the size class's range, for RAGGED kernels), per-env shared
+// memory from `wsmem` on.  `smem` and `warp` (the warp's index in its CTA)
+// serve the CTA-wide bulk staging of the one-step plain kernel only, the one
+// form that synchronises its CTA; every other form is warp-local, which lets
+// a persistent kernel run different size classes in the warps of one CTA.
+template <int G, int SLOTS, int NC, bool RAW, bool RAGGED, bool TILED>
+__device__ __forceinline__ void world_step_body(const StepParams &p, unsigned char *smem,
+                                                unsigned long long *mbar, int warp, int slot0,
+                                                unsigned char *wsmem) {
   constexpr int EPW = 32 / G;
   constexpr unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int NL = NC > 0 ? NC : p.N;  // layout capacity per env
   const int P = NC > 0 ? NC * (NC - 1) / 2 : p.P;
-  if constexpr (!RAGGED && !RAW) {
-    // listed stepping: a block past the end of the list has nothing to do
-    // (uniform over the block, before its first barrier)
-    if (p.env_list && (int)(blockIdx.x * kFusedWarps * EPW) >= *p.env_count) return;
-  }
   // Bulk staging (one-step plain kernels, full CTAs): the CTA's envs are
   // contiguous in every plane, so one thread issues a bulk copy per plane,
   // for the parameters, the actions and the kinds into the per-env area
   // (which is free until the poses are published), counted on one mbarrier.
   constexpr int CE = kFusedWarps * EPW;  // envs per CTA
-  __shared__ __align__(8) unsigned long long s_mbar;
+  constexpr bool kCanStage = !RAW && !RAGGED && !TILED;
+  unsigned long long &s_mbar = *mbar;
   bool bulk = false;
-  if constexpr (!RAW && !RAGGED && !TILED)
+  if constexpr (kCanStage)
     bulk = p.bulk && !p.env_list && (blockIdx.x + 1) * CE <= p.E;
   unsigned char *stage = smem;
   const uint32_t plane_b = (uint32_t)(CE * NL * 4), param_b = 4 * plane_b;
@@ -140,13 +143,13 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
                p.actions + (size_t)blockIdx.x * CE * p.A * 3, act_b, bar);
     bulk_g2s(smem_u32(stage + 6 * plane_b + param_b + act_b), p.kind + e0, kind_b, bar);
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int grp = lane / G, lg = lane % G;
   const int LC = G * kLaneCand;  // candidate capacity per env
   (void)LC;
   const unsigned gbits = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   const unsigned lt = (1u << lane) - 1u;
-  unsigned char *es = smem + (warp * EPW + grp) * fused_env_bytes(NL, G);
+  unsigned char *es = wsmem + grp * fused_env_bytes(NL, G);
   float4 *s_bp = reinterpret_cast<float4 *>(es);  // [NL] {x, y, inflated R, kind}
   float4 *s_ng = s_bp + NL;                        // [NL] {cos, sin, ha, hb}
   float4 *s_mi = s_ng + NL;                        // [NL] {1/m, 1/I, R, action torque}
@@ -158,14 +161,15 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   uint16_t *s_lc = reinterpret_cast<uint16_t *>(s_rec);
   uint16_t *s_cand = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(s_rec) +
                                                   fused_rec_bytes(G));  // compact list
-  __syncthreads();  // the staging mbarrier is initialised before any thread waits on it
+  // the staging mbarrier is initialised before any thread waits on it
+  if constexpr (kCanStage) __syncthreads();
 
   // this group's environment: index, entity base and count, action rows
   int e, N, A_e;
   size_t eb, arow0;
   bool valid;
   if constexpr (RAGGED) {
-    e = p.env_begin + (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+    e = p.env_begin + slot0 + grp;
     valid = e < p.env_end;
     const int s0 = valid ? p.soff[e] : 0, s1 = valid ? p.soff[e + 1] : 0;
     eb = (size_t)s0;
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
     arow0 = valid ? (size_t)p.aoff[oe] : 0;
     A_e = valid ? p.aoff[oe + 1] - p.aoff[oe] : 0;
   } else {
-    const int slot = (blockIdx.x * kFusedWarps + warp) * EPW + grp;
+    const int slot = slot0 + grp;
     if (!RAW && p.env_list) {
       valid = slot < *p.env_count;
       e = valid ? p.env_list[slot] : 0;
@@ -683,6 +687,75 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   }
   if (stats && valid && lg == 0) atomicAdd(stats + kStatEnvSteps, (unsigned long long)tile);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, 1);  // VMAS_DEVERR_NONFINITE
+}
+
+// One launch steps a grid of CTAs of kFusedWarps warps, 32 / G envs per warp.
+template <int G, int SLOTS, int NC, bool RAW = false, bool RAGGED = false, bool TILED = false>
+__global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
+    world_step_kernel(const StepParams p) {
+  constexpr int EPW = 32 / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  if constexpr (!RAGGED && !RAW) {
+    // listed stepping: a block past the end of the list has nothing to do
+    // (uniform over the block, before its first barrier)
+    if (p.env_list && (int)(blockIdx.x * kFusedWarps * EPW) >= *p.env_count) return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int NL = NC > 0 ? NC : p.N;
+  world_step_body<G, SLOTS, NC, RAW, RAGGED, TILED>(
+      p, smem, &s_mbar, warp, (blockIdx.x * kFusedWarps + warp) * EPW,
+      smem + warp * EPW * fused_env_bytes(NL, G));
+}
+
+// ---- ragged worlds in one persistent launch ------------------------------
+// Every size class of a packed ragged world in one launch: each warp takes
+// work items from an atomic counter (one atomicAdd by lane 0 per item; no
+// warp ever waits on another) until the queue is empty.  An item is one
+// warp's worth of envs of one class (32 / G of them); items are numbered
+// largest class first, so the longest items start first and the short ones
+// fill the tail.  The classes' lane layouts are (kPersistLanes, kPersistSlots in params.cuh).
+// Each warp owns RaggedQueueParams::slab bytes of shared memory, the most
+// any class needs for one warp's envs.
+__host__ __device__ inline int persist_slab_bytes() {
+  int m = 0;
+  for (int c = 0; c < 5; ++c) {
+    const int cap = 8 << c, g = c == 0 || c == 1 ? 8 : (c == 2 ? 16 : 32);
+    const int b = (32 / g) * fused_env_bytes(cap, g);
+    m = b > m ? b : m;
+  }
+  return m;
+}
+constexpr int kPersistMinBlocks = 4;  // resident CTAs per SM the registers target
+
+__global__ void __launch_bounds__(kFusedWarps * 32, kPersistMinBlocks)
+    ragged_persistent_kernel(const RaggedQueueParams q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *slab = smem + warp * q.slab;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(q.queue, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= q.n_items) break;
+    // class of the item: items run class 4 (largest) first, class 0 last
+    if (item < q.item_end[4]) {
+      world_step_body<32, 4, 0, false, true, true>(q.p[4], smem, nullptr, warp, item * 1, slab);
+    } else if (item < q.item_end[3]) {
+      world_step_body<32, 2, 0, false, true, true>(q.p[3], smem, nullptr, warp,
+                                                   (item - q.item_end[4]) * 1, slab);
+    } else if (item < q.item_end[2]) {
+      world_step_body<16, 2, 0, false, true, true>(q.p[2], smem, nullptr, warp,
+                                                   (item - q.item_end[3]) * 2, slab);
+    } else if (item < q.item_end[1]) {
+      world_step_body<8, 2, 0, false, true, true>(q.p[1], smem, nullptr, warp,
+                                                  (item - q.item_end[2]) * 4, slab);
+    } else {
+      world_step_body<8, 1, 0, false, true, true>(q.p[0], smem, nullptr, warp,
+                                                  (item - q.item_end[1]) * 4, slab);
+    }
+    __syncwarp();
+  }
 }
 
 }  // namespace vmas

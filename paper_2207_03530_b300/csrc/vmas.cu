@@ -154,6 +154,33 @@ int launch_ragged_class(const StepParams &p, int G, int slots, int n_envs, cudaS
   }
 }
 
+int launch_ragged_persistent(vmas::RaggedQueueParams q, cudaStream_t st) {
+  if (q.n_items <= 0) return VMAS_OK;
+  q.slab = vmas::persist_slab_bytes();
+  const int smem = vmas::kFusedWarps * q.slab;
+  static int resident = 0, sms = 0;  // per process: one device model
+  if (!resident) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(vmas::ragged_persistent_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    int dev = 0;
+    VMAS_CUDA(cudaGetDevice(&dev));
+    VMAS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VMAS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &resident, vmas::ragged_persistent_kernel, vmas::kFusedWarps * 32, smem));
+    if (resident < 1) resident = 1;
+  }
+  // one wave of resident CTAs, fewer when there are fewer items than warps
+  const int need = (q.n_items + vmas::kFusedWarps - 1) / vmas::kFusedWarps;
+  const int grid = std::min(need, sms * resident);
+  vmas::ragged_persistent_kernel<<<grid, vmas::kFusedWarps * 32, smem, st>>>(q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "ragged_persistent_kernel launch");
+  return VMAS_OK;
+}
+
 // Lanes per environment: the smallest group that holds every entity in at
 // most 4 slots (N <= 8: 4 lanes, <= 32: 8, <= 64: 16, else 32).
 int group_lanes(int N) {

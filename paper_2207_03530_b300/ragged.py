@@ -85,6 +85,18 @@ class RaggedWorld:
         _lib.check(self._L.vmas_ragged_set_tuning(self._h, arr.ctypes.data if arr is not None else None,
                                                   int(steps_per_launch)))
 
+    @property
+    def persistent(self) -> bool:
+        """True when every size class runs in one persistent launch (atomic
+        work queue); False for one launch per class."""
+        v = ctypes.c_int32()
+        _lib.check(self._L.vmas_ragged_get_schedule(self._h, ctypes.byref(v)))
+        return bool(v.value)
+
+    @persistent.setter
+    def persistent(self, on: bool) -> None:
+        _lib.check(self._L.vmas_ragged_set_schedule(self._h, 1 if on else 0))
+
     def autotune(self, actions: torch.Tensor) -> None:
         _lib.check(self._L.vmas_ragged_autotune(self._h, actions.data_ptr(), int(actions.shape[0]),
                                                 _stream()))

@@ -19,14 +19,25 @@ def _setup(n_envs, seed, dense=True, T=50):
     return sc, World(sc), act, goals
 
 
+# Gates.  The gradient is a chain of ~150 substep Jacobians evaluated in
+# FP32: rounding of 6e-8 per operation, accumulated as a random walk over
+# the substeps, gives about 7e-7 of the largest gradient entry; contact
+# Jacobians (stiffness c / k times h^2 / m) amplify it where contacts
+# cluster, measured up to 4.6e-6 in the dense 64-env scene.  GRAD_TOL
+# leaves a factor of 2 over that.  The loss is a sum of squares of FP32
+# positions: relative error a few times 1e-7.
+GRAD_TOL = 1e-5
+LOSS_TOL = 1e-6
+
+
 def _relerr(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-12)
 
 
 @pytest.mark.parametrize("dense", [False, True])
 def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense):
-    """64 envs x 50 steps x 3 substeps: loss to 1e-4 and gradient to 2e-3 of
-    the oracle's (normwise, per tensor); FP32 through 150 substeps of stiff
+    """64 envs x 50 steps x 3 substeps: loss and gradient against the
+    oracle's (normwise, per tensor); FP32 through 150 substeps of stiff
     contacts."""
     from paper_2207_03530_b300.diff import rollout_loss
 
@@ -36,9 +47,11 @@ def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense):
     loss = rollout_loss(w, a, g, ckpt_every=10)
     loss.sum().backward()
     ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
-    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= 1e-4
+    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= LOSS_TOL
     err = _relerr(a.grad.cpu().numpy(), ref_grad)
-    assert err <= 2e-3, err
+    print("\n[adjoint] 64 envs dense=%s: loss err %.2e, gradient err %.2e"
+          % (dense, _relerr(loss.detach().cpu().numpy(), ref_loss), err))
+    assert err <= GRAD_TOL, err
     # the world's own state is untouched by the differentiable rollout
     assert np.array_equal(w.state().cpu().numpy(), sc.init_state)
     w.close()
@@ -56,8 +69,10 @@ def test_full_config_gradient_on_sampled_envs(vmas_lib, orc):
     pick = np.array([0, 1234, 2047, 4095])
     sub = sc.subset(pick)
     ref_loss, ref_grad = orc.rollout_grad(sub, sub.init_state, act[:, pick], goals[pick])
-    assert _relerr(loss.detach().cpu().numpy()[pick], ref_loss) <= 1e-4
-    assert _relerr(a.grad.cpu().numpy()[:, pick], ref_grad) <= 2e-3
+    assert _relerr(loss.detach().cpu().numpy()[pick], ref_loss) <= LOSS_TOL
+    print("\n[adjoint] 4,096 envs sampled: gradient err %.2e"
+          % _relerr(a.grad.cpu().numpy()[:, pick], ref_grad))
+    assert _relerr(a.grad.cpu().numpy()[:, pick], ref_grad) <= GRAD_TOL
     w.close()
 
 
@@ -137,6 +152,7 @@ def test_lane_groups_of_every_width(vmas_lib, orc, which, E):
     loss = rollout_loss(w, a, torch.from_numpy(goals).cuda(), ckpt_every=7)
     loss.sum().backward()
     ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
-    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= 1e-4
-    assert _relerr(a.grad.cpu().numpy(), ref_grad) <= 2e-3
+    assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= LOSS_TOL
+    print("\n[adjoint] %s E=%d: gradient err %.2e" % (which, E, _relerr(a.grad.cpu().numpy(), ref_grad)))
+    assert _relerr(a.grad.cpu().numpy(), ref_grad) <= GRAD_TOL
     w.close()

@@ -120,7 +120,7 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     rw.autotune(pact[:6])
     assert np.array_equal(rw.state().cpu().numpy(), before)
     lanes, tile = rw.tuning()
-    assert tile in (1, 2, 4, 8, 16) and all(l in (4, 8, 16, 32) for l in lanes)
+    assert tile in (1, 2, 4, 8, 16, 32, 64) and all(l in (4, 8, 16, 32) for l in lanes)
     rw.rollout(pact)
     rw.rollout(pact)  # graph replay
     got = rw.state().cpu().numpy()
@@ -136,8 +136,10 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     rw2.close()
 
 
-def test_extreme_env_sizes(vmas_lib, orc):
-    """Envs of 1 entity and of 128 entities (the largest class) side by side."""
+@pytest.mark.parametrize("persistent", [False, True])
+def test_extreme_env_sizes(vmas_lib, orc, persistent):
+    """Envs of 1 entity and of 128 entities (the largest class) side by side,
+    under either schedule."""
     from paper_2207_03530_b300.ragged import RaggedWorld
 
     big = scenes.mixed_scene(1, 3)
@@ -155,6 +157,7 @@ def test_extreme_env_sizes(vmas_lib, orc):
     rw = RaggedWorld([1, n_big], shape, flags, size_a, size_b, mass, inertia, st,
                      substeps=2, dt=0.05, drag=0.1)
     assert rw.class_envs[0] == 1 and rw.class_envs[4] == 1
+    rw.persistent = persistent
     pact = torch.zeros((rw.n_action_rows, 3), device="cuda")
     rw.step(pact)
     got = rw.state().cpu().numpy()
@@ -205,6 +208,7 @@ def test_full_config_sampled_envs(vmas_lib, orc):
     rw.autotune(pact[:8])
     lanes, tile = rw.tuning()
     rw2.set_tuning(lanes, tile)
+    rw2.persistent = rw.persistent
     rw.rollout(pact[:1])
     got = rw.state().cpu().numpy()
     full, sel = _unpack_state(got, counts, sc.n_entities)
@@ -220,3 +224,60 @@ def test_full_config_sampled_envs(vmas_lib, orc):
     rw.close()
     rw2.check()
     rw2.close()
+
+
+PERSIST_LANES = [8, 8, 16, 32, 32]  # the persistent schedule's fixed lanes per class
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed):
+    """Every size class in one persistent launch (warps take one warp's worth
+    of envs at a time from an atomic work queue, largest class first):
+    against the FP64 oracle, and bitwise equal to the per-class launches
+    with the same lanes per class, stepped one at a time and in tiled,
+    graph-captured rollouts (replayed twice)."""
+    sc, counts = scenes.ragged_scene(300, seed)
+    act = scenes.make_actions(sc, 8, seed)
+    per, pers = _ragged(sc, counts), _ragged(sc, counts)
+    assert (pers.class_envs > 0).sum() >= 4
+    per.set_tuning(PERSIST_LANES, 1)
+    pers.persistent = True
+    assert pers.persistent and not per.persistent
+    pact = torch.from_numpy(_packed_actions(per, sc, act)).cuda()
+    for t in range(2):
+        per.step(pact[t])
+        pers.step(pact[t])
+    a, b = per.state().cpu().numpy(), pers.state().cpu().numpy()
+    assert np.array_equal(a, b)
+    got, sel = _unpack_state(b, counts, sc.n_entities)
+    ref = orc.step(sc, sc.init_state, act[:2], threads=8)
+    assert normwise_err(got[sel], ref[sel]).max() <= TOL
+    for rw in (per, pers):
+        rw.set_tuning(None if rw is pers else PERSIST_LANES, 3)
+        rw.rollout(pact[2:])
+        rw.rollout(pact[2:])  # replay of the captured graph
+    assert np.array_equal(per.state().cpu().numpy(), pers.state().cpu().numpy())
+    for rw in (per, pers):
+        rw.check()
+        rw.close()
+
+
+@pytest.mark.parametrize("n_envs", [0, 1, 3, 37])
+def test_persistent_schedule_small_worlds(vmas_lib, orc, n_envs):
+    """Fewer work items than warps, classes left empty, and an empty world."""
+    sc, counts = scenes.ragged_scene(max(n_envs, 1), 9)
+    if n_envs == 0:
+        sc, counts = sc.subset([]), counts[:0]
+    rw = _ragged(sc, counts)
+    rw.persistent = True
+    act = scenes.make_actions(sc, 3, 2)
+    pact = torch.from_numpy(_packed_actions(rw, sc, act)).cuda() if n_envs else \
+        torch.zeros((3, 0, 3), device="cuda")
+    rw.set_tuning(None, 2)
+    rw.rollout(pact)
+    if n_envs:
+        got, sel = _unpack_state(rw.state().cpu().numpy(), counts, sc.n_entities)
+        ref = orc.step(sc, sc.init_state, act, threads=8)
+        assert normwise_err(got[sel], ref[sel]).max() <= TOL
+    rw.check()
+    rw.close()

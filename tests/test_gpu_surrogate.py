@@ -8,10 +8,10 @@
   same rounding), neighbour masks exactly.
 * Network output: the rounding points are the same on both sides; what is
   left is FP32 summation order and the rare activation that rounds to the
-  neighbouring bfloat16 value, so the output agrees to 5e-3 relative (norm).
+  neighbouring bfloat16 value (FWD_TOL below, relative, norm).
 * Gradient: the CUDA backward feeds bfloat16 copies of the upstream
   gradients to its GEMMs (2^-9 relative each), the reference stays in FP64:
-  every parameter block agrees to 3e-2 relative (Frobenius norm).
+  every parameter block within GRAD_TOL (relative, Frobenius norm).
 * Fallback: envs that fall back to the plain step are bitwise equal to it;
   the rest take the prediction.
 """
@@ -23,6 +23,25 @@ from paper_2207_03530_b300 import scenes
 
 pytestmark = pytest.mark.gpu
 
+
+# Gates, from where the GPU and the FP64 reference can differ.  Both round
+# at the same points (bfloat16 weights and activations), so the forward
+# differs only where FP32 accumulation order moves a pre-activation across a
+# bfloat16 rounding boundary: with K <= 128 terms the accumulated FP32
+# difference is about K 2^-24 relative, a fraction 128 2^-24 / 2^-9 = 4e-3
+# of activations sit that close to a boundary, and each such flip moves its
+# activation by one bfloat16 step (2^-8 relative): normwise 2^-8 sqrt(4e-3)
+# = 2.5e-4.  FWD_TOL is twice that.  The backward feeds bfloat16 copies of
+# the upstream gradient to each GEMM (the reference keeps FP64): each
+# rounding is a relative error uniform in +-2^-9 (RMS 1.1e-3), and the
+# deepest block (We1) sits behind five of them: RMS 1.1e-3 sqrt(5) =
+# 2.5e-3.  GRAD_TOL is twice that; b3's gradient (the FP32 sum of the
+# output gradient) meets no rounding.  Measured: forward <= 1.1e-4,
+# gradient blocks <= 1.9e-3, b3 2.8e-6, loss 1.7e-8.
+FWD_TOL = 5e-4
+GRAD_TOL = 5e-3
+GRAD_TOL_B3 = 1e-5
+LOSS_TOL = 1e-6
 
 def _bf(x):
     """bfloat16 rounding (nearest even) of float32 values, as float64."""
@@ -182,7 +201,9 @@ def test_forward_matches_reference(vmas_lib, E, crowd, mode):
     ref = S.forward(w64, node, edge, mask)
     w, sur, out = _cuda_forward(sc, w64, act, mode)
     err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
-    assert err <= 5e-3, err
+    print("\n[surrogate] forward %s E=%d crowd=%.2f: err %.2e, max abs %.2e"
+          % (mode, E, crowd, err, np.abs(out - ref).max()))
+    assert err <= FWD_TOL, err
     w.close()
     sur.close()
 
@@ -203,7 +224,8 @@ def test_fused_forward_full_size_sampled(vmas_lib):
                                   sub.size_a[:, :16], sub.mass[:, :16])
     ref = S.forward(w64, node, edge, mask)
     got = out.reshape(E, 16, 8)[pick].reshape(-1, 8)
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 5e-3
+    print("\n[surrogate] forward 262,144 sampled: err %.2e" % (np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= FWD_TOL
     w.close()
     sur.close()
 
@@ -252,14 +274,16 @@ def test_gradient_matches_reference(vmas_lib):
     loss_r, g_r = S.loss_and_grad(w64, node, edge, mask, target.astype(np.float64))
     w, sur, _ = _cuda_forward(sc, w64, act)
     loss, grad = sur.loss_grad(w, torch.from_numpy(act).cuda(), torch.from_numpy(target).cuda())
-    assert float(loss.item()) == pytest.approx(loss_r, rel=2e-3)
+    print("\n[surrogate] loss rel err %.2e" % abs(float(loss.item()) / loss_r - 1))
+    assert float(loss.item()) == pytest.approx(loss_r, rel=LOSS_TOL)
     from paper_2207_03530_b300.surrogate import unflatten
 
     g = unflatten(grad.cpu().numpy())
     for k in S.ORDER:
         ref = g_r[k]
         e = np.linalg.norm(g[k] - ref) / max(np.linalg.norm(ref), 1e-12)
-        assert e <= 3e-2, (k, e)
+        print("\n[surrogate] gradient %s: err %.2e" % (k, e))
+        assert e <= (GRAD_TOL_B3 if k == "b3" else GRAD_TOL), (k, e)
     w.close()
     sur.close()
 
