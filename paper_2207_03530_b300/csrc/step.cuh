@@ -95,14 +95,35 @@ __device__ __forceinline__ bool pair_active(uint32_t ki, uint32_t kj) {
 // cos and sin of a body angle, written out (no library call): Cody-Waite
 // reduction r = th - k pi/2 with pi/2 split in three floats (1.5703125 and
 // 4.8387050628662109e-4 have 8 and 12 significant bits, so k times them is
-// exact for |k| < 2^12), then the Taylor series of sin to r^9 and cos to r^10
-// on |r| <= pi/4 (truncation below 2e-9) and the quadrant k mod 4.  Absolute
-// error about 1e-7.  Shared by every kernel that needs a body frame.
+// exact for |k| < 2^12, i.e. |th| below about 6,400 rad), then the Taylor
+// series of sin to r^9 and cos to r^10 on |r| <= pi/4 (truncation below
+// 2e-9) and the quadrant k mod 4.  Angles beyond that range (a body spun for
+// a long rollout) take the same reduction in FP64 with pi/2 split in three
+// doubles of 33, 33 and 53 significant bits (k times the first two exact
+// for |k| < 2^20, i.e. |th| below about 1.6e6 rad; beyond, the error grows
+// in proportion to |th|; past about 1e15 rad, and for inf or NaN, the result
+// is a unit vector with no relation to th).
+// Absolute error about 1e-7.  Shared by every kernel that needs a body frame.
 __device__ __forceinline__ void body_axes(float th, float &c, float &s) {
-  const float k = rintf(th * 0.63661977236758134f);  // 2 / pi
-  float r = fmaf(-k, 1.5703125f, th);
-  r = fmaf(-k, 4.8387050628662109e-4f, r);
-  r = fmaf(-k, -4.3711388286737929e-8f, r);
+  float k = rintf(th * 0.63661977236758134f);  // 2 / pi
+  float r;
+  int q;
+  if (fabsf(k) < 4096.f) {
+    r = fmaf(-k, 1.5703125f, th);
+    r = fmaf(-k, 4.8387050628662109e-4f, r);
+    r = fmaf(-k, -4.3711388286737929e-8f, r);
+    q = ((int)k) & 3;
+  } else {
+    const double t = (double)th;
+    const double kd = rint(t * 0.63661977236758134308);
+    double rd = fma(-kd, 0x1.921fb544p+0, t);
+    rd = fma(-kd, 0x1.0b4611a6p-34, rd);
+    rd = fma(-kd, 0x1.3198a2e037073p-69, rd);
+    // beyond about 1e15 rad (and for inf or NaN) the reduction has lost
+    // every digit: take r = 0, so the result stays a unit vector
+    r = fabs(rd) <= 0.8 ? (float)rd : 0.f;
+    q = __double2int_rz(kd - 4.0 * floor(kd * 0.25)) & 3;  // k mod 4; NaN gives 0
+  }
   const float z = r * r;
   const float ps = fmaf(fmaf(fmaf(2.7557319223985891e-6f, z, -1.9841269841269841e-4f), z,
                              8.3333333333333333e-3f), z, -1.6666666666666667e-1f);
@@ -110,7 +131,6 @@ __device__ __forceinline__ void body_axes(float th, float &c, float &s) {
   const float pc = fmaf(fmaf(fmaf(fmaf(-2.7557319223985891e-7f, z, 2.4801587301587302e-5f), z,
                                   -1.3888888888888889e-3f), z, 4.1666666666666667e-2f), z, -0.5f);
   const float cr = fmaf(z, pc, 1.0f);
-  const int q = ((int)k) & 3;
   c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
   s = q == 0 ? sr : (q == 1 ? cr : (q == 2 ? -sr : -cr));
 }

@@ -449,7 +449,7 @@ def ragged_scene(n_envs: int = 65536, seed: int = 0, max_agents: int = 64,
         sc.init_state[envs, idx, 0] = x
         sc.init_state[envs, idx, 1] = y
         sc.init_state[envs, idx, 4] = rng.uniform(0, 2 * math.pi, size=len(envs)).astype(np.float32)
-    for q in range(max_agents):
+    for q in range(int(na.max()) if n_envs else 0):
         envs = envs_all[na > q]
         x, y = P.place_free(np.full(n_envs, 0.05), -0.9, 0.9, envs=envs)
         P.cx[envs, P.n], P.cy[envs, P.n], P.R[envs, P.n] = x, y, 0.05

@@ -307,7 +307,9 @@ def test_body_axes_accuracy(vmas_lib):
 
     rng = np.random.default_rng(0)
     th = np.concatenate([rng.uniform(-7, 7, 50000), rng.uniform(-2000, 2000, 50000),
-                         np.array([0, 1e-30, np.pi / 4, -np.pi / 4, np.pi / 2, np.pi, 4000.0])])
+                         rng.uniform(-1.6e6, 1.6e6, 50000),
+                         np.array([0, 1e-30, np.pi / 4, -np.pi / 4, np.pi / 2, np.pi, 4000.0,
+                                   6433.0, 6434.0, 6435.0, -6435.0, 1e4, -1e5, 1e6, 1.6e6])])
     th = th.astype(np.float32)
     d_th = torch.from_numpy(th).cuda()
     out = torch.empty((len(th), 2), device="cuda")
@@ -317,6 +319,15 @@ def test_body_axes_accuracy(vmas_lib):
     t64 = th.astype(np.float64)
     err = max(np.abs(cs[:, 0] - np.cos(t64)).max(), np.abs(cs[:, 1] - np.sin(t64)).max())
     assert err <= 1.5e-7, err
+    # beyond the stated range the result stays a defined, bounded value
+    far = np.array([3e6, -1e9, 3.4e38, -3.4e38, np.inf, np.nan], np.float32)
+    d_far = torch.from_numpy(far).cuda()
+    out = torch.empty((len(far), 2), device="cuda")
+    _lib.check(vmas_lib.vmas_debug_body_axes(d_far.data_ptr(), out.data_ptr(), len(far),
+                                             torch.cuda.current_stream().cuda_stream))
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.isfinite(o).all()
+    assert np.abs(np.hypot(o[:, 0], o[:, 1]) - 1.0).max() <= 1e-6
 
 
 def test_rollout_host_streams_every_state(vmas_lib):
