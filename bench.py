@@ -117,7 +117,7 @@ def _alu_roofline(ops_per_unit, units_per_s, note):
 
 
 # the sources the plain step kernel is compiled from
-STEP_KERNEL_SOURCES = ("contact.cuh", "params.cuh", "step.cuh", "step_fused.cuh")
+STEP_KERNEL_SOURCES = ("contact.cuh", "mbar.cuh", "params.cuh", "step.cuh", "step_fused.cuh")
 
 
 def _code_text(text):
@@ -634,7 +634,7 @@ def run_ragged(args):
     act = torch.rand((T, rw.n_action_rows, 3), device="cuda", generator=gen) * 2 - 1
     rw.autotune(act[:64])
     lanes, tile = rw.tuning()
-    persistent = rw.persistent
+    schedule = rw.schedule
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, args.steps // 100)
     cs = ClockSampler(torch.device("cuda", 0))
@@ -657,14 +657,15 @@ def run_ragged(args):
     # A/B of the two schedules: one launch per size class (autotuned lanes)
     # against one persistent launch over every class (atomic work queue), at
     # several steps per launch
+    names = {0: "per-class", 1: "persistent-128reg", 2: "persistent-96reg"}
     ab = []
-    for sched in (False, True):
+    for sched in (0, 1, 2):
         for t in sorted({tile, 8, 16, 32}):
-            rw.persistent = sched
+            rw.schedule = sched
             rw.set_tuning(lanes, t)
-            ab.append({"schedule": "persistent" if sched else "per-class", "steps_per_launch": t,
+            ab.append({"schedule": names[sched], "steps_per_launch": t,
                        "env_steps_per_s": E * T / (timed_rollout() / 1e3)})
-    rw.persistent = persistent
+    rw.schedule = schedule
     rw.set_tuning(lanes, tile)
     rw.close()
     del act
@@ -691,7 +692,7 @@ def run_ragged(args):
         "roofline": _hbm_roofline(b_env, value, "latency-bound size classes "
                                   "(ncu: the 128-entity class)"),
         "entities": int(counts.sum()), "envs": E, "lanes_per_class": [int(x) for x in lanes],
-        "steps_per_launch": tile, "schedule": "persistent" if persistent else "per-class",
+        "steps_per_launch": tile, "schedule": names[schedule],
         "schedules_ab": ab, "padded_regular_world_value": padded, "clocks": cs.summary(),
         "dtype": "f32",
         "data": "synthetic",
@@ -790,6 +791,54 @@ def run_surrogate(args):
             res[S].update({"plain_s1_value": out["plain_s1"]["value"],
                            "plain_s1_mean_pos_err_50": e1, "plain_s1_pos_err_at_50": e1_end})
         del out
+    # the box world (the paper-scale scene: 16 agents, 4 boxes, 4 walls), the
+    # network trained on its plain-step transitions and run on the layered
+    # (tcgen05) path; errors for the agents and for the boxes
+    scb = scenes.paper_scene(E, args.seed)
+    actb = torch.rand((T, E, scb.n_actuated, 3), device="cuda", generator=gen) * 2 - 1
+    surb = Surrogate(max(E, E_train), seed=args.seed)
+    trainb = train_on_plain_step(surb, E_train, args.train_steps, args.lr, args.seed + 2000,
+                                 log=sys.stderr, boxes=True)
+    box_res = {}
+    for name, mode, sc_ in (("plain", False, scb), ("surrogate", "layered", scb),
+                            ("plain_s1", False, dataclasses_replace(scb, substeps=1))):
+        w = World(sc_)
+        pos = torch.empty((T, E, 20, 2), device="cuda")
+        nfb = torch.zeros(T, dtype=torch.int32, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * T)]
+        with cs:
+            for t in range(T):
+                ev[2 * t].record()
+                if mode:
+                    surb.step(w, actb[t], n_fallback=nfb[t:t + 1])
+                else:
+                    w.step(actb[t])
+                ev[2 * t + 1].record()
+                pos[t] = w.state()[:, :20, :2]
+            torch.cuda.synchronize()
+        ms = statistics.median(ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(3, T))
+        box_res[name] = dict(pos=pos, value=E / (ms / 1e3), nfb=float(nfb.float().mean()))
+        w.close()
+    surb.check()
+    surb.close()
+    refb = box_res["plain"]["pos"]
+
+    def body_err(p_):
+        d = (p_ - refb).norm(dim=-1)
+        return float(d[..., :16].mean()), float(d[..., 16:].mean())
+
+    box_world = {
+        "workload": "%d envs x (16 agent spheres + 4 movable boxes + 4 walls), 5 substeps, "
+                    "%d steps" % (E, T),
+        "plain_value": box_res["plain"]["value"],
+        "surrogate_value": box_res["surrogate"]["value"],
+        "surrogate_mean_pos_err_50_agents_boxes": body_err(box_res["surrogate"]["pos"]),
+        "plain_s1_value": box_res["plain_s1"]["value"],
+        "plain_s1_mean_pos_err_50_agents_boxes": body_err(box_res["plain_s1"]["pos"]),
+        "fallback_envs_per_step": box_res["surrogate"]["nfb"],
+        "train": {"seconds": trainb[0], "transitions": trainb[2], "envs": E_train,
+                  "steps": args.train_steps, "final_loss": trainb[1], "lr": args.lr}}
+    del box_res, refb
     r5 = res[5]
     # useful network FLOPs per env: the edge MLP on every present edge (up to
     # 6 nearest agents within 0.3, counted on the start state) and the node
@@ -818,7 +867,8 @@ def run_surrogate(args):
         "plain_s1_mean_pos_err_50": r5["plain_s1_mean_pos_err_50"],
         "plain_s1_pos_err_at_50": r5["plain_s1_pos_err_at_50"],
         "fallback_envs_per_step": r5["fallback_envs_per_step"], "train": r5["train"],
-        "substeps_1": {k: v for k, v in res[1].items()}, "clocks": cs.summary(),
+        "substeps_1": {k: v for k, v in res[1].items()}, "box_world": box_world,
+        "clocks": cs.summary(),
         "dtype": "bf16 network / f32 fallback", "data": "synthetic",
         "config": {"workload": "%d envs x (16 agent spheres + 4 walls), 5 (and 1) substeps, "
                                "%d steps" % (E, T)}}), flush=True)

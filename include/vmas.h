@@ -228,16 +228,20 @@ int vmas_check(vmas_world *world, void *stream, int32_t *bits);
  *  - per class (schedule 0): each class by the fused kernel compiled for its
  *    choice of lanes per environment (4, 8, 16 or 32), the classes' launches
  *    side by side;
- *  - persistent (schedule 1): every class in ONE launch, whose warps take
- *    one warp's worth of envs at a time from an atomic work queue, largest
- *    class first, with fixed lanes per class (8, 8, 16, 32, 32).  No warp
- *    ever waits on another: a warp takes its next item with one atomic add.
+ *  - persistent (schedules 1 and 2): every class in ONE launch, whose warps
+ *    take one warp's worth of envs at a time from an atomic work queue,
+ *    largest class first, with fixed lanes per class (8, 8, 16, 32, 32).  No
+ *    warp ever waits on another: a warp takes its next item with one atomic
+ *    add.  Schedule 1 is the kernel built for 128 registers (4 CTAs per SM),
+ *    schedule 2 the same kernel built for 96 (5 CTAs per SM; the largest
+ *    class spills registers).
  * Rollouts run steps_per_launch world steps per launch and are captured once
  * into a CUDA graph per (actions buffer, n_steps, tuning, schedule), then
  * replayed.  vmas_ragged_autotune times the lanes per class, then every
- * steps_per_launch under both schedules, on the caller's actions (the world
- * state is restored afterwards), and keeps the fastest.  Both schedules give
- * bitwise the same result for the same lanes per class. */
+ * steps_per_launch under every schedule as a graph-captured rollout of
+ * n_steps steps, on the caller's actions (the world state is restored
+ * afterwards), and keeps the fastest.  Every schedule gives bitwise the same
+ * result for the same lanes per class. */
 typedef struct vmas_ragged vmas_ragged;
 typedef struct {
   int32_t n_envs, substeps;
@@ -266,10 +270,11 @@ int vmas_ragged_check(vmas_ragged *world, void *stream, int32_t *bits);
 int vmas_ragged_set_tuning(vmas_ragged *world, const int32_t *lanes, int32_t steps_per_launch);
 int vmas_ragged_get_tuning(const vmas_ragged *world, int32_t *lanes, int32_t *steps_per_launch);
 int vmas_ragged_autotune(vmas_ragged *world, const float *d_actions, int32_t n_steps, void *stream);
-/* Schedule: 0 = per-class launches (default at create), 1 = one persistent
- * launch with an atomic work queue.  VMAS_EINVAL for other values. */
-int vmas_ragged_set_schedule(vmas_ragged *world, int32_t persistent);
-int vmas_ragged_get_schedule(const vmas_ragged *world, int32_t *persistent);
+/* Schedule: 0 = per-class launches (default at create), 1 or 2 = one
+ * persistent launch with an atomic work queue (128- or 96-register build).
+ * VMAS_EINVAL for other values. */
+int vmas_ragged_set_schedule(vmas_ragged *world, int32_t schedule);
+int vmas_ragged_get_schedule(const vmas_ragged *world, int32_t *schedule);
 
 /* LIDAR (section 3: agents can carry LIDAR sensors).  Every actuated
  * entity of every env casts n_rays rays from its centre at angles
@@ -440,17 +445,32 @@ int vmas_sur_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions
  * NULL. */
 int vmas_sur_debug_features(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
                             uint16_t *d_node, uint16_t *d_edge, float *d_mask, void *stream);
+/* Wait for `stream` and return VMAS_EDEVICE (clearing the word) if one of
+ * the surrogate's kernels raised its device error word (VMAS_DEVERR_TIMEOUT:
+ * a tensor-core GEMM's bounded wait for its copies or MMAs ran out; the CTA
+ * left its rows unwritten and freed its tensor memory). */
+int vmas_sur_check(vmas_surrogate *sur, void *stream, int32_t *bits);
 /* Diagnostic: the surrogate's GEMM, C [M][N] = A B with A(m, k) =
  * trans_a ? a[k lda + m] : a[m lda + k] and B(k, n) = trans_b ? b[n ldb + k]
  * : b[k ldb + n], bfloat16 operands (bits), FP32 accumulation; plus bias [N]
  * (FP32, may be NULL) into d_out_f32 [M][N] (may be NULL) and GELU (gelu != 0)
  * of it rounded into d_out_bf16 [M][N] (may be NULL).  splits > 1 sums K in
- * that many chunks (then no bias, GELU or bfloat16 output); it allocates a
- * temporary buffer and waits for `stream`. */
+ * that many chunks (then no bias, GELU or bfloat16 output).  Untransposed A
+ * with transposed B, K a multiple of 16 up to 128, N up to 128 and no split
+ * run on the tcgen05 GEMM (tensor memory accumulators, TMA-staged operands);
+ * the rest on the warp-level mma GEMM.  It allocates temporary buffers,
+ * waits for `stream`, and returns VMAS_EDEVICE if a bounded wait of the
+ * tcgen05 GEMM ran out. */
 int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N, int32_t K,
                          const uint16_t *d_a, int32_t lda, const uint16_t *d_b, int32_t ldb,
                          const float *d_bias, int32_t gelu, float *d_out_f32,
                          uint16_t *d_out_bf16, int32_t splits, void *stream);
+
+/* Diagnostic: which GEMM the surrogate's kernels use, process-wide: 0 = the
+ * tcgen05 GEMM wherever the shape allows (the default), 1 = the warp-level
+ * mma GEMM only (for comparisons), -1 = leave it.  tc_launches (may be NULL)
+ * receives the number of tcgen05 GEMM launches in this process so far. */
+int vmas_debug_gemm_engine(int32_t engine, int64_t *tc_launches);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *vmas_last_error(void);

@@ -34,6 +34,20 @@ differences of the unrounded loss; features against hand-computed values.
 
 Training loss: mean over agents and the 4 outputs of (out - target)^2, the
 target being the true step's deltas divided by (0.01, 0.01, 0.1, 0.1).
+
+The box world (the paper-scale layout: 16 agents, 4 movable rotatable boxes,
+4 walls) runs the same network on 20 nodes per env (``features_box``):
+
+  node features of a box: as an agent's with R = its half diagonal in place
+      of r (10 R in slot 4, the wall gaps of its bounding circle), and
+      10: 1, 11: cos theta, 12: sin theta, 13: 0.1 omega, 14: 0.01 tau / I;
+  edges: the 6 nearest other nodes (agents or boxes) within 0.3, with the
+      surface gap taken between bounding circles, |d| - R_i - R_j, and for a
+      box neighbour 7: 1, 8: cos theta_j, 9: sin theta_j, 10: 0.1 omega_j;
+  outputs: a box uses 6 (theta' = theta + 0.1 out4, omega' = omega + out5);
+  loss: the mean of (out - target)^2 over the outputs each node uses.
+An agent, and an agent's edge to an agent, read the same values in both
+worlds.
 """
 from __future__ import annotations
 
@@ -44,6 +58,8 @@ import numpy as np
 K = 6
 RADIUS = 0.3
 X_SCALE, V_SCALE = 0.01, 0.1
+TH_SCALE, OM_SCALE = 0.1, 1.0
+AGENTS, BOXES = 16, 4
 SHAPES = {"We1": (64, 16), "be1": (64,), "We2": (64, 64), "be2": (64,),
           "W1": (128, 80), "b1": (128,), "W2": (128, 128), "b2": (128,),
           "W3": (8, 128), "b3": (8,)}
@@ -105,6 +121,75 @@ def features(state, actions, radius_a, mass):
     return node, edge, mask
 
 
+def _bounding(shape, a, b):
+    """Bounding radius: a sphere's radius, a box's half diagonal."""
+    return math.hypot(0.5 * a, 0.5 * b) if shape == 1 else a
+
+
+def features_box(state, actions, shape, size_a, size_b, mass, inertia):
+    """Box world: state [E, 24, 6] (16 agents, 4 boxes, 4 walls), actions
+    [E, >= 20, 3], per-entity arrays [E, 24].  Returns node [E*20, 16], edge
+    [E*20, K, 16], mask [E*20, K] (float64, unrounded)."""
+    state = np.asarray(state, np.float64)
+    E = state.shape[0]
+    NN = AGENTS + BOXES
+    node = np.zeros((E * NN, 16))
+    edge = np.zeros((E * NN, K, 16))
+    mask = np.zeros((E * NN, K))
+    for e in range(E):
+        R = [_bounding(int(shape[e, i]), float(size_a[e, i]), float(size_b[e, i]))
+             for i in range(NN)]
+        box = [int(shape[e, i]) == 1 for i in range(NN)]
+        for i in range(NN):
+            row = e * NN + i
+            x, y, vx, vy, th, om = state[e, i]
+            m = float(mass[e, i])
+            gaps = [1.0 - x - R[i], 1.0 + x - R[i], 1.0 - y - R[i], 1.0 + y - R[i]]
+            node[row, :10] = [10 * vx, 10 * vy, actions[e, i, 0] / m, actions[e, i, 1] / m,
+                              10 * R[i], 1.0 / m] + [min(g, RADIUS) / RADIUS for g in gaps]
+            if box[i]:
+                I = float(inertia[e, i])
+                if I == 0.0:
+                    I = m * (float(size_a[e, i]) ** 2 + float(size_b[e, i]) ** 2) / 12.0
+                node[row, 10:15] = [1.0, math.cos(th), math.sin(th), 0.1 * om,
+                                    0.01 * actions[e, i, 2] / I]
+            cand = []
+            for j in range(NN):
+                if j == i:
+                    continue
+                dx, dy = state[e, j, 0] - x, state[e, j, 1] - y
+                dist = math.sqrt(dx * dx + dy * dy)
+                if dist < RADIUS:
+                    cand.append((dist, j, dx, dy))
+            cand.sort(key=lambda c: (c[0], c[1]))
+            for k, (dist, j, dx, dy) in enumerate(cand[:K]):
+                edge[row, k, :7] = [dx / RADIUS, dy / RADIUS, 10 * (state[e, j, 2] - vx),
+                                    10 * (state[e, j, 3] - vy), 10 * R[j],
+                                    (dist - R[i] - R[j]) / RADIUS, 1.0]
+                if box[j]:
+                    edge[row, k, 7:11] = [1.0, math.cos(state[e, j, 4]), math.sin(state[e, j, 4]),
+                                          0.1 * state[e, j, 5]]
+                mask[row, k] = 1.0
+    return node, edge, mask
+
+
+def used_outputs(n_envs, nodes):
+    """Outputs each row uses: 4 for an agent (node < 16), 6 for a box."""
+    return np.tile(np.where(np.arange(nodes) < AGENTS, 4, 6), n_envs)
+
+
+def targets_box(state, next_state):
+    """Normalised one-step deltas [E*20, 6] of the nodes of the box world
+    (x, y over 0.01, vx, vy over 0.1, theta over 0.1, omega over 1; 0 in the
+    angle columns of agents)."""
+    s, n = np.asarray(state, np.float64), np.asarray(next_state, np.float64)
+    NN = AGENTS + BOXES
+    d = (n[:, :NN, :6] - s[:, :NN, :6]) / np.array(
+        [X_SCALE, X_SCALE, V_SCALE, V_SCALE, TH_SCALE, OM_SCALE])
+    d[:, :AGENTS, 4:] = 0.0
+    return d.reshape(-1, 6)
+
+
 def init_weights(seed=0):
     """Deterministic initialisation (uniform fan-in scaling), weights rounded
     to bfloat16; W3 rows 4..7 and all biases start at zero."""
@@ -144,15 +229,20 @@ def forward(w, node, edge, mask, round_bf=True, keep=False):
     return out
 
 
-def loss_and_grad(w, node, edge, mask, target, round_bf=True):
-    """Loss mean((out[:, :4] - target)^2) and its gradient (FP64 backward
-    through the stored forward values)."""
+def loss_and_grad(w, node, edge, mask, target, round_bf=True, used=None):
+    """Loss: the mean of (out - target)^2 over the outputs each row uses
+    (``used`` [R], default 4 for every row; target [R, >= max used]), and
+    its gradient (FP64 backward through the stored forward values)."""
     R = node.shape[0]
     out, c = forward(w, node, edge, mask, round_bf, keep=True)
-    diff = out[:, :4] - target
-    loss = float((diff ** 2).mean())
-    d_out = np.zeros_like(out)
-    d_out[:, :4] = 2.0 * diff / (4 * R)
+    used = np.full(R, 4) if used is None else np.asarray(used)
+    cols = np.arange(8)[None, :] < used[:, None]
+    tgt = np.zeros((R, 8))
+    tgt[:, :target.shape[1]] = target
+    diff = np.where(cols, out - tgt, 0.0)
+    count = float(used.sum())
+    loss = float((diff ** 2).sum() / count)
+    d_out = 2.0 * diff / count
     g = {}
     g["W3"] = d_out.T @ c["h2"]
     g["b3"] = d_out.sum(0)

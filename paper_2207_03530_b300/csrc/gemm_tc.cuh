@@ -1,0 +1,293 @@
+// The surrogate's large GEMMs on the 5th-generation tensor cores (sm_103a):
+// C[m, n] = sum_k A[m][k] B[n][k] (+ bias[n], GELU on the bfloat16 copy),
+// bfloat16 operands, FP32 accumulation, for M up to millions of rows (16 per
+// env, or 96 for the edge MLP), N <= 128 and K <= 128 a multiple of 16: the
+// shapes of the network's layers and of their input gradients.
+//
+//   operands  cp.async.bulk.tensor (TMA) 2D tiles into shared memory with the
+//             128-byte swizzle, K-major: a 128-row tile of A per stage (two
+//             stages), the whole of B once per CTA; K past the tensor's end
+//             and rows past M are filled with zeros by the copy engine
+//   MMA       tcgen05.mma kind::f16 (M = 128, N = N rounded up to 16, K = 16
+//             per instruction), issued by one thread, accumulating in TMEM:
+//             two 128-column accumulators, so the MMAs of tile i + 1 run
+//             while the four warps read tile i back
+//   epilogue  tcgen05.ld (32 lanes x 32 bits: thread t of warp w owns TMEM
+//             lane 32 w + t, i.e. one output row), bias, FP32 and bfloat16
+//             stores, GELU (the same device function as the warp-mma path)
+//   waits     every mbarrier wait is bounded (about a second); a CTA whose
+//             wait runs out sets VMAS_DEVERR_TIMEOUT in the error word, waits
+//             (bounded) for its copies in flight, frees its TMEM and returns
+//
+// Persistent: a grid of at most two CTAs per SM (the shared-memory request is
+// padded so that no third fits, which keeps the two 256-column TMEM
+// allocations of an SM within its 512 columns) walks the 128-row tiles.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mbar.cuh"
+#include "surrogate.cuh"
+#include "vmas.h"
+
+namespace vmas {
+namespace sur {
+
+constexpr int kTcM = 128;                // rows per tile (the MMA's M)
+constexpr int kTcAtom = kTcM * 128;      // bytes of a 64-wide K slice of a tile
+constexpr int kTcCols = 256;             // TMEM columns per CTA (two accumulators)
+constexpr int kTcMinSmem = 80 * 1024;    // at most two CTAs per SM
+constexpr int kTcWaitTries = 1 << 20;    // polls of at most ~1 us each
+
+struct TcGemmArgs {
+  int M, N, K;         // N <= 128, K <= 128, K % 16 == 0
+  int n_pad;           // N rounded up to 16: the MMA's N and B's box height
+  int katoms;          // ceil(K / 64): 64-element K slices per tile
+  const float *bias;   // [N] or null
+  int act;             // 1: GELU on the bfloat16 output
+  float *out_f32;      // [M][ldc_f] or null
+  int ldc_f;
+  bf16 *out_bf;        // [M][ldc_b] or null
+  int ldc_b;
+  int *err;            // device error word
+  int vec_f, vec_b;    // 16-byte stores allowed (aligned bases, ldc_f % 4, ldc_b % 8)
+};
+
+__host__ __device__ inline int tc_smem_bytes(int katoms, int n_pad) {
+  const int b = 1024 + 2 * katoms * kTcAtom + katoms * n_pad * 128 + 64;
+  return b < kTcMinSmem ? kTcMinSmem : b;
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: 8-row groups 1024 bytes apart (stride byte offset), the
+// leading byte offset unused for this layout (1), descriptor version 1,
+// swizzle mode 2 (128 B).  `addr` is the shared-memory byte address of the
+// K slice's first element; the slice's 1024-byte atom must be aligned.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                   // leading byte offset (16 B, unused)
+  d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1u << 46;                   // version
+  d |= (uint64_t)2u << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, bfloat16 A and B,
+// both K-major, N >> 3 and M >> 4.
+__host__ __device__ inline uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcGemmArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KA = g.katoms;
+  unsigned char *sA = base;                        // [2 stages][KA atoms][128 rows][128 B]
+  unsigned char *sB = base + 2 * KA * kTcAtom;     // [KA atoms][n_pad rows][128 B]
+  unsigned long long *bar =
+      reinterpret_cast<unsigned long long *>(sB + KA * g.n_pad * 128);  // full[2], done[2], bfull
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 5);
+  const uint32_t full0 = smem_u32(&bar[0]), done0 = smem_u32(&bar[2]), bfull = smem_u32(&bar[4]);
+  const int tiles = (g.M + kTcM - 1) / kTcM;
+  const int mine = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const uint32_t a_bytes = (uint32_t)(KA * kTcAtom), b_bytes = (uint32_t)(KA * g.n_pad * 128);
+  const int ksteps = g.K / 16;
+  const uint32_t idesc = tc_idesc(kTcM, g.n_pad);
+
+  if (tid == 0) {
+    for (int q = 0; q < 5; ++q) mbar_init(smem_u32(&bar[q]), 1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // loads and MMA commits issued per stage (thread 0's counts)
+  int issued[2] = {0, 0}, committed[2] = {0, 0};
+  auto load_a = [&](int i) {  // thread 0: tile of local index i into stage i & 1
+    const int s = i & 1, row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM;
+    mbar_expect_tx(full0 + 8 * s, a_bytes);
+    for (int a = 0; a < KA; ++a)
+      tma_load_2d(smem_u32(sA + (s * KA + a) * kTcAtom), &tmA, 64 * a, row, full0 + 8 * s);
+    ++issued[s];
+  };
+  if (tid == 0 && mine > 0) {
+    mbar_expect_tx(bfull, b_bytes);
+    for (int a = 0; a < KA; ++a)
+      tma_load_2d(smem_u32(sB + a * g.n_pad * 128), &tmB, 64 * a, 0, bfull);
+    load_a(0);
+    if (mine > 1) load_a(1);
+  }
+  bool failed = false;  // thread 0: a wait of its own ran out
+  auto issue = [&](int i) {  // thread 0: the MMAs of local tile i, committed to done[i & 1]
+    const int s = i & 1;
+    if (i == 0 && !mbar_wait(bfull, 0, kTcWaitTries)) { failed = true; return; }
+    if (!mbar_wait(full0 + 8 * s, (uint32_t)((i >> 1) & 1), kTcWaitTries)) { failed = true; return; }
+    tc_fence_after();
+    const uint32_t a0 = smem_u32(sA + s * KA * kTcAtom), b0 = smem_u32(sB);
+    for (int j = 0; j < ksteps; ++j) {
+      const uint32_t off_a = (uint32_t)((j >> 2) * kTcAtom + (j & 3) * 32);
+      const uint32_t off_b = (uint32_t)((j >> 2) * g.n_pad * 128 + (j & 3) * 32);
+      tc_mma(tmem + (uint32_t)(s * 128), tc_desc(a0 + off_a), tc_desc(b0 + off_b), idesc,
+             j > 0 ? 1u : 0u);
+    }
+    tc_commit(done0 + 8 * s);
+    ++committed[s];
+  };
+  if (tid == 0 && mine > 0) issue(0);
+
+  for (int i = 0; i < mine; ++i) {
+    const int s = i & 1;
+    if (tid == 0 && i + 1 < mine && !failed) issue(i + 1);
+    const bool late = !mbar_wait(done0 + 8 * s, (uint32_t)((i >> 1) & 1), kTcWaitTries);
+    if (__syncthreads_or(late || failed)) {
+      failed = true;
+      break;
+    }
+    tc_fence_after();
+    // stage s is free once its MMAs have completed: prefetch tile i + 2
+    if (tid == 0 && i + 2 < mine) load_a(i + 2);
+    const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM + warp * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * 128);
+    for (int c0 = 0; c0 < g.n_pad; c0 += 16) {
+      float v[16];
+      tc_ld16(tbase + (uint32_t)c0, v);
+      if (row < g.M && c0 + 16 <= g.N) {
+        // a full 16-column block of this row
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (g.bias) v[q] += g.bias[c0 + q];
+        if (g.out_f32) {
+          float *o = g.out_f32 + (size_t)row * g.ldc_f + c0;
+          if (g.vec_f) {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+              *reinterpret_cast<float4 *>(o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[q] = v[q];
+          }
+        }
+        if (g.out_bf) {
+          bf16 *o = g.out_bf + (size_t)row * g.ldc_b + c0;
+          uint32_t w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float x0 = g.act ? gelu(v[2 * q]) : v[2 * q];
+            const float x1 = g.act ? gelu(v[2 * q + 1]) : v[2 * q + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            w[q] = *reinterpret_cast<const uint32_t *>(&h);
+          }
+          if (g.vec_b) {
+            reinterpret_cast<uint4 *>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<uint4 *>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              o[2 * q] = __ushort_as_bfloat16((unsigned short)(w[q] & 0xffffu));
+              o[2 * q + 1] = __ushort_as_bfloat16((unsigned short)(w[q] >> 16));
+            }
+          }
+        }
+      } else if (row < g.M) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int n = c0 + q;
+          if (n < g.N) {
+            float x = v[q];
+            if (g.bias) x += g.bias[n];
+            if (g.out_f32) g.out_f32[(size_t)row * g.ldc_f + n] = x;
+            if (g.out_bf) g.out_bf[(size_t)row * g.ldc_b + n] = __float2bfloat16_rn(g.act ? gelu(x) : x);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // both TMEM accumulators' readers are done before the next MMAs
+  }
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(g.err, VMAS_DEVERR_TIMEOUT);
+      // wait (bounded) for the copies still in flight into this CTA's memory
+      // and for the MMAs still reading it and writing TMEM
+      for (int s = 0; s < 2; ++s) {
+        if (issued[s] > 0) mbar_wait(full0 + 8 * s, (uint32_t)((issued[s] - 1) & 1), kTcWaitTries);
+        if (committed[s] > 0)
+          mbar_wait(done0 + 8 * s, (uint32_t)((committed[s] - 1) & 1), kTcWaitTries);
+      }
+      if (mine > 0) mbar_wait(bfull, 0, kTcWaitTries);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols)
+                 : "memory");
+  }
+}
+
+}  // namespace sur
+}  // namespace vmas

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -25,7 +26,8 @@ struct vmas_world {
   float dt = 0, drag = 0, gx = 0, gy = 0, c = 0, k = 0, vmax = 0;
   float skin = 0;  // candidate-list margin
   bool diff_ok = false;  // every entity a sphere, N <= 32 (differentiable rollout)
-  bool sur_ok = false;   // 16 actuated agent spheres then 4 fixed walls (surrogate)
+  bool sur_ok = false;   // a layout the learned surrogate serves (sur_layout != 0)
+  int sur_layout = 0;    // 1: 16 agent spheres + 4 walls; 2: 16 agents + 4 boxes + 4 walls
   bool stage_timeout_test = false;  // vmas_debug_stage_timeout
   int tile = 1;          // world steps per launch in vmas_rollout
   float *planes = nullptr;  // 6 * E * N
@@ -65,8 +67,9 @@ int launch_step(const StepParams &p, cudaStream_t st, bool tiled = false);
 // One launch of the step kernel over a ragged world's size class.
 int launch_ragged_class(const StepParams &p, int G, int slots, int n_envs, cudaStream_t st);
 // One persistent launch over every size class of a ragged world (q.slab is
-// filled in here); the caller zeroes *q.queue on `st` first.
-int launch_ragged_persistent(vmas::RaggedQueueParams q, cudaStream_t st);
+// filled in here); the caller zeroes *q.queue on `st` first.  budget 1: the
+// 128-register build (4 CTAs per SM), 2: the 96-register build (5 per SM).
+int launch_ragged_persistent(vmas::RaggedQueueParams q, int budget, cudaStream_t st);
 
 }  // namespace vmas_host
 

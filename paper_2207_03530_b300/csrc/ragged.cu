@@ -30,7 +30,8 @@ struct vmas_ragged {
   int lanes[kClasses] = {};          // chosen lanes per env
   int slots[kClasses] = {};          // chosen entities per lane
   int tile = 1;                      // steps per launch in rollouts
-  int persistent = 0;                // 1: one persistent launch per tile for all classes
+  int persistent = 0;                // 1, 2: one persistent launch per tile for all classes
+                                     // (128- or 96-register build)
   int *queue = nullptr;              // work-queue counters, one per launch of a rollout
   int queue_cap = 0;
   float *planes = nullptr;           // 6 planes x total, sorted order
@@ -134,7 +135,7 @@ int ragged_persist_tile(vmas_ragged *r, const float *d_actions, int tile, int *c
   }
   q.n_items = end;
   q.queue = counter;
-  return launch_ragged_persistent(q, st);
+  return launch_ragged_persistent(q, r->persistent, st);
 }
 
 // One tile of `tile` steps for every class, actions of the tile's first step
@@ -494,7 +495,7 @@ int vmas_ragged_set_tuning(vmas_ragged *r, const int32_t *lanes, int32_t steps_p
 
 int vmas_ragged_set_schedule(vmas_ragged *r, int32_t persistent) {
   if (!r) return fail(VMAS_EINVAL, "world is NULL");
-  if (persistent != 0 && persistent != 1) return fail(VMAS_EINVAL, "persistent must be 0 or 1");
+  if (persistent < 0 || persistent > 2) return fail(VMAS_EINVAL, "schedule must be 0, 1 or 2");
   r->persistent = persistent;
   ++r->version;
   return VMAS_OK;
@@ -525,6 +526,11 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
   cudaEvent_t a, b;
   VMAS_CUDA(cudaEventCreate(&a));
   VMAS_CUDA(cudaEventCreate(&b));
+  // every candidate starts from the caller's state: a state evolved by the
+  // earlier candidates' steps (more contacts, say) would bias the choice
+  auto restore = [&]() {
+    return cudaMemcpyAsync(r->planes, r->backup, bytes, cudaMemcpyDeviceToDevice, st);
+  };
   const int tiles[] = {1, 2, 4, 8, 16, 32, 64};
   constexpr int kTiles = (int)(sizeof(tiles) / sizeof(tiles[0]));
   int rc = VMAS_OK;
@@ -539,6 +545,7 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
       StepParams p = ragged_params(r, c);
       float ms = 0;
       for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {  // first pass warms up
+        restore();
         cudaEventRecord(a, st);
         for (int t = 0; t < n_steps && rc == VMAS_OK; ++t) {
           p.actions = d_actions + (size_t)t * r->total_act * 3;
@@ -553,26 +560,31 @@ int vmas_ragged_autotune(vmas_ragged *r, const float *d_actions, int32_t n_steps
     r->lanes[c] = best_g;
     r->slots[c] = r->cap[c] / best_g;
   }
-  // steps per launch, all classes together, under either schedule (the
-  // per-class launches with the lanes just chosen, or one persistent launch)
+  // steps per launch and schedule, all classes together, each timed as the
+  // graph-captured rollout it will run as (the per-class launches are graph
+  // branches that run side by side; a stream of direct launches would
+  // serialise them)
   float best = 3.4e38f;
   int best_tile = 1, best_sched = 0;
-  for (int sched = 0; sched < 2 && rc == VMAS_OK; ++sched) {
-    r->persistent = sched;
+  for (int sched = 0; sched < 3 && rc == VMAS_OK; ++sched) {
     for (int ti = 0; ti < kTiles && rc == VMAS_OK; ++ti) {
       const int tile = tiles[ti];
       if (tile > n_steps) break;
+      r->persistent = sched;
+      r->tile = tile;
+      ++r->version;
+      restore();
+      rc = vmas_ragged_rollout(r, d_actions, n_steps, stream);  // capture + warm-up
       float ms = 0;
-      for (int rep = 0; rep < 2 && rc == VMAS_OK; ++rep) {
+      if (rc == VMAS_OK) {
+        restore();
         cudaEventRecord(a, st);
-        for (int t = 0; t + tile <= n_steps && rc == VMAS_OK; t += tile)
-          rc = ragged_launch_tile(r, d_actions + (size_t)t * r->total_act * 3, tile, st);
+        rc = vmas_ragged_rollout(r, d_actions, n_steps, stream);  // replay
         cudaEventRecord(b, st);
         cudaEventSynchronize(b);
         cudaEventElapsedTime(&ms, a, b);
       }
-      const float per_step = ms / (float)((n_steps / tile) * tile);
-      if (per_step < best) { best = per_step; best_tile = tile; best_sched = sched; }
+      if (rc == VMAS_OK && ms < best) { best = ms; best_tile = tile; best_sched = sched; }
     }
   }
   r->tile = best_tile;

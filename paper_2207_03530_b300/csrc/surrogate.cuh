@@ -1,14 +1,18 @@
 // Learned surrogate of the world step (sm_103a): bfloat16 tensor-core GEMMs
-// with FP32 accumulation (warp-level mma.sync m16n8k16), and the feature,
-// aggregation, loss, GELU-backward and Adam kernels around them.
+// with FP32 accumulation (warp-level mma.sync m16n8k16 here, tcgen05 in
+// gemm_tc.cuh), and the feature, aggregation, loss, GELU-backward and Adam
+// kernels around them.
 //
-// Network (per agent of a walled 16-agent sphere world; all sizes fixed):
+// Network (per node of a walled world: 16 agent spheres, and in the box
+// world also 4 movable boxes; all widths fixed):
 //   node features n (16), edge features e (16) for up to K = 6 nearest other
-//   agents within 0.3;  edge MLP he = bf(gelu(We1 bf(e) + be1)) (16 -> 64),
+//   nodes within 0.3;  edge MLP he = bf(gelu(We1 bf(e) + be1)) (16 -> 64),
 //   m = gelu(We2 he + be2) (64 -> 64), M = bf(sum of m over the edges);
 //   node MLP z = [bf(n), M] (80), h1 = bf(gelu(W1 z + b1)) (-> 128),
-//   h2 = bf(gelu(W2 h1 + b2)) (-> 128), out = W3 h2 + b3 (-> 8, 4 used);
-//   next state x' = x + 0.01 out[0:2], v' = v + 0.1 out[2:4].
+//   h2 = bf(gelu(W2 h1 + b2)) (-> 128), out = W3 h2 + b3 (-> 8; 4 used by an
+//   agent, 6 by a box);  next state x' = x + 0.01 out[0:2],
+//   v' = v + 0.1 out[2:4], and for a box theta' = theta + 0.1 out[4],
+//   omega' = omega + out[5].
 // bf() rounds to bfloat16; gelu(z) = z (1 + erf(z / sqrt 2)) / 2.
 #pragma once
 
@@ -16,14 +20,19 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "contact.cuh"
+
 namespace vmas {
 namespace sur {
 
-constexpr int kK = 6;            // neighbour slots per agent
+constexpr int kK = 6;            // neighbour slots per node
 constexpr int kAgents = 16;      // agents per env
-constexpr int kEnts = 20;        // 16 agents + 4 walls
+constexpr int kEnts = 20;        // sphere world: 16 agents + 4 walls
+constexpr int kBoxes = 4;        // box world: 16 agents + 4 boxes + 4 walls
+constexpr int kNodesMax = kAgents + kBoxes;
 constexpr float kRadius = 0.3f;
 constexpr float kXScale = 0.01f, kVScale = 0.1f;
+constexpr float kThScale = 0.1f, kOmScale = 1.0f;  // box angle and angular velocity
 
 using bf16 = __nv_bfloat16;
 
@@ -216,29 +225,47 @@ __global__ void col_sum_kernel(float *part, const float *x, int M, int N, int ch
 }
 
 // ------------------------------------------------------------ features
-// One thread per agent row r = e * 16 + i, reading a world's state planes
-// (entity e * N + j; agents are entities 0..15, the walls the last 4),
-// per-entity parameters {1/m, 1/I, radius, -} and actions [E][A][3] (agent i
-// takes row i).  Writes node [R][16], edge [K][R][16] (bfloat16; slot-major:
-// row k R + r is agent r's k-th neighbour) and mask [K][R].
+// One thread per node row r = e * nodes + i, reading a world's state planes
+// (entity e * N + j; the nodes are entities 0 .. nodes-1: 16 agents, then in
+// the box world the 4 boxes; the walls are the last 4 entities), per-entity
+// parameters {1/m, 1/I, half size a, half size b}, kinds and actions
+// [E][A][3] (node i takes row i).  Writes node [R][16], edge [K][R][16]
+// (bfloat16; slot-major: row k R + r is node r's k-th neighbour) and mask
+// [K][R].
+//   node  0: 10 vx, 1: 10 vy, 2: fx / m, 3: fy / m, 4: 10 R (bounding radius:
+//         a sphere's radius, a box's half diagonal), 5: 1 / m, 6..9: the
+//         gaps to the walls at x = +1, -1, y = +1, -1 of the bounding circle,
+//         min(gap, 0.3) / 0.3; boxes only: 10: 1, 11: cos theta,
+//         12: sin theta, 13: 0.1 omega, 14: 0.01 torque / I
+//   edge  0: dx / 0.3, 1: dy / 0.3 (d = x_j - x_i), 2: 10 dvx, 3: 10 dvy,
+//         4: 10 R_j, 5: (|d| - R_i - R_j) / 0.3, 6: 1; neighbour a box:
+//         7: 1, 8: cos theta_j, 9: sin theta_j, 10: 0.1 omega_j
+// An agent of the sphere world, and an agent's edge to an agent, read the
+// same values in both worlds.
 struct FeatureArgs {
-  int E, N, A;
-  const float *px, *py, *vx, *vy;
+  int E, N, A, nodes;
+  const float *px, *py, *vx, *vy, *th, *om;
   const float4 *param;
+  const uint8_t *kind;
   const float *actions;
   bf16 *node, *edge;
   float *mask;
 };
 
+__device__ __forceinline__ float bounding_radius(const float4 pr, uint32_t kind) {
+  return (kind & 3u) == 1u ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
+}
+
 __global__ void features_kernel(const FeatureArgs f) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int R = f.E * kAgents;
+  const int R = f.E * f.nodes;
   if (r >= R) return;
-  const int e = r / kAgents, i = r % kAgents;
+  const int e = r / f.nodes, i = r % f.nodes;
   const size_t b = (size_t)e * f.N;
   const float x = f.px[b + i], y = f.py[b + i], vx = f.vx[b + i], vy = f.vy[b + i];
   const float4 pi = f.param[b + i];
-  const float ri = pi.z, im = pi.x;
+  const bool box_i = (f.kind[b + i] & 3u) == 1u;
+  const float ri = bounding_radius(pi, f.kind[b + i]), im = pi.x;
   const float *a = f.actions + ((size_t)e * f.A + i) * 3;
   float nf[16];
   nf[0] = 10.f * vx;
@@ -252,13 +279,21 @@ __global__ void features_kernel(const FeatureArgs f) {
   for (int q = 0; q < 4; ++q) nf[6 + q] = fminf(gaps[q], kRadius) / kRadius;
 #pragma unroll
   for (int q = 10; q < 16; ++q) nf[q] = 0.f;
+  if (box_i) {
+    const float th = f.th[b + i];
+    nf[10] = 1.f;
+    nf[11] = cosf(th);
+    nf[12] = sinf(th);
+    nf[13] = 0.1f * f.om[b + i];
+    nf[14] = 0.01f * a[2] * pi.y;
+  }
 #pragma unroll
   for (int q = 0; q < 16; ++q) f.node[(size_t)r * 16 + q] = __float2bfloat16_rn(nf[q]);
-  // the K nearest other agents within the radius (ties: lower index first)
+  // the K nearest other nodes within the radius (ties: lower index first)
   float bd[kK];
   int bj[kK];
   int n = 0;
-  for (int j = 0; j < kAgents; ++j) {
+  for (int j = 0; j < f.nodes; ++j) {
     if (j == i) continue;
     const float dx = f.px[b + j] - x, dy = f.py[b + j] - y;
     const float d = sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
@@ -283,7 +318,8 @@ __global__ void features_kernel(const FeatureArgs f) {
     float mk = 0.f;
     if (k < n) {
       const int j = bj[k];
-      const float rj = f.param[b + j].z;
+      const uint32_t kj = f.kind[b + j];
+      const float rj = bounding_radius(f.param[b + j], kj);
       v[0] = (f.px[b + j] - x) / kRadius;
       v[1] = (f.py[b + j] - y) / kRadius;
       v[2] = 10.f * (f.vx[b + j] - vx);
@@ -291,6 +327,13 @@ __global__ void features_kernel(const FeatureArgs f) {
       v[4] = 10.f * rj;
       v[5] = (bd[k] - ri - rj) / kRadius;
       v[6] = 1.f;
+      if ((kj & 3u) == 1u) {
+        const float thj = f.th[b + j];
+        v[7] = 1.f;
+        v[8] = cosf(thj);
+        v[9] = sinf(thj);
+        v[10] = 0.1f * f.om[b + j];
+      }
       mk = 1.f;
     }
 #pragma unroll
@@ -341,20 +384,23 @@ __global__ void edge_back_kernel(int R, const float *d_zin, const float *mask, c
   d_zbf[t] = __float2bfloat16_rn(v);
 }
 
-// Loss mean((out[:, :4] - y)^2): d_out = 2 (out - y) / (4 R) (columns 4..7
-// zero); per-block partial sums of the squared error into part[blockIdx.x].
-__global__ void loss_kernel(int R, const float *out, const float *y, float *d_out32, bf16 *d_outbf,
-                            float *part) {
+// Loss: the mean of (out - y)^2 over the outputs each row uses (4 for an
+// agent, 6 for a box: node i >= 16 of its env); y is [R][tw].  d_out =
+// 2 (out - y) / count (unused columns zero), count = the used outputs of all
+// rows; per-block partial sums of the squared error into part[blockIdx.x].
+__global__ void loss_kernel(int R, int nodes, int tw, float count, const float *out, const float *y,
+                            float *d_out32, bf16 *d_outbf, float *part) {
   __shared__ float red[256];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   float se = 0.f;
   if (t < R * 8) {
     const int r = t / 8, c = t % 8;
+    const int used = (r % nodes) < kAgents ? 4 : 6;
     float d = 0.f;
-    if (c < 4) {
-      const float diff = out[(size_t)r * 8 + c] - y[(size_t)r * 4 + c];
+    if (c < used) {
+      const float diff = out[(size_t)r * 8 + c] - y[(size_t)r * tw + c];
       se = diff * diff;
-      d = 2.f * diff / (4.f * (float)R);
+      d = 2.f * diff / count;
     }
     d_out32[t] = d;
     d_outbf[t] = __float2bfloat16_rn(d);
@@ -369,7 +415,7 @@ __global__ void loss_kernel(int R, const float *out, const float *y, float *d_ou
 }
 
 // One block of 256 threads: strided partial sums, then a tree.
-__global__ void finish_loss_kernel(const float *part, int n, int R, float *loss) {
+__global__ void finish_loss_kernel(const float *part, int n, float count, float *loss) {
   __shared__ float red[256];
   float s = 0.f;
   for (int q = threadIdx.x; q < n; q += blockDim.x) s += part[q];
@@ -379,7 +425,7 @@ __global__ void finish_loss_kernel(const float *part, int n, int R, float *loss)
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *loss = red[0] / (4.f * (float)R);
+  if (threadIdx.x == 0) *loss = red[0] / count;
 }
 
 // Adam on FP32 master parameters; weights (not biases) mirrored to bfloat16.
@@ -452,30 +498,113 @@ __global__ void predict_kernel(const PredictArgs a) {
   }
 }
 
-// Agents' (x, y, vx, vy) rows [E * 16][4] of a world's planes.
-__global__ void save_agents_kernel(int E, int N, const float *px, const float *py,
-                                   const float *vx, const float *vy, float *save) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= E * kAgents) return;
-  const size_t g = (size_t)(r / kAgents) * N + r % kAgents;
-  save[(size_t)r * 4 + 0] = px[g];
-  save[(size_t)r * 4 + 1] = py[g];
-  save[(size_t)r * 4 + 2] = vx[g];
-  save[(size_t)r * 4 + 3] = vy[g];
+// Box world: applies the prediction (agents x, y, vx, vy; boxes also theta,
+// omega) to every env whose predicted bodies overlap one another, or the
+// walls at +-1, by at most `limit` (sphere-sphere by centre distance,
+// sphere-box and box-box by the step's own narrow phase, a box against a
+// wall by its deepest corner); every other env is left unchanged and
+// appended to `list`.  One thread per env.
+struct PredictBoxArgs {
+  int E, N;
+  float *px, *py, *vx, *vy, *th, *om;
+  const float4 *param;
+  const float *out;  // [E * 20][8]
+  float limit;
+  int *list, *list_len;
+};
+
+__global__ void predict_box_kernel(const PredictBoxArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  constexpr int NB = kNodesMax;
+  const size_t b = (size_t)e * a.N;
+  float px[NB], py[NB], pvx[NB], pvy[NB], pth[NB], pom[NB];
+  bool finite = true;
+  for (int i = 0; i < NB; ++i) {
+    const float *o = a.out + ((size_t)e * NB + i) * 8;
+    px[i] = fmaf(kXScale, o[0], a.px[b + i]);
+    py[i] = fmaf(kXScale, o[1], a.py[b + i]);
+    pvx[i] = fmaf(kVScale, o[2], a.vx[b + i]);
+    pvy[i] = fmaf(kVScale, o[3], a.vy[b + i]);
+    pth[i] = i < kAgents ? a.th[b + i] : fmaf(kThScale, o[4], a.th[b + i]);
+    pom[i] = i < kAgents ? a.om[b + i] : fmaf(kOmScale, o[5], a.om[b + i]);
+    finite = finite && isfinite(px[i]) && isfinite(py[i]) && isfinite(pvx[i]) &&
+             isfinite(pvy[i]) && isfinite(pth[i]) && isfinite(pom[i]);
+  }
+  float worst = -1e30f;  // deepest predicted overlap
+  if (finite) {
+    for (int i = 0; i < NB; ++i) {
+      const float4 pi = a.param[b + i];
+      if (i < kAgents) {
+        worst = fmaxf(worst, wall_overlap(px[i], py[i], pi.z));
+        for (int j = i + 1; j < kAgents; ++j) {
+          const float dx = px[i] - px[j], dy = py[i] - py[j];
+          worst = fmaxf(worst, pi.z + a.param[b + j].z -
+                                   sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+        }
+        for (int j = kAgents; j < NB; ++j) {
+          const float4 pj = a.param[b + j];
+          Hit h;
+          if (hit_sphere_box(px[i], py[i], pi.z, px[j], py[j], cosf(pth[j]), sinf(pth[j]), pj.z,
+                             pj.w, h))
+            worst = fmaxf(worst, -h.g);
+        }
+      } else {
+        const float c = cosf(pth[i]), sn = sinf(pth[i]);
+        for (int k = 0; k < 4; ++k) {  // corners against the walls
+          const float u = (k == 1 || k == 2) ? pi.z : -pi.z, v = k >= 2 ? pi.w : -pi.w;
+          const float cx = px[i] + u * c - v * sn, cy = py[i] + u * sn + v * c;
+          worst = fmaxf(worst, fmaxf(fmaxf(cx - 1.f, -1.f - cx), fmaxf(cy - 1.f, -1.f - cy)));
+        }
+        for (int j = i + 1; j < NB; ++j) {
+          const float4 pj = a.param[b + j];
+          const Poly A{px[i], py[i], c, sn, pi.z, pi.w, true};
+          const Poly B{px[j], py[j], cosf(pth[j]), sinf(pth[j]), pj.z, pj.w, true};
+          Hit h;
+          if (hit_poly_poly(A, B, h)) worst = fmaxf(worst, -h.g);
+        }
+      }
+    }
+  }
+  if (!finite || !(worst <= a.limit)) {
+    a.list[atomicAdd(a.list_len, 1)] = e;
+    return;
+  }
+  for (int i = 0; i < NB; ++i) {
+    a.px[b + i] = px[i];
+    a.py[b + i] = py[i];
+    a.vx[b + i] = pvx[i];
+    a.vy[b + i] = pvy[i];
+    if (i >= kAgents) {
+      a.th[b + i] = pth[i];
+      a.om[b + i] = pom[i];
+    }
+  }
 }
 
-// Training targets: the step's deltas over (0.01, 0.01, 0.1, 0.1).
-__global__ void targets_kernel(int E, int N, const float *px, const float *py, const float *vx,
-                               const float *vy, const float *save, float *target) {
+// The nodes' (x, y, vx, vy, theta, omega) rows [E * nodes][6] of a world's
+// planes.
+__global__ void save_nodes_kernel(int E, int N, int nodes, const float *planes, size_t EN,
+                                  float *save) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= E * kAgents) return;
-  const size_t g = (size_t)(r / kAgents) * N + r % kAgents;
-  const float *s0 = save + (size_t)r * 4;
-  float *t = target + (size_t)r * 4;
-  t[0] = (px[g] - s0[0]) / kXScale;
-  t[1] = (py[g] - s0[1]) / kXScale;
-  t[2] = (vx[g] - s0[2]) / kVScale;
-  t[3] = (vy[g] - s0[3]) / kVScale;
+  if (r >= E * nodes) return;
+  const size_t g = (size_t)(r / nodes) * N + r % nodes;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) save[(size_t)r * 6 + f] = planes[f * EN + g];
+}
+
+// Training targets [E * nodes][tw]: the step's deltas over (0.01, 0.01, 0.1,
+// 0.1) and, when tw = 6, (0.1, 1) for theta and omega (0 for agents).
+__global__ void targets_kernel(int E, int N, int nodes, int tw, const float *planes, size_t EN,
+                               const float *save, float *target) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= E * nodes) return;
+  const size_t g = (size_t)(r / nodes) * N + r % nodes;
+  const float *s0 = save + (size_t)r * 6;
+  float *t = target + (size_t)r * tw;
+  const float sc[6] = {kXScale, kXScale, kVScale, kVScale, kThScale, kOmScale};
+  for (int f = 0; f < tw; ++f)
+    t[f] = (r % nodes) < kAgents && f >= 4 ? 0.f : (planes[f * EN + g] - s0[f]) / sc[f];
 }
 
 }  // namespace sur

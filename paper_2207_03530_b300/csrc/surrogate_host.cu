@@ -3,6 +3,7 @@
 // that predicts a whole world step of the 16-agent walled sphere world, with
 // the plain step as the fallback for envs whose prediction overlaps.
 
+#include "gemm_tc.cuh"
 #include "host.h"
 #include "surrogate_fused.cuh"
 
@@ -17,6 +18,18 @@ using namespace vmas::sur;  // parameter offsets kOff*
 constexpr int kSurParams = vmas::sur::kParams;
 constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
 
+// K-major (transposed) bfloat16 copies of the weights whose products with an
+// upstream gradient are plain row-major GEMMs in the backward, so that they
+// too run on the tensor-core GEMM: W2^T [128][128], W1^T [80][128],
+// We2^T [64][64].
+constexpr int kOffW2T = 0, kOffW1T = 128 * 128, kOffWe2T = kOffW1T + 80 * 128,
+              kTransposed = kOffWe2T + 64 * 64;
+
+// 0: the tcgen05 GEMM wherever the shape allows it (the default);
+// 1: the warp-mma GEMM only (for A/B comparisons).  Process-wide.
+int g_gemm_engine = 0;
+std::atomic<long long> g_tc_launches{0};  // tcgen05 GEMM launches so far
+
 }  // namespace
 
 struct vmas_surrogate {
@@ -28,6 +41,8 @@ struct vmas_surrogate {
   int adam_t = 0;
   float *p32 = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   bf16 *pbf = nullptr;
+  bf16 *pbfT = nullptr;  // transposed weight copies (kOff*T)
+  int *err = nullptr;    // device error word of the surrogate's kernels
   // forward
   bf16 *node = nullptr, *edge = nullptr, *he = nullptr, *zin = nullptr, *h1 = nullptr,
        *h2 = nullptr;
@@ -48,7 +63,7 @@ void free_sur(vmas_surrogate *s) {
                   s->he,    s->zin,   s->h1,     s->h2,     s->mask,   s->ze2,    s->out,
                   s->ze1,   s->z1,    s->z2,     s->d_out,  s->g128,   s->d_zin,  s->ge,
                   s->d_outbf, s->g128bf, s->gebf, s->part,  s->loss_part, s->save, s->target,
-                  s->list,  s->list_len};
+                  s->list,  s->list_len, s->pbfT, s->err};
   for (void *q : ptrs) cudaFree(q);
   delete s;
 }
@@ -58,15 +73,20 @@ bool dalloc(T **ptr, size_t count) {
   return cudaMalloc((void **)ptr, (count > 0 ? count : 1) * sizeof(T)) == cudaSuccess;
 }
 
+// Network rows per env of a world (16 agents, or 16 agents + 4 boxes) and
+// the width of its training targets (x y vx vy, plus theta omega for boxes).
+int nodes_of(const vmas_world *w) { return w->sur_layout == 2 ? sur::kNodesMax : sur::kAgents; }
+int target_width(const vmas_world *w) { return w->sur_layout == 2 ? 6 : 4; }
+
 int ensure_training(vmas_surrogate *s) {
   if (s->ze1) return VMAS_OK;
-  const size_t R = (size_t)s->cap * sur::kAgents, RK = R * sur::kK;
+  const size_t R = (size_t)s->cap * sur::kNodesMax, RK = R * sur::kK;
   const bool ok = dalloc(&s->ze1, RK * 64) && dalloc(&s->z1, R * 128) && dalloc(&s->z2, R * 128) &&
                   dalloc(&s->d_out, R * 8) && dalloc(&s->d_outbf, R * 8) &&
                   dalloc(&s->g128, R * 128) && dalloc(&s->g128bf, R * 128) &&
                   dalloc(&s->d_zin, R * 80) && dalloc(&s->ge, RK * 64) &&
-                  dalloc(&s->gebf, RK * 64) && dalloc(&s->save, R * 4) &&
-                  dalloc(&s->target, R * 4);
+                  dalloc(&s->gebf, RK * 64) && dalloc(&s->save, R * 6) &&
+                  dalloc(&s->target, R * 6);
   if (!ok) {
     cudaGetLastError();
     return fail(VMAS_ENOMEM, "cudaMalloc failed for the surrogate's training buffers");
@@ -76,12 +96,100 @@ int ensure_training(vmas_surrogate *s) {
 
 unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// C = A B (+ bias, GELU) through gemm_bf16_kernel; `splits` > 1 sums K in
-// chunks into part, reduced into out_f32 (then no bias / bf16 output).
+// cuTensorMapEncodeTiled, reached through the runtime (no link to the
+// driver library); null when unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of a row-major bfloat16 matrix [rows][K] (leading dimension ld
+// elements): boxes of 64 K-elements (128 bytes, the swizzle span) by
+// box_rows rows, 128-byte swizzle, zero fill past the edges.
+bool tc_map(CUtensorMap *m, const bf16 *p, int rows, int K, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C = A B^T-stored (B[n][k]) on the tensor cores; false (nothing enqueued)
+// when the shape or a tensor map does not allow it.
+bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+             const float *bias, int act, float *out_f32, int ldc_f, bf16 *out_bf, int ldc_b,
+             int *err, int *rc) {
+  auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+  if (g_gemm_engine != 0 || !err || M < 1 || N < 1 || N > 128 || K < 16 || K > 128 || K % 16 ||
+      lda % 8 || ldb % 8 || !al16(A) || !al16(B))
+    return false;
+  sur::TcGemmArgs g{};
+  g.M = M; g.N = N; g.K = K;
+  g.n_pad = (N + 15) / 16 * 16;
+  g.katoms = (K + 63) / 64;
+  g.bias = bias; g.act = act;
+  g.out_f32 = out_f32; g.ldc_f = ldc_f; g.out_bf = out_bf; g.ldc_b = ldc_b;
+  g.err = err;
+  g.vec_f = out_f32 && al16(out_f32) && ldc_f % 4 == 0;
+  g.vec_b = out_bf && al16(out_bf) && ldc_b % 8 == 0;
+  CUtensorMap ma, mb;
+  if (!tc_map(&ma, A, M, K, lda, sur::kTcM) || !tc_map(&mb, B, N, K, ldb, g.n_pad)) return false;
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(sur::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sur::tc_smem_bytes(2, 128)) != cudaSuccess) {
+      cudaGetLastError();
+      n_sm = 0;
+      return false;
+    }
+  }
+  const int tiles = (M + sur::kTcM - 1) / sur::kTcM;
+  const int grid = std::min(tiles, 2 * n_sm);
+  sur::gemm_tc_kernel<<<grid, 128, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, g);
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) ++g_tc_launches;
+  *rc = e == cudaSuccess ? VMAS_OK : cuda_fail(e, "gemm_tc_kernel launch");
+  return true;
+}
+
+// C = A B (+ bias, GELU): on the tensor cores (gemm_tc_kernel) when A is
+// row-major, B stored [N][K], K a multiple of 16 up to 128, N up to 128 and
+// an error word is given; otherwise through gemm_bf16_kernel (warp mma), where
+// `splits` > 1 sums K in chunks into part, reduced into out_f32 (then no
+// bias / bf16 output).
 int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, int lda,
          const bf16 *B, int ldb, const float *bias, int act, float *out_f32, int ldc_f,
-         bf16 *out_bf, int ldc_b, float *part = nullptr, int splits = 1) {
+         bf16 *out_bf, int ldc_b, float *part = nullptr, int splits = 1, int *err = nullptr) {
   if (M == 0 || N == 0) return VMAS_OK;
+  if (!ta && tb && splits == 1) {
+    int rc = VMAS_OK;
+    if (gemm_tc(st, M, N, K, A, lda, B, ldb, bias, act, out_f32, ldc_f, out_bf, ldc_b, err, &rc))
+      return rc;
+  }
   sur::GemmArgs g{};
   g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
   g.bias = bias; g.act = act;
@@ -133,7 +241,9 @@ int sur_check(vmas_surrogate *s, vmas_world *w, const float *d_actions) {
   if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
   if (!w) return fail(VMAS_EINVAL, "world is NULL");
   if (!w->sur_ok)
-    return fail(VMAS_EINVAL, "world layout is not 16 actuated agent spheres then 4 fixed lines");
+    return fail(VMAS_EINVAL,
+                "world layout is not 16 actuated agent spheres, optionally 4 actuated boxes, "
+                "then 4 fixed lines");
   if (w->E > s->cap)
     return fail(VMAS_EINVAL, "world has " + std::to_string(w->E) + " envs, surrogate capacity " +
                                  std::to_string(s->cap));
@@ -146,13 +256,14 @@ int sur_check(vmas_surrogate *s, vmas_world *w, const float *d_actions) {
 int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool train,
                 cudaStream_t st) {
   const int E = w->E;
-  const int R = E * sur::kAgents, RK = R * sur::kK;
+  const int R = E * nodes_of(w), RK = R * sur::kK;
   if (E == 0) return VMAS_OK;
   sur::FeatureArgs f{};
   const size_t EN = (size_t)E * w->N;
-  f.E = E; f.N = w->N; f.A = w->A;
+  f.E = E; f.N = w->N; f.A = w->A; f.nodes = nodes_of(w);
   f.px = w->planes; f.py = w->planes + EN; f.vx = w->planes + 2 * EN; f.vy = w->planes + 3 * EN;
-  f.param = w->param; f.actions = d_actions;
+  f.th = w->planes + 4 * EN; f.om = w->planes + 5 * EN;
+  f.param = w->param; f.kind = w->kind; f.actions = d_actions;
   f.node = s->node; f.edge = s->edge; f.mask = s->mask;
   sur::features_kernel<<<blocks_for(R, 128), 128, 0, st>>>(f);
   VMAS_CUDA(cudaGetLastError());
@@ -161,29 +272,31 @@ int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool t
   int rc;
   // edge MLP
   if ((rc = gemm(st, false, true, RK, 64, 16, s->edge, 16, W + kOffWe1, 16, P + kOffbe1, 1,
-                 train ? s->ze1 : nullptr, 64, s->he, 64)))
+                 train ? s->ze1 : nullptr, 64, s->he, 64, nullptr, 1, s->err)))
     return rc;
   if ((rc = gemm(st, false, true, RK, 64, 64, s->he, 64, W + kOffWe2, 64, P + kOffbe2, 0, s->ze2,
-                 64, nullptr, 0)))
+                 64, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   sur::aggregate_kernel<<<blocks_for((size_t)R * 80, 256), 256, 0, st>>>(R, s->ze2, s->mask,
                                                                           s->node, s->zin);
   VMAS_CUDA(cudaGetLastError());
   // node MLP
   if ((rc = gemm(st, false, true, R, 128, 80, s->zin, 80, W + kOffW1, 80, P + kOffb1, 1,
-                 train ? s->z1 : nullptr, 128, s->h1, 128)))
+                 train ? s->z1 : nullptr, 128, s->h1, 128, nullptr, 1, s->err)))
     return rc;
   if ((rc = gemm(st, false, true, R, 128, 128, s->h1, 128, W + kOffW2, 128, P + kOffb2, 1,
-                 train ? s->z2 : nullptr, 128, s->h2, 128)))
+                 train ? s->z2 : nullptr, 128, s->h2, 128, nullptr, 1, s->err)))
     return rc;
   return gemm(st, false, true, R, 8, 128, s->h2, 128, W + kOffW3, 128, P + kOffb3, 0, s->out, 8,
-              nullptr, 0);
+              nullptr, 0, nullptr, 1, s->err);
 }
 
-// Loss against target [R][4] and the gradient into s->grad (after sur_forward
-// with train = true).
-int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, cudaStream_t st) {
-  const int R = E * sur::kAgents, RK = R * sur::kK;
+// Loss against target [R][tw] and the gradient into s->grad (after
+// sur_forward with train = true), for E envs of `nodes` rows each.
+int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *target, float *d_loss,
+                 cudaStream_t st) {
+  const int R = E * nodes, RK = R * sur::kK;
+  const float count = (float)E * (float)(sur::kAgents * 4 + (nodes - sur::kAgents) * 6);
   float *G = s->grad;
   const bf16 *W = s->pbf;
   VMAS_CUDA(cudaMemsetAsync(G, 0, kSurParams * sizeof(float), st));
@@ -192,10 +305,11 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
     return VMAS_OK;
   }
   const int lb = (int)blocks_for((size_t)R * 8, 256);
-  sur::loss_kernel<<<lb, 256, 0, st>>>(R, s->out, target, s->d_out, s->d_outbf, s->loss_part);
+  sur::loss_kernel<<<lb, 256, 0, st>>>(R, nodes, tw, count, s->out, target, s->d_out, s->d_outbf,
+                                       s->loss_part);
   VMAS_CUDA(cudaGetLastError());
   if (d_loss) {
-    sur::finish_loss_kernel<<<1, 256, 0, st>>>(s->loss_part, lb, R, d_loss);
+    sur::finish_loss_kernel<<<1, 256, 0, st>>>(s->loss_part, lb, count, d_loss);
     VMAS_CUDA(cudaGetLastError());
   }
   int rc;
@@ -216,8 +330,8 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
                  128, nullptr, 0, s->part, sp)))
     return rc;
   if ((rc = col_sum(st, G + kOffb2, s->g128, R, 128, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 128, 128, s->g128bf, 128, W + kOffW2, 128, nullptr, 0,
-                 s->g128, 128, nullptr, 0)))
+  if ((rc = gemm(st, false, true, R, 128, 128, s->g128bf, 128, s->pbfT + kOffW2T, 128, nullptr, 0,
+                 s->g128, 128, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // node layer 1
   sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
@@ -227,8 +341,8 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
                  nullptr, 0, s->part, sp)))
     return rc;
   if ((rc = col_sum(st, G + kOffb1, s->g128, R, 128, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 80, 128, s->g128bf, 128, W + kOffW1, 80, nullptr, 0, s->d_zin,
-                 80, nullptr, 0)))
+  if ((rc = gemm(st, false, true, R, 80, 128, s->g128bf, 128, s->pbfT + kOffW1T, 128, nullptr, 0,
+                 s->d_zin, 80, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // edge layer 2 (through the masked sum)
   sur::edge_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>(R, s->d_zin, s->mask,
@@ -238,8 +352,8 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
                  nullptr, 0, s->part, sp)))
     return rc;
   if ((rc = col_sum(st, G + kOffbe2, s->ge, RK, 64, s->part))) return rc;
-  if ((rc = gemm(st, false, false, RK, 64, 64, s->gebf, 64, W + kOffWe2, 64, nullptr, 0, s->ge, 64,
-                 nullptr, 0)))
+  if ((rc = gemm(st, false, true, RK, 64, 64, s->gebf, 64, s->pbfT + kOffWe2T, 64, nullptr, 0, s->ge,
+                 64, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // edge layer 1
   sur::gelu_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>((size_t)RK * 64, s->ge,
@@ -251,6 +365,8 @@ int sur_backward(vmas_surrogate *s, int E, const float *target, float *d_loss, c
   return col_sum(st, G + kOffbe1, s->ge, RK, 64, s->part);
 }
 
+int refresh_transposed(vmas_surrogate *s, cudaStream_t st);
+
 int sur_adam(vmas_surrogate *s, float lr, cudaStream_t st) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   ++s->adam_t;
@@ -259,7 +375,7 @@ int sur_adam(vmas_surrogate *s, float lr, cudaStream_t st) {
   sur::adam_kernel<<<blocks_for(kSurParams, 256), 256, 0, st>>>(
       kSurParams, s->p32, s->grad, s->adam_m, s->adam_v, s->pbf, lr, b1, b2, eps, c1, c2);
   VMAS_CUDA(cudaGetLastError());
-  return VMAS_OK;
+  return refresh_transposed(s, st);
 }
 
 // The fused inference kernel over the world's envs: network output into
@@ -295,6 +411,27 @@ __global__ void f32_to_bf16_kernel(const float *x, bf16 *y, int n) {
   if (t < n) y[t] = __float2bfloat16_rn(x[t]);
 }
 
+// The transposed weight copies from the bfloat16 weights.
+__global__ void transpose_weights_kernel(const bf16 *w, bf16 *wt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 128 * 128) {  // W2 [128][128]
+    const int o = t / 128, i = t % 128;
+    wt[kOffW2T + i * 128 + o] = w[kOffW2 + t];
+  } else if (t < 128 * 128 + 128 * 80) {  // W1 [128][80]
+    const int q = t - 128 * 128, o = q / 80, i = q % 80;
+    wt[kOffW1T + i * 128 + o] = w[kOffW1 + q];
+  } else if (t < kTransposed) {  // We2 [64][64]
+    const int q = t - 128 * 128 - 128 * 80, o = q / 64, i = q % 64;
+    wt[kOffWe2T + i * 64 + o] = w[kOffWe2 + q];
+  }
+}
+
+int refresh_transposed(vmas_surrogate *s, cudaStream_t st) {
+  transpose_weights_kernel<<<blocks_for(kTransposed, 256), 256, 0, st>>>(s->pbf, s->pbfT);
+  VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -314,7 +451,7 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
     s->n_sm = 1;
   }
   s->cap = max_envs;
-  const size_t R = (size_t)max_envs * sur::kAgents, RK = R * sur::kK;
+  const size_t R = (size_t)max_envs * sur::kNodesMax, RK = R * sur::kK;
   const bool ok =
       dalloc(&s->p32, kSurParams) && dalloc(&s->grad, kSurParams) && dalloc(&s->adam_m, kSurParams) &&
       dalloc(&s->adam_v, kSurParams) && dalloc(&s->pbf, kSurParams) && dalloc(&s->node, R * 16) &&
@@ -322,7 +459,8 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
       dalloc(&s->h1, R * 128) && dalloc(&s->h2, R * 128) && dalloc(&s->mask, RK) &&
       dalloc(&s->ze2, RK * 64) && dalloc(&s->out, R * 8) &&
       dalloc(&s->part, (size_t)kSplitCap * 128 * 128) && dalloc(&s->loss_part, R * 8 / 256 + 1) &&
-      dalloc(&s->list, (size_t)max_envs) && dalloc(&s->list_len, 1);
+      dalloc(&s->list, (size_t)max_envs) && dalloc(&s->list_len, 1) &&
+      dalloc(&s->pbfT, kTransposed) && dalloc(&s->err, 4);
   if (!ok) {
     cudaGetLastError();
     free_sur(s);
@@ -332,6 +470,8 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
   if (e == cudaSuccess) e = cudaMemset(s->pbf, 0, kSurParams * sizeof(bf16));
   if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, kSurParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, kSurParams * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s->pbfT, 0, kTransposed * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMemset(s->err, 0, 4 * sizeof(int));
   if (e != cudaSuccess) {
     free_sur(s);
     return cuda_fail(e, "surrogate init");
@@ -353,6 +493,7 @@ int vmas_sur_set_params(vmas_surrogate *s, const float *h_params) {
   VMAS_CUDA(cudaMemcpy(s->p32, h_params, kSurParams * sizeof(float), cudaMemcpyHostToDevice));
   f32_to_bf16_kernel<<<blocks_for(kSurParams, 256), 256>>>(s->p32, s->pbf, kSurParams);
   VMAS_CUDA(cudaGetLastError());
+  if (int rc = refresh_transposed(s, nullptr)) return rc;
   VMAS_CUDA(cudaMemset(s->adam_m, 0, kSurParams * sizeof(float)));
   VMAS_CUDA(cudaMemset(s->adam_v, 0, kSurParams * sizeof(float)));
   VMAS_CUDA(cudaDeviceSynchronize());
@@ -379,11 +520,11 @@ int vmas_sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, f
   int rc = sur_check(s, w, d_actions);
   if (rc) return rc;
   cudaStream_t st = as_stream(stream);
-  if (s->mode == VMAS_SUR_FUSED)
+  if (s->mode == VMAS_SUR_FUSED && w->sur_layout == 1)
     return sur_fused(s, w, d_actions, d_out ? d_out : s->out, false, 0.f, st);
   if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
   if (d_out && w->E)
-    VMAS_CUDA(cudaMemcpyAsync(d_out, s->out, (size_t)w->E * sur::kAgents * 8 * sizeof(float),
+    VMAS_CUDA(cudaMemcpyAsync(d_out, s->out, (size_t)w->E * nodes_of(w) * 8 * sizeof(float),
                               cudaMemcpyDeviceToDevice, st));
   return VMAS_OK;
 }
@@ -396,7 +537,7 @@ int vmas_sur_loss_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions,
   if ((rc = ensure_training(s))) return rc;
   cudaStream_t st = as_stream(stream);
   if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
-  if ((rc = sur_backward(s, w->E, d_target, d_loss, st))) return rc;
+  if ((rc = sur_backward(s, w->E, nodes_of(w), target_width(w), d_target, d_loss, st))) return rc;
   if (d_grad)
     VMAS_CUDA(cudaMemcpyAsync(d_grad, s->grad, kSurParams * sizeof(float), cudaMemcpyDeviceToDevice,
                               st));
@@ -419,24 +560,23 @@ static int sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actio
                           float *d_loss, cudaStream_t st) {
   int rc = ensure_training(s);
   if (rc) return rc;
-  const int E = w->E, R = E * sur::kAgents;
+  const int E = w->E, nodes = nodes_of(w), tw = target_width(w), R = E * nodes;
   if (E == 0) {
     VMAS_CUDA(cudaMemsetAsync(s->grad, 0, kSurParams * sizeof(float), st));
     if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
     return VMAS_OK;
   }
   const size_t EN = (size_t)E * w->N;
-  float *px = w->planes, *py = px + EN, *vx = px + 2 * EN, *vy = px + 3 * EN;
   if ((rc = sur_forward(s, w, d_actions, true, st))) return rc;
-  sur::save_agents_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save);
+  sur::save_nodes_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, nodes, w->planes, EN, s->save);
   VMAS_CUDA(cudaGetLastError());
   StepParams p = make_params(w);
   p.actions = d_actions;
   if ((rc = launch_step(p, st))) return rc;
-  sur::targets_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, px, py, vx, vy, s->save,
+  sur::targets_kernel<<<blocks_for(R, 256), 256, 0, st>>>(E, w->N, nodes, tw, w->planes, EN, s->save,
                                                            s->target);
   VMAS_CUDA(cudaGetLastError());
-  return sur_backward(s, E, s->target, d_loss, st);
+  return sur_backward(s, E, nodes, tw, s->target, d_loss, st);
 }
 
 int vmas_sur_train_grad(vmas_surrogate *s, vmas_world *w, const float *d_actions, float *d_loss,
@@ -474,8 +614,19 @@ int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, floa
     return VMAS_OK;
   }
   VMAS_CUDA(cudaMemsetAsync(s->list_len, 0, sizeof(int), st));
-  if (s->mode == VMAS_SUR_FUSED) {
+  if (s->mode == VMAS_SUR_FUSED && w->sur_layout == 1) {
     if ((rc = sur_fused(s, w, d_actions, nullptr, true, limit, st))) return rc;
+  } else if (w->sur_layout == 2) {
+    if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
+    sur::PredictBoxArgs a{};
+    const size_t EN = (size_t)E * w->N;
+    a.E = E; a.N = w->N;
+    a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
+    a.th = w->planes + 4 * EN; a.om = w->planes + 5 * EN;
+    a.param = w->param; a.out = s->out; a.limit = limit;
+    a.list = s->list; a.list_len = s->list_len;
+    sur::predict_box_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
+    VMAS_CUDA(cudaGetLastError());
   } else {
     if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
     sur::PredictArgs a{};
@@ -505,7 +656,7 @@ int vmas_sur_debug_features(vmas_surrogate *s, vmas_world *w, const float *d_act
   if (rc) return rc;
   cudaStream_t st = as_stream(stream);
   if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
-  const size_t R = (size_t)w->E * sur::kAgents, RK = R * sur::kK;
+  const size_t R = (size_t)w->E * nodes_of(w), RK = R * sur::kK;
   if (!R) return VMAS_OK;
   if (d_node) VMAS_CUDA(cudaMemcpyAsync(d_node, s->node, R * 16 * 2, cudaMemcpyDeviceToDevice, st));
   if (d_edge) VMAS_CUDA(cudaMemcpyAsync(d_edge, s->edge, RK * 16 * 2, cudaMemcpyDeviceToDevice, st));
@@ -528,15 +679,50 @@ int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N,
     return fail(VMAS_EINVAL, "leading dimension too small");
   cudaStream_t st = as_stream(stream);
   float *part = nullptr;
+  int *err = nullptr;
   if (splits > 1) VMAS_CUDA(cudaMalloc(&part, (size_t)splits * M * N * sizeof(float)));
-  const int rc = gemm(st, trans_a, trans_b, M, N, K, reinterpret_cast<const bf16 *>(d_a), lda,
-                      reinterpret_cast<const bf16 *>(d_b), ldb, d_bias, gelu ? 1 : 0, d_out_f32, N,
-                      reinterpret_cast<bf16 *>(d_out_bf16), N, part, splits);
-  if (part) {
-    cudaStreamSynchronize(st);
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
     cudaFree(part);
+    cudaFree(err);
+    return fail(VMAS_ENOMEM, "GEMM error word");
   }
+  int rc = gemm(st, trans_a, trans_b, M, N, K, reinterpret_cast<const bf16 *>(d_a), lda,
+                reinterpret_cast<const bf16 *>(d_b), ldb, d_bias, gelu ? 1 : 0, d_out_f32, N,
+                reinterpret_cast<bf16 *>(d_out_bf16), N, part, splits, err);
+  int h_err = 0;
+  if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    if (rc == VMAS_OK) rc = cuda_fail(cudaGetLastError(), "GEMM");
+  } else if (h_err && rc == VMAS_OK) {
+    rc = fail(VMAS_EDEVICE, "GEMM device error word set (bits " + std::to_string(h_err) + ")");
+  }
+  cudaFree(part);
+  cudaFree(err);
   return rc;
+}
+
+int vmas_debug_gemm_engine(int32_t engine, int64_t *tc_launches) {
+  if (engine != -1 && engine != 0 && engine != 1)
+    return fail(VMAS_EINVAL, "engine must be -1, 0 or 1");
+  if (engine >= 0) g_gemm_engine = engine;
+  if (tc_launches) *tc_launches = g_tc_launches.load();
+  return VMAS_OK;
+}
+
+int vmas_sur_check(vmas_surrogate *s, void *stream, int32_t *bits) {
+  if (!s) return fail(VMAS_EINVAL, "surrogate is NULL");
+  cudaStream_t st = as_stream(stream);
+  int h = 0;
+  VMAS_CUDA(cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VMAS_CUDA(cudaStreamSynchronize(st));
+  if (bits) *bits = h;
+  if (h) {
+    VMAS_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+    VMAS_CUDA(cudaStreamSynchronize(st));
+    return fail(VMAS_EDEVICE, "surrogate device error word set (bits " + std::to_string(h) + ")");
+  }
+  return VMAS_OK;
 }
 
 }  // extern "C"

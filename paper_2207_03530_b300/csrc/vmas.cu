@@ -23,6 +23,7 @@
 #include "diff.cuh"
 #include "host.h"
 #include "lidar.cuh"
+#include "ragged_persistent.cuh"
 #include "step_fused.cuh"
 
 static_assert(vmas::kStatCount == VMAS_STATS_COUNT, "stats layout");
@@ -154,14 +155,14 @@ int launch_ragged_class(const StepParams &p, int G, int slots, int n_envs, cudaS
   }
 }
 
-int launch_ragged_persistent(vmas::RaggedQueueParams q, cudaStream_t st) {
-  if (q.n_items <= 0) return VMAS_OK;
+template <int MINB>
+int launch_ragged_persistent_b(vmas::RaggedQueueParams q, cudaStream_t st) {
   q.slab = vmas::persist_slab_bytes();
   const int smem = vmas::kFusedWarps * q.slab;
-  static int resident = 0, sms = 0;  // per process: one device model
+  static int resident = 0, sms = 0;  // per process and budget: one device model
   if (!resident) {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(vmas::ragged_persistent_kernel,
+      cudaError_t e = cudaFuncSetAttribute(vmas::ragged_persistent_kernel<MINB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
@@ -169,16 +170,21 @@ int launch_ragged_persistent(vmas::RaggedQueueParams q, cudaStream_t st) {
     VMAS_CUDA(cudaGetDevice(&dev));
     VMAS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     VMAS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &resident, vmas::ragged_persistent_kernel, vmas::kFusedWarps * 32, smem));
+        &resident, vmas::ragged_persistent_kernel<MINB>, vmas::kFusedWarps * 32, smem));
     if (resident < 1) resident = 1;
   }
   // one wave of resident CTAs, fewer when there are fewer items than warps
   const int need = (q.n_items + vmas::kFusedWarps - 1) / vmas::kFusedWarps;
   const int grid = std::min(need, sms * resident);
-  vmas::ragged_persistent_kernel<<<grid, vmas::kFusedWarps * 32, smem, st>>>(q);
+  vmas::ragged_persistent_kernel<MINB><<<grid, vmas::kFusedWarps * 32, smem, st>>>(q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "ragged_persistent_kernel launch");
   return VMAS_OK;
+}
+
+int launch_ragged_persistent(vmas::RaggedQueueParams q, int budget, cudaStream_t st) {
+  if (q.n_items <= 0) return VMAS_OK;
+  return budget == 2 ? launch_ragged_persistent_b<5>(q, st) : launch_ragged_persistent_b<4>(q, st);
 }
 
 // Lanes per environment: the smallest group that holds every entity in at
@@ -547,7 +553,24 @@ int vmas_world_create(const vmas_world_desc *d, vmas_world **out) {
         else
           ok = d->shape[t] == VMAS_LINE && !(fl & (VMAS_MOVABLE | VMAS_ACTUATED));
       }
-    w->sur_ok = ok;
+    // the box world (the paper-scale layout): 16 such agents (rows 0..15),
+    // 4 movable, rotatable, actuated boxes (rows 16..19), 4 fixed lines
+    bool ok2 = N == 24 && w->A >= 20;
+    for (int e = 0; e < E && ok2; ++e)
+      for (int i = 0; i < N && ok2; ++i) {
+        const size_t t = (size_t)e * N + i;
+        const int fl = d->flags[t];
+        if (i < 16)
+          ok2 = d->shape[t] == VMAS_SPHERE && (fl & VMAS_MOVABLE) && (fl & VMAS_ACTUATED) &&
+                !(fl & VMAS_ROTATABLE);
+        else if (i < 20)
+          ok2 = d->shape[t] == VMAS_BOX && (fl & VMAS_MOVABLE) && (fl & VMAS_ROTATABLE) &&
+                (fl & VMAS_ACTUATED);
+        else
+          ok2 = d->shape[t] == VMAS_LINE && !(fl & (VMAS_MOVABLE | VMAS_ACTUATED));
+      }
+    w->sur_layout = ok ? 1 : (ok2 ? 2 : 0);
+    w->sur_ok = w->sur_layout != 0;
   }
   {
     // candidate-list margin: half the median bounding radius of the movable

@@ -86,16 +86,25 @@ class RaggedWorld:
                                                   int(steps_per_launch)))
 
     @property
-    def persistent(self) -> bool:
-        """True when every size class runs in one persistent launch (atomic
-        work queue); False for one launch per class."""
+    def schedule(self) -> int:
+        """0: one launch per size class; 1, 2: every class in one persistent
+        launch with an atomic work queue (128- or 96-register build)."""
         v = ctypes.c_int32()
         _lib.check(self._L.vmas_ragged_get_schedule(self._h, ctypes.byref(v)))
-        return bool(v.value)
+        return v.value
+
+    @schedule.setter
+    def schedule(self, value: int) -> None:
+        _lib.check(self._L.vmas_ragged_set_schedule(self._h, int(value)))
+
+    @property
+    def persistent(self) -> bool:
+        """True when every size class runs in one persistent launch."""
+        return self.schedule != 0
 
     @persistent.setter
     def persistent(self, on: bool) -> None:
-        _lib.check(self._L.vmas_ragged_set_schedule(self._h, 1 if on else 0))
+        self.schedule = 1 if on else 0
 
     def autotune(self, actions: torch.Tensor) -> None:
         _lib.check(self._L.vmas_ragged_autotune(self._h, actions.data_ptr(), int(actions.shape[0]),

@@ -74,6 +74,16 @@ def _p(x):
     return None if x is None else x.data_ptr()
 
 
+def nodes_of(world) -> int:
+    """Network rows per env: 16 agents, or 20 (16 agents + 4 boxes) in the
+    box world (the paper-scale layout of 24 entities)."""
+    return 20 if world.n_entities == 24 else 16
+
+
+def target_width(world) -> int:
+    return 6 if world.n_entities == 24 else 4
+
+
 class Surrogate:
     """The network's parameters, Adam state and activations for worlds of up
     to ``max_envs`` envs on the current CUDA device."""
@@ -129,19 +139,23 @@ class Surrogate:
         return world._handle()
 
     def forward(self, world: World, actions: torch.Tensor, stream=None) -> torch.Tensor:
-        """Network output [E * 16, 8] on the world's current state."""
+        """Network output [E * nodes, 8] on the world's current state (nodes:
+        16 agents, or 16 agents + 4 boxes in the box world)."""
         w = self._world(world, actions)
-        out = torch.empty((world.n_envs * 16, 8), dtype=torch.float32, device=actions.device)
+        out = torch.empty((world.n_envs * nodes_of(world), 8), dtype=torch.float32,
+                          device=actions.device)
         _lib.check(self._L.vmas_sur_forward(self._handle(), w, _p(actions), _p(out),
                                             _stream_handle(stream)))
         return out
 
     def loss_grad(self, world: World, actions, target, stream=None):
-        """(loss [1], gradient [param_count()]) against target [E * 16, 4]."""
+        """(loss [1], gradient [param_count()]) against target [E * nodes,
+        tw] (tw = 4: x y vx vy; 6 in the box world: also theta omega)."""
         w = self._world(world, actions)
         _dev(target)
-        if tuple(target.shape) != (world.n_envs * 16, 4):
-            raise ValueError("target must have shape [E * 16, 4]")
+        shape = (world.n_envs * nodes_of(world), target_width(world))
+        if tuple(target.shape) != shape:
+            raise ValueError("target must have shape %s" % (shape,))
         loss = torch.zeros(1, dtype=torch.float32, device=actions.device)
         grad = torch.zeros(param_count(), dtype=torch.float32, device=actions.device)
         _lib.check(self._L.vmas_sur_loss_grad(self._handle(), w, _p(actions), _p(target),
@@ -194,11 +208,21 @@ class Surrogate:
                                          _p(n_fallback), _stream_handle(stream)))
         return n_fallback
 
+    def check(self, stream=None) -> int:
+        """Wait for the stream; raise if a kernel set the surrogate's device
+        error word (a tensor-core GEMM's bounded wait ran out)."""
+        bits = ctypes.c_int32(0)
+        rc = self._L.vmas_sur_check(self._handle(), _stream_handle(stream), ctypes.byref(bits))
+        if rc == _lib.VMAS_EDEVICE:
+            raise _lib.VmasError(rc, "surrogate device error bits %d" % bits.value)
+        _lib.check(rc)
+        return bits.value
+
     def debug_features(self, world: World, actions, stream=None):
-        """(node [E*16, 16], edge [6, E*16, 16], mask [6, E*16]) as float32
-        (bfloat16 values) for the world's current state."""
+        """(node [E*nodes, 16], edge [6, E*nodes, 16], mask [6, E*nodes]) as
+        float32 (bfloat16 values) for the world's current state."""
         w = self._world(world, actions)
-        R = world.n_envs * 16
+        R = world.n_envs * nodes_of(world)
         dev = actions.device
         node = torch.zeros((R, 16), dtype=torch.bfloat16, device=dev)
         edge = torch.zeros((K, R, 16), dtype=torch.bfloat16, device=dev)
@@ -230,6 +254,20 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a=False, trans_b=False, bi
     return out, obf
 
 
+def set_gemm_engine(engine: str) -> None:
+    """Which GEMM the surrogate's kernels use, process-wide: "tcgen05" (the
+    default: the tensor-core GEMM wherever the shape allows) or "mma" (the
+    warp-level mma GEMM only, for comparisons)."""
+    _lib.check(_lib.load().vmas_debug_gemm_engine({"tcgen05": 0, "mma": 1}[engine], None))
+
+
+def tcgen05_gemm_launches() -> int:
+    """How many tcgen05 GEMMs this process has launched so far."""
+    n = ctypes.c_int64(0)
+    _lib.check(_lib.load().vmas_debug_gemm_engine(-1, ctypes.byref(n)))
+    return n.value
+
+
 def allreduce_mean(tensors, group=None):
     """Average CUDA tensors over the ranks of a torch.distributed group in
     place: directly with NCCL, through host memory with gloo."""
@@ -247,9 +285,10 @@ def allreduce_mean(tensors, group=None):
 
 
 def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=None, substeps=5,
-                        group=None, envs=None):
+                        group=None, envs=None, boxes=False):
     """Trains ``sur`` on the GPU on transitions the plain step makes: a world
-    of the surrogate's layout (``substeps`` per step) advanced by uniform
+    of the surrogate's layout (``substeps`` per step; ``boxes``: the
+    paper-scale scene of 16 agents, 4 boxes and 4 walls) advanced by uniform
     random actions, reset to its start every ``reset_every`` steps; Adam with
     a cosine schedule from lr0 to lr0 / 100.  Returns (seconds, final mean
     loss, transitions).
@@ -261,7 +300,8 @@ def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=No
     same update."""
     from . import scenes
 
-    sc = scenes.surrogate_scene(n_envs, seed, substeps=substeps)
+    sc = (scenes.paper_scene(n_envs, seed, substeps=substeps) if boxes
+          else scenes.surrogate_scene(n_envs, seed, substeps=substeps))
     if envs is not None:
         sc = sc.subset(envs)
     w = World(sc)
@@ -277,7 +317,7 @@ def train_on_plain_step(sur, n_envs, n_steps, lr0, seed, reset_every=100, log=No
         if t % reset_every == 0:
             w.set_state(init)
         # the same action stream on every rank: each takes its envs' rows
-        act = torch.rand((n_envs, 16, 3), device="cuda", generator=gen) * 2 - 1
+        act = torch.rand((n_envs, sc.n_actuated, 3), device="cuda", generator=gen) * 2 - 1
         if pick is not None:
             act = act.index_select(0, pick).contiguous()
         lr = lr0 * (0.01 + 0.99 * 0.5 * (1 + math.cos(math.pi * t / n_steps)))

@@ -136,8 +136,8 @@ def test_graph_rollout_tiles_and_autotune(vmas_lib):
     rw2.close()
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_extreme_env_sizes(vmas_lib, orc, persistent):
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+def test_extreme_env_sizes(vmas_lib, orc, schedule):
     """Envs of 1 entity and of 128 entities (the largest class) side by side,
     under either schedule."""
     from paper_2207_03530_b300.ragged import RaggedWorld
@@ -157,7 +157,7 @@ def test_extreme_env_sizes(vmas_lib, orc, persistent):
     rw = RaggedWorld([1, n_big], shape, flags, size_a, size_b, mass, inertia, st,
                      substeps=2, dt=0.05, drag=0.1)
     assert rw.class_envs[0] == 1 and rw.class_envs[4] == 1
-    rw.persistent = persistent
+    rw.schedule = schedule
     pact = torch.zeros((rw.n_action_rows, 3), device="cuda")
     rw.step(pact)
     got = rw.state().cpu().numpy()
@@ -208,7 +208,7 @@ def test_full_config_sampled_envs(vmas_lib, orc):
     rw.autotune(pact[:8])
     lanes, tile = rw.tuning()
     rw2.set_tuning(lanes, tile)
-    rw2.persistent = rw.persistent
+    rw2.schedule = rw.schedule
     rw.rollout(pact[:1])
     got = rw.state().cpu().numpy()
     full, sel = _unpack_state(got, counts, sc.n_entities)
@@ -229,8 +229,8 @@ def test_full_config_sampled_envs(vmas_lib, orc):
 PERSIST_LANES = [8, 8, 16, 32, 32]  # the persistent schedule's fixed lanes per class
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed):
+@pytest.mark.parametrize("seed,schedule", [(0, 1), (1, 1), (0, 2)])
+def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed, schedule):
     """Every size class in one persistent launch (warps take one warp's worth
     of envs at a time from an atomic work queue, largest class first):
     against the FP64 oracle, and bitwise equal to the per-class launches
@@ -241,7 +241,7 @@ def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed):
     per, pers = _ragged(sc, counts), _ragged(sc, counts)
     assert (pers.class_envs > 0).sum() >= 4
     per.set_tuning(PERSIST_LANES, 1)
-    pers.persistent = True
+    pers.schedule = schedule
     assert pers.persistent and not per.persistent
     pact = torch.from_numpy(_packed_actions(per, sc, act)).cuda()
     for t in range(2):

@@ -191,3 +191,68 @@ def test_forward_hand_worked_catches_planted_mistakes():
     mistakes += [dict(drop_bias=b) for b in ("be1", "be2", "b1", "b2", "b3")]
     for mk in mistakes:
         assert not np.array_equal(net(**mk), HAND_OUT), mk
+
+
+def test_box_world_features_hand_worked():
+    """Box world: the node of a box (bounding radius = half diagonal, angle,
+    angular velocity, torque over inertia) and an agent's edge to it, worked
+    by hand.  Box 16: 0.1 x 0.2 at (0.1, 0), theta = pi / 6, omega = 2,
+    mass 5, default inertia 5 (0.1^2 + 0.2^2) / 12 = 0.0208333, action
+    (0.5, -1, 0.6); agent 3 at the origin (r = 0.05, mass 2), every other
+    body more than 0.3 away."""
+    E, N = 1, 24
+    st = np.zeros((E, N, 6))
+    shape = np.zeros((E, N), int)
+    sa = np.full((E, N), 0.05)
+    sb = np.zeros((E, N))
+    mass = np.full((E, N), 2.0)
+    inertia = np.zeros((E, N))
+    xs = np.linspace(-0.8, 0.8, 5)
+    far = [(x, y) for y in (-0.8, 0.8) for x in xs] + [(-0.8, -0.4), (0.8, -0.4), (-0.8, 0.4),
+                                                       (0.8, 0.4), (-0.4, 0.45)]
+    k = 0
+    for i in range(16):
+        if i != 3:
+            st[0, i, :2] = far[k]
+            k += 1
+    shape[0, 16:20] = 1
+    sa[0, 16:20], sb[0, 16:20], mass[0, 16:20] = 0.1, 0.2, 5.0
+    st[0, 16, :2], st[0, 16, 4], st[0, 16, 5] = (0.1, 0.0), math.pi / 6, 2.0
+    for q, (x, y) in enumerate([(0.45, 0.45), (0.45, -0.45), (-0.45, -0.05)]):
+        st[0, 17 + q, :2] = (x, y)
+    shape[0, 20:] = 2
+    act = np.zeros((E, 20, 3))
+    act[0, 16] = [0.5, -1.0, 0.6]
+    node, edge, mask = S.features_box(st, act, shape, sa, sb, mass, inertia)
+    R = math.hypot(0.05, 0.1)  # 0.1118034
+    I = 5.0 * (0.01 + 0.04) / 12.0
+    np.testing.assert_allclose(node[16], [0, 0, 0.1, -0.2, 10 * R, 0.2, 1, 1, 1, 1, 1,
+                                          math.sqrt(3) / 2, 0.5, 0.2, 0.01 * 0.6 / I, 0],
+                               rtol=0, atol=1e-12)
+    assert mask[3].sum() == 1.0 and mask[16].sum() == 1.0
+    np.testing.assert_allclose(edge[3, 0, :11], [0.1 / 0.3, 0, 0, 0, 10 * R,
+                                                 (0.1 - 0.05 - R) / 0.3, 1, 1, math.sqrt(3) / 2,
+                                                 0.5, 0.2], rtol=0, atol=1e-12)
+    # the box's edge back to the agent carries no box fields
+    np.testing.assert_allclose(edge[16, 0, :8], [-0.1 / 0.3, 0, 0, 0, 0.5,
+                                                 (0.1 - R - 0.05) / 0.3, 1, 0], atol=1e-12)
+    # an agent's node is the sphere world's (zeros past slot 9)
+    assert np.all(node[3, 10:] == 0) and node[3, 4] == 0.5
+
+
+def test_box_world_loss_counts_used_outputs():
+    """The loss averages over the outputs each row uses: 4 per agent, 6 per
+    box (88 per env); a box's angle columns count, an agent's do not."""
+    rng = np.random.default_rng(4)
+    w = S.init_weights(1)
+    R = 20
+    node = rng.normal(0, 0.5, (R, 16))
+    edge = rng.normal(0, 0.5, (R, S.K, 16))
+    mask = (rng.uniform(size=(R, S.K)) < 0.5).astype(float)
+    out = S.forward(w, node, edge, mask)
+    tgt = rng.normal(0, 1, (R, 6))
+    used = S.used_outputs(1, 20)
+    assert used.sum() == 88
+    loss, _ = S.loss_and_grad(w, node, edge, mask, tgt, used=used)
+    se = ((out[:16, :4] - tgt[:16, :4]) ** 2).sum() + ((out[16:, :6] - tgt[16:, :6]) ** 2).sum()
+    assert loss == pytest.approx(se / 88, rel=1e-12)
