@@ -682,10 +682,10 @@ def run_ragged(args):
     torch.cuda.synchronize()
     padded = E * 17 / (a.elapsed_time(b) / 1e3)
     w.close()
-    # per env-step, as for the plain step: state read + write of every
-    # entity and the useful action rows (the tiled rollout touches the state
-    # once per launch, so this is what a one-step launch would move)
-    b_env = (int(counts.sum()) * 48 + int(rw.n_action_rows) * 12) / E
+    # per env-step: the state of every entity read and written once per
+    # launch of `tile` steps (it stays on chip in between), the useful action
+    # rows every step
+    b_env = (int(counts.sum()) * 48 / tile + int(rw.n_action_rows) * 12) / E
     print(json.dumps({
         "form": "ragged", "metric": "env-steps/s, ragged rollout (CUDA graph, autotuned)",
         "value": value, "unit": UNIT, "ms_per_rollout": ms, "rollout_steps": T,

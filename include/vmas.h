@@ -313,6 +313,13 @@ int vmas_diff_backward(vmas_world *world, const float *d_actions, int32_t n_step
                        const float *d_goals, int32_t ckpt_every, const float *d_ckpt,
                        const float *d_dloss, float *d_grad, void *stream);
 
+/* Diagnostic: lanes per env of the differentiable rollout, process-wide:
+ * 1 = one group of G lanes per env (G the smallest power of two >= n_entities),
+ * 2 = two such groups per env, each summing half of every entity's pairs
+ * (the default, 0, where two groups fit a warp).  Both give the gradient to
+ * rounding; split 2 fills twice the warps. */
+int vmas_debug_diff_split(int32_t split);
+
 /* Test hook for failure detection without a GPU fault: while `on` is set,
  * every CTA of vmas_step that stages its inputs with bulk copies waits for 16
  * transaction bytes that no copy delivers, so its bounded wait runs out (in
@@ -370,25 +377,35 @@ int vmas_step_noalloc(const vmas_step_noalloc_args *args, void *stream);
 /* ---- Learned surrogate of the world step --------------------------------
  * Not part of the paper's method: a network trained on the transitions that
  * the step of section 3 (Eqs. 1-3, all substeps) produces, standing in for
- * it on the walled sphere world: per env 16 movable, actuated, non-rotating
- * agent spheres (action rows 0..15) then 4 fixed lines (the walls at x = +-1
- * and y = +-1).  Worlds of any other layout give VMAS_EINVAL.
+ * it on two world layouts (walls at x = +-1 and y = +-1):
+ *  - the sphere world: per env 16 movable, actuated, non-rotating agent
+ *    spheres (action rows 0..15), then 4 fixed lines;
+ *  - the box world (the paper-scale layout): the same 16 agents, then 4
+ *    movable, rotatable, actuated boxes (action rows 16..19, torque used),
+ *    then 4 fixed lines.
+ * Worlds of any other layout give VMAS_EINVAL.  The network has one row
+ * ("node") per agent and per box: nodes = 16 or 20 per env.
  *
- * Network, per agent: node features (10 vx, 10 vy, f/m, 10 r, 1/m and the
- * 4 wall gaps min(gap, 0.3)/0.3); edge features for up to 6 nearest other
- * agents within 0.3 (relative position / 0.3, 10 relative velocity, 10 r_j,
- * surface gap / 0.3, 1); edge MLP 16 -> 64 -> 64 (GELU) summed over the
- * edges; node MLP 80 -> 128 -> 128 -> 8 (GELU); prediction
- * x' = x + 0.01 out[0:2], v' = v + 0.1 out[2:4].  Weights and activations
- * bfloat16, accumulation FP32 (tensor-core mma), biases FP32.
+ * Network, per node: node features (10 vx, 10 vy, f/m, 10 R, 1/m and the 4
+ * wall gaps min(gap, 0.3)/0.3 of its bounding circle of radius R; a box adds
+ * a flag, cos theta, sin theta, 0.1 omega, 0.01 torque / I); edge features
+ * for up to 6 nearest other nodes within 0.3 (relative position / 0.3, 10
+ * relative velocity, 10 R_j, bounding-circle gap / 0.3, 1; a box neighbour
+ * adds a flag, cos theta_j, sin theta_j, 0.1 omega_j); edge MLP 16 -> 64 ->
+ * 64 (GELU) summed over the edges; node MLP 80 -> 128 -> 128 -> 8 (GELU);
+ * prediction x' = x + 0.01 out[0:2], v' = v + 0.1 out[2:4], and for a box
+ * theta' = theta + 0.1 out[4], omega' = omega + out[5].  Weights and
+ * activations bfloat16, accumulation FP32 (tensor cores: tcgen05 for the
+ * layered path's large GEMMs, warp-level mma elsewhere), biases FP32.
  *
  * Parameters: vmas_sur_param_count() FP32 values in the order We1 [64][16],
  * be1 [64], We2 [64][64], be2 [64], W1 [128][80], b1 [128], W2 [128][128],
  * b2 [128], W3 [8][128], b3 [8] (weights [out][in]); the library keeps an
  * FP32 master copy and rounds the weights to bfloat16 for the GEMMs.
- * Training minimises mean((out[:, 0:4] - target)^2), the target being the
- * plain step's deltas (x, y, vx, vy) over (0.01, 0.01, 0.1, 0.1), with Adam
- * (beta 0.9 / 0.999, eps 1e-8).
+ * Training minimises the mean of (out - target)^2 over the outputs each node
+ * uses (4 for an agent, 6 for a box), the target being the plain step's
+ * deltas of (x, y, vx, vy[, theta, omega]) over (0.01, 0.01, 0.1, 0.1[, 0.1,
+ * 1]), with Adam (beta 0.9 / 0.999, eps 1e-8).
  *
  * A surrogate is created for at most max_envs envs (its activations are
  * sized for them) and serves any world of that layout and size; d_actions
@@ -404,16 +421,18 @@ int vmas_sur_set_params(vmas_surrogate *sur, const float *h_params);
 int vmas_sur_get_params(vmas_surrogate *sur, float *h_params);
 /* Inference kernels of vmas_sur_forward and vmas_sur_step:
  * VMAS_SUR_FUSED (the default): one kernel, one warp per env, everything on
- * chip; VMAS_SUR_LAYERED: one GEMM launch per layer over all envs, with the
- * activations in device memory (the path training uses).  Both give the
- * same results. */
+ * chip (sphere world only; box worlds always take the layered path);
+ * VMAS_SUR_LAYERED: one GEMM launch per layer over all envs, with the
+ * activations in device memory (the path training uses).  Both round at the
+ * same points. */
 enum { VMAS_SUR_FUSED = 0, VMAS_SUR_LAYERED = 1 };
 int vmas_sur_set_mode(vmas_surrogate *sur, int32_t mode);
-/* The network on the world's current state: d_out [n_envs * 16][8] (device,
- * may be NULL), row e * 16 + i for agent i of env e. */
+/* The network on the world's current state: d_out [n_envs * nodes][8]
+ * (device, may be NULL), row e * nodes + i for node i of env e. */
 int vmas_sur_forward(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
                      float *d_out, void *stream);
-/* Loss against d_target [n_envs * 16][4] into d_loss [1] (may be NULL) and
+/* Loss against d_target [n_envs * nodes][tw] (tw = 4: x y vx vy; 6 in the
+ * box world: also theta omega) into d_loss [1] (may be NULL) and
  * its gradient, kept for vmas_sur_adam and copied to d_grad
  * [vmas_sur_param_count()] (may be NULL).  The world is not changed. */
 int vmas_sur_loss_grad(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
@@ -431,18 +450,19 @@ int vmas_sur_train_grad(vmas_surrogate *sur, vmas_world *world, const float *d_a
 /* vmas_sur_train_grad then one Adam update. */
 int vmas_sur_train_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions, float lr,
                         float *d_loss, void *stream);
-/* One world step by the surrogate.  Envs whose predicted agents overlap one
- * another, or a wall, by more than `limit` world units (or whose prediction is
- * not finite) are stepped by the plain step instead; the other envs take the
- * prediction (x, y, vx, vy of the agents; angles and walls unchanged).
+/* One world step by the surrogate.  Envs whose predicted bodies overlap one
+ * another, or a wall, by more than `limit` world units (sphere-box and box-box
+ * by the step's narrow phase; or whose prediction is not finite) are stepped
+ * by the plain step instead; the other envs take the prediction (x, y, vx,
+ * vy of the agents and boxes, and the boxes' theta, omega; walls unchanged).
  * d_n_fallback (device int32, may be NULL) receives the number of envs that
  * fell back. */
 int vmas_sur_step(vmas_surrogate *sur, vmas_world *world, const float *d_actions, float limit,
                   int32_t *d_n_fallback, void *stream);
 /* Diagnostic: the features of the world's current state as bfloat16 bits,
- * d_node [n_envs * 16][16], d_edge [6][n_envs * 16][16] (neighbour slot
- * major), d_mask [6][n_envs * 16] (1 for a present neighbour); any may be
- * NULL. */
+ * d_node [n_envs * nodes][16], d_edge [6][n_envs * nodes][16] (neighbour
+ * slot major), d_mask [6][n_envs * nodes] (1 for a present neighbour); any
+ * may be NULL. */
 int vmas_sur_debug_features(vmas_surrogate *sur, vmas_world *world, const float *d_actions,
                             uint16_t *d_node, uint16_t *d_edge, float *d_mask, void *stream);
 /* Wait for `stream` and return VMAS_EDEVICE (clearing the word) if one of

@@ -17,10 +17,15 @@
 // The contact mask is piecewise constant (no term from the jump at g = 0);
 // forces on immovable entities are dropped, so their lF is 0.
 //
-// Layout: groups of G lanes (G = 4, 8, 16 or 32, the smallest power of two
-// >= N), one environment per group and 32 / G per warp, entity i in lane i
-// of its group (N <= 32); the pair sums of entity i run over j = 0 .. N-1 in
-// order, the same order as a serial loop over canonical pairs.  Checkpoints every K steps hold (x, y, vx, vy)
+// Layout: groups of SPL G lanes (G = 4, 8, 16 or 32, the smallest power of
+// two >= N; SPL = 1 or 2), one environment per group and 32 / (SPL G) per
+// warp, entity i in lane i of each of its SPL half-groups (N <= 32).  With
+// SPL = 1 the pair sums of entity i run over j = 0 .. N-1 in order, the same
+// order as a serial loop over canonical pairs; with SPL = 2 the two halves
+// of the group sum j < ceil(N/2) and the rest, and one shuffle adds the two
+// partial sums (both halves then hold the same bits), which halves each
+// substep's dependent chain and doubles the warps a small batch of envs
+// fills.  Checkpoints every K steps hold (x, y, vx, vy)
 // of every entity; the backward pass re-runs each K-step segment forward from
 // its checkpoint into shared memory (positions at every substep start) and
 // sweeps it backward, segments last to first.
@@ -84,7 +89,8 @@ struct DiffLane {
   int row;
 };
 
-// Entity `ent` of env e (its group's lanes in gmask; valid = the group has an env).
+// Entity `ent` of env e (the lanes of its group's first half in gmask, lane
+// = this entity's lane in that half; valid = the group has an env).
 __device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, bool valid, int ent,
                                               unsigned gmask, int lane) {
   DiffLane L{};
@@ -103,22 +109,45 @@ __device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, bool v
   return L;
 }
 
-// One forward substep of entity `lane` of its env; s_pos holds every entity's (x, y).
+// One forward substep of entity `lane` of its env; s_pos holds every entity's
+// (x, y).  SPL = 2: this lane sums the pairs of its half (`half`) of j and
+// the partner lane (lane ^ G) the other half.
+template <int G, int SPL>
 __device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane &L, int lane,
-                                             const float2 *s_pos, const uint8_t *s_kind,
+                                             int half, const float2 *s_pos, const uint8_t *s_kind,
                                              const float *s_r, float fax, float fay, float &x,
                                              float &y, float &vx, float &vy) {
   float Fx = fax + L.m * p.gx, Fy = fay + L.m * p.gy;
-  if (L.ok && (L.kd & kCollidable)) {
-    for (int j = 0; j < p.N; ++j) {
-      if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
-      const float2 q = s_pos[j];
-      float fx, fy;
-      if (sphere_force(x, y, q.x, q.y, L.r + s_r[j], p, fx, fy, nullptr)) {
-        Fx += fx;
-        Fy += fy;
+  if constexpr (SPL == 1) {
+    if (L.ok && (L.kd & kCollidable)) {
+      for (int j = 0; j < p.N; ++j) {
+        if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+        const float2 q = s_pos[j];
+        float fx, fy;
+        if (sphere_force(x, y, q.x, q.y, L.r + s_r[j], p, fx, fy, nullptr)) {
+          Fx += fx;
+          Fy += fy;
+        }
       }
     }
+  } else {
+    float Px = 0.f, Py = 0.f;
+    if (L.ok && (L.kd & kCollidable)) {
+      const int span = (p.N + 1) / 2, j0 = half * span, j1 = min(p.N, j0 + span);
+      for (int j = j0; j < j1; ++j) {
+        if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+        const float2 q = s_pos[j];
+        float fx, fy;
+        if (sphere_force(x, y, q.x, q.y, L.r + s_r[j], p, fx, fy, nullptr)) {
+          Px += fx;
+          Py += fy;
+        }
+      }
+    }
+    Px += __shfl_xor_sync(0xffffffffu, Px, G);
+    Py += __shfl_xor_sync(0xffffffffu, Py, G);
+    Fx += Px;
+    Fy += Py;
   }
   if (L.mov) {
     vx = p.damp * vx + Fx * L.im * p.h;
@@ -128,30 +157,33 @@ __device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane
   }
 }
 
-template <int G>
+template <int G, int SPL>
 __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const DiffParams p) {
-  constexpr int EPW = 32 / G;
+  constexpr int EPW = 32 / (G * SPL);
   __shared__ float2 s_pos_all[kDiffWarps][32];
   __shared__ uint8_t s_kind_all[kDiffWarps][32];
   __shared__ float s_r_all[kDiffWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = lane / G, ent = lane % G;
+  const int grp = lane / (G * SPL), ent = lane % G, half = (lane / G) % SPL;
   const int e0 = (blockIdx.x * kDiffWarps + warp) * EPW;
   if (e0 >= p.E) return;  // whole warp leaves together
   const int e = e0 + grp;
   const bool valid = e < p.E;
-  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G * SPL);
   float2 *s_pos = s_pos_all[warp] + grp * G;
   uint8_t *s_kind = s_kind_all[warp] + grp * G;
   float *s_r = s_r_all[warp] + grp * G;
-  const DiffLane L = diff_lane(p, e, valid, ent, gmask, lane);
+  const DiffLane L = diff_lane(p, e, valid, ent, gmask, grp * G * SPL + ent);
+  const bool w0 = half == 0;  // the lane that writes this entity's shared and global values
   const size_t t0 = L.ok ? (size_t)e * p.N + ent : 0;
   float x = L.ok ? p.px[t0] : 0.f, y = L.ok ? p.py[t0] : 0.f;
   float vx = L.ok ? p.vx[t0] : 0.f, vy = L.ok ? p.vy[t0] : 0.f;
-  s_kind[ent] = (uint8_t)L.kd;
-  s_r[ent] = L.r;
+  if (w0) {
+    s_kind[ent] = (uint8_t)L.kd;
+    s_r[ent] = L.r;
+  }
   for (int t = 0; t < p.T; ++t) {
-    if (t % p.K == 0 && L.ok) {
+    if (t % p.K == 0 && L.ok && w0) {
       float4 *c = reinterpret_cast<float4 *>(p.ckpt) + ((size_t)(t / p.K) * p.E + e) * p.N + ent;
       *c = make_float4(x, y, vx, vy);
     }
@@ -162,9 +194,9 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
       fay = a[1];
     }
     for (int s = 0; s < p.S; ++s) {
-      s_pos[ent] = make_float2(x, y);
+      if (w0) s_pos[ent] = make_float2(x, y);
       __syncwarp();
-      diff_substep(p, L, ent, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
+      diff_substep<G, SPL>(p, L, ent, half, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
       __syncwarp();
     }
   }
@@ -175,7 +207,7 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
     l = dx * dx + dy * dy;
   }
   for (int o = G / 2; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if (ent == 0 && valid) p.loss[e] = l;
+  if (ent == 0 && w0 && valid) p.loss[e] = l;
 }
 
 // Dynamic shared memory per warp: positions at the K * S + 1 substep starts
@@ -184,28 +216,31 @@ __host__ __device__ inline size_t diff_traj_bytes(int K, int S) {
   return (size_t)(K * S + 1) * 32 * sizeof(float2);
 }
 
-template <int G>
+template <int G, int SPL>
 __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const DiffParams p) {
-  constexpr int EPW = 32 / G;
+  constexpr int EPW = 32 / (G * SPL);
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ float2 s_lf_all[kDiffWarps][32];
   __shared__ uint8_t s_kind_all[kDiffWarps][32];
   __shared__ float s_r_all[kDiffWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = lane / G, ent = lane % G;
+  const int grp = lane / (G * SPL), ent = lane % G, half = (lane / G) % SPL;
   const int e0 = (blockIdx.x * kDiffWarps + warp) * EPW;
   if (e0 >= p.E) return;  // whole warp leaves together
   const int e = e0 + grp;
   const bool valid = e < p.E;
-  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G);
-  // traj row q holds the 32 lanes' positions; this group's are at grp * G
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G * SPL);
+  const bool w0 = half == 0;  // the lane that writes this entity's shared and global values
+  // traj row q holds 32 entity slots; this group's entities are at grp * G
   float2 *traj = reinterpret_cast<float2 *>(dsm + warp * diff_traj_bytes(p.K, p.S)) + grp * G;
   float2 *s_lf = s_lf_all[warp] + grp * G;
   uint8_t *s_kind = s_kind_all[warp] + grp * G;
   float *s_r = s_r_all[warp] + grp * G;
-  const DiffLane L = diff_lane(p, e, valid, ent, gmask, lane);
-  s_kind[ent] = (uint8_t)L.kd;
-  s_r[ent] = L.r;
+  const DiffLane L = diff_lane(p, e, valid, ent, gmask, grp * G * SPL + ent);
+  if (w0) {
+    s_kind[ent] = (uint8_t)L.kd;
+    s_r[ent] = L.r;
+  }
   float lx = 0.f, ly = 0.f, lvx = 0.f, lvy = 0.f;
   const int nseg = (p.T + p.K - 1) / p.K;
   for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -223,9 +258,9 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
         fay = a[1];
       }
       for (int s = 0; s < p.S; ++s, ++q) {
-        traj[q * 32 + ent] = make_float2(x, y);
+        if (w0) traj[q * 32 + ent] = make_float2(x, y);
         __syncwarp();
-        diff_substep(p, L, ent, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
+        diff_substep<G, SPL>(p, L, ent, half, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
         __syncwarp();
       }
     }
@@ -250,25 +285,48 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
         }
         gax += lfx;
         gay += lfy;
-        s_lf[ent] = make_float2(lfx, lfy);
+        if (w0) s_lf[ent] = make_float2(lfx, lfy);
         __syncwarp();
-        if (L.ok && (L.kd & kCollidable)) {
-          const float2 me = traj[q * 32 + ent];
-          for (int j = 0; j < p.N; ++j) {
-            if (j == ent || !pair_active(L.kd, s_kind[j])) continue;
-            const float2 o = traj[q * 32 + j];
-            float fx, fy, J[3];
-            if (sphere_force(me.x, me.y, o.x, o.y, L.r + s_r[j], p, fx, fy, J)) {
-              const float2 lj = s_lf[j];
-              const float dx = lfx - lj.x, dy = lfy - lj.y;
-              lx += J[0] * dx + J[1] * dy;
-              ly += J[1] * dx + J[2] * dy;
+        if constexpr (SPL == 1) {
+          if (L.ok && (L.kd & kCollidable)) {
+            const float2 me = traj[q * 32 + ent];
+            for (int j = 0; j < p.N; ++j) {
+              if (j == ent || !pair_active(L.kd, s_kind[j])) continue;
+              const float2 o = traj[q * 32 + j];
+              float fx, fy, J[3];
+              if (sphere_force(me.x, me.y, o.x, o.y, L.r + s_r[j], p, fx, fy, J)) {
+                const float2 lj = s_lf[j];
+                const float dx = lfx - lj.x, dy = lfy - lj.y;
+                lx += J[0] * dx + J[1] * dy;
+                ly += J[1] * dx + J[2] * dy;
+              }
             }
           }
+        } else {
+          float px_ = 0.f, py_ = 0.f;
+          if (L.ok && (L.kd & kCollidable)) {
+            const float2 me = traj[q * 32 + ent];
+            const int span = (p.N + 1) / 2, j0 = half * span, j1 = min(p.N, j0 + span);
+            for (int j = j0; j < j1; ++j) {
+              if (j == ent || !pair_active(L.kd, s_kind[j])) continue;
+              const float2 o = traj[q * 32 + j];
+              float fx, fy, J[3];
+              if (sphere_force(me.x, me.y, o.x, o.y, L.r + s_r[j], p, fx, fy, J)) {
+                const float2 lj = s_lf[j];
+                const float dx = lfx - lj.x, dy = lfy - lj.y;
+                px_ += J[0] * dx + J[1] * dy;
+                py_ += J[1] * dx + J[2] * dy;
+              }
+            }
+          }
+          px_ += __shfl_xor_sync(0xffffffffu, px_, G);
+          py_ += __shfl_xor_sync(0xffffffffu, py_, G);
+          lx += px_;
+          ly += py_;
         }
         __syncwarp();
       }
-      if (L.act) {
+      if (L.act && w0) {
         float *g = p.grad + (((size_t)t * p.E + e) * p.A + L.row) * 3;
         g[0] = gax;
         g[1] = gay;

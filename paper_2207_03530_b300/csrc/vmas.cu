@@ -875,6 +875,15 @@ int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
 // of two that holds the env's entities.
 static int diff_group_lanes(int N) { return N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32; }
 
+// Half-groups per env in the differentiable rollout: 2 (each env's pair
+// loops split over two half-groups of lanes) wherever two groups fit a warp,
+// unless vmas_debug_diff_split chose otherwise.  Process-wide.
+static int g_diff_split = 0;  // 0: automatic
+static int diff_split(int G) {
+  if (G >= 32) return 1;
+  return g_diff_split ? g_diff_split : 2;
+}
+
 static int diff_setup(vmas_world *w, int32_t T, int32_t K, vmas::DiffParams *p) {
   if (!w) return fail(VMAS_EINVAL, "world is NULL");
   if (!w->diff_ok)
@@ -918,14 +927,18 @@ int vmas_diff_rollout(vmas_world *w, const float *d_actions, int32_t n_steps,
   p.goals = d_goals;
   p.ckpt = d_ckpt;
   p.loss = d_loss;
-  const int G = diff_group_lanes(w->N), per_cta = vmas::kDiffWarps * (32 / G);
+  const int G = diff_group_lanes(w->N), spl = diff_split(G);
+  const int per_cta = vmas::kDiffWarps * (32 / (G * spl));
   const int grid = (w->E + per_cta - 1) / per_cta;
   cudaStream_t st = as_stream(stream);
-  switch (G) {
-    case 4: vmas::diff_forward_kernel<4><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
-    case 8: vmas::diff_forward_kernel<8><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
-    case 16: vmas::diff_forward_kernel<16><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
-    default: vmas::diff_forward_kernel<32><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+  switch (G * 4 + spl) {
+    case 4 * 4 + 1: vmas::diff_forward_kernel<4, 1><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 4 * 4 + 2: vmas::diff_forward_kernel<4, 2><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 8 * 4 + 1: vmas::diff_forward_kernel<8, 1><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 8 * 4 + 2: vmas::diff_forward_kernel<8, 2><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 16 * 4 + 1: vmas::diff_forward_kernel<16, 1><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    case 16 * 4 + 2: vmas::diff_forward_kernel<16, 2><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
+    default: vmas::diff_forward_kernel<32, 1><<<grid, vmas::kDiffWarps * 32, 0, st>>>(p); break;
   }
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
@@ -946,11 +959,18 @@ int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
   if (smem > 220 * 1024)
     return fail(VMAS_EINVAL, "ckpt_every * substeps too large for on-chip segment replay; "
                              "use a shorter checkpoint interval");
-  const int G = diff_group_lanes(w->N), per_cta = vmas::kDiffWarps * (32 / G);
-  auto kern = G == 4 ? vmas::diff_backward_kernel<4>
-                     : G == 8 ? vmas::diff_backward_kernel<8>
-                              : G == 16 ? vmas::diff_backward_kernel<16>
-                                        : vmas::diff_backward_kernel<32>;
+  const int G = diff_group_lanes(w->N), spl = diff_split(G);
+  const int per_cta = vmas::kDiffWarps * (32 / (G * spl));
+  auto kern = vmas::diff_backward_kernel<32, 1>;
+  switch (G * 4 + spl) {
+    case 4 * 4 + 1: kern = vmas::diff_backward_kernel<4, 1>; break;
+    case 4 * 4 + 2: kern = vmas::diff_backward_kernel<4, 2>; break;
+    case 8 * 4 + 1: kern = vmas::diff_backward_kernel<8, 1>; break;
+    case 8 * 4 + 2: kern = vmas::diff_backward_kernel<8, 2>; break;
+    case 16 * 4 + 1: kern = vmas::diff_backward_kernel<16, 1>; break;
+    case 16 * 4 + 2: kern = vmas::diff_backward_kernel<16, 2>; break;
+    default: break;
+  }
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -966,6 +986,12 @@ int vmas_diff_backward(vmas_world *w, const float *d_actions, int32_t n_steps,
   const int grid = (w->E + per_cta - 1) / per_cta;
   kern<<<grid, vmas::kDiffWarps * 32, smem, st>>>(p);
   VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int vmas_debug_diff_split(int32_t split) {
+  if (split < 0 || split > 2) return fail(VMAS_EINVAL, "split must be 0, 1 or 2");
+  g_diff_split = split;
   return VMAS_OK;
 }
 

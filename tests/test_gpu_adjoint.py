@@ -34,8 +34,19 @@ def _relerr(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-12)
 
 
+@pytest.fixture(params=[1, 2], ids=["split1", "split2"])
+def split(request, vmas_lib):
+    """Lanes per env of the differentiable rollout: one group, or two
+    half-groups that each sum half of every entity's pairs (the default)."""
+    from paper_2207_03530_b300 import _lib
+
+    _lib.check(vmas_lib.vmas_debug_diff_split(request.param))
+    yield request.param
+    _lib.check(vmas_lib.vmas_debug_diff_split(0))
+
+
 @pytest.mark.parametrize("dense", [False, True])
-def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense):
+def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense, split):
     """64 envs x 50 steps x 3 substeps: loss and gradient against the
     oracle's (normwise, per tensor); FP32 through 150 substeps of stiff
     contacts."""
@@ -49,8 +60,8 @@ def test_loss_and_gradient_match_oracle(vmas_lib, orc, dense):
     ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
     assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= LOSS_TOL
     err = _relerr(a.grad.cpu().numpy(), ref_grad)
-    print("\n[adjoint] 64 envs dense=%s: loss err %.2e, gradient err %.2e"
-          % (dense, _relerr(loss.detach().cpu().numpy(), ref_loss), err))
+    print("\n[adjoint] 64 envs dense=%s split=%d: loss err %.2e, gradient err %.2e"
+          % (dense, split, _relerr(loss.detach().cpu().numpy(), ref_loss), err))
     assert err <= GRAD_TOL, err
     # the world's own state is untouched by the differentiable rollout
     assert np.array_equal(w.state().cpu().numpy(), sc.init_state)
@@ -132,7 +143,7 @@ def _sphere_subset(sc, ents, A):
 
 
 @pytest.mark.parametrize("which,E", [("n3", 5), ("n6", 17), ("n16", 7), ("n16", 1)])
-def test_lane_groups_of_every_width(vmas_lib, orc, which, E):
+def test_lane_groups_of_every_width(vmas_lib, orc, which, E, split):
     """Envs of 3, 6 and 16 spheres take 4, 8 and 16 lanes (8, 4 and 2 envs
     per warp); env counts that leave groups of a warp empty."""
     from paper_2207_03530_b300 import World
@@ -153,6 +164,7 @@ def test_lane_groups_of_every_width(vmas_lib, orc, which, E):
     loss.sum().backward()
     ref_loss, ref_grad = orc.rollout_grad(sc, sc.init_state, act, goals)
     assert _relerr(loss.detach().cpu().numpy(), ref_loss) <= LOSS_TOL
-    print("\n[adjoint] %s E=%d: gradient err %.2e" % (which, E, _relerr(a.grad.cpu().numpy(), ref_grad)))
+    print("\n[adjoint] %s E=%d split=%d: gradient err %.2e"
+          % (which, E, split, _relerr(a.grad.cpu().numpy(), ref_grad)))
     assert _relerr(a.grad.cpu().numpy(), ref_grad) <= GRAD_TOL
     w.close()
