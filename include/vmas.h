@@ -315,9 +315,9 @@ int vmas_diff_backward(vmas_world *world, const float *d_actions, int32_t n_step
 
 /* Diagnostic: lanes per env of the differentiable rollout, process-wide:
  * 1 = one group of G lanes per env (G the smallest power of two >= n_entities),
- * 2 = two such groups per env, each summing half of every entity's pairs
- * (the default, 0, where two groups fit a warp).  Both give the gradient to
- * rounding; split 2 fills twice the warps. */
+ * 2 = two such groups per env where two fit a warp, each summing half of
+ * every entity's pairs; 0 = the default (1).  Both give the gradient to
+ * rounding; split 2 fills twice the warps with the same envs. */
 int vmas_debug_diff_split(int32_t split);
 
 /* Test hook for failure detection without a GPU fault: while `on` is set,

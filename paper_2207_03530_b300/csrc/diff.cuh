@@ -23,9 +23,10 @@
 // SPL = 1 the pair sums of entity i run over j = 0 .. N-1 in order, the same
 // order as a serial loop over canonical pairs; with SPL = 2 the two halves
 // of the group sum j < ceil(N/2) and the rest, and one shuffle adds the two
-// partial sums (both halves then hold the same bits), which halves each
-// substep's dependent chain and doubles the warps a small batch of envs
-// fills.  Checkpoints every K steps hold (x, y, vx, vy)
+// partial sums (both halves then hold the same bits), which shortens each
+// substep's pair loop and doubles the warps a small batch of envs fills (the
+// host uses SPL = 1 unless asked otherwise: the envs in flight, not the
+// warps, bound this latency-bound chain).  Checkpoints every K steps hold (x, y, vx, vy)
 // of every entity; the backward pass re-runs each K-step segment forward from
 // its checkpoint into shared memory (positions at every substep start) and
 // sweeps it backward, segments last to first.

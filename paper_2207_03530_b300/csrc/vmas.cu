@@ -875,13 +875,16 @@ int vmas_pair_table(const vmas_world *w, int32_t *pair_i, int32_t *pair_j) {
 // of two that holds the env's entities.
 static int diff_group_lanes(int N) { return N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32; }
 
-// Half-groups per env in the differentiable rollout: 2 (each env's pair
-// loops split over two half-groups of lanes) wherever two groups fit a warp,
-// unless vmas_debug_diff_split chose otherwise.  Process-wide.
-static int g_diff_split = 0;  // 0: automatic
+// Half-groups per env in the differentiable rollout: 1 by default; 2 (each
+// env's pair loops split over two half-groups of lanes, where two groups fit
+// a warp) when vmas_debug_diff_split chose it.  Process-wide.  The split
+// fills more warps but not more envs, and costs the second half-group's copy
+// of the integration: measured 546 against 507 us for the 4,096-env
+// backward, so it stays off.
+static int g_diff_split = 0;  // 0: automatic (1)
 static int diff_split(int G) {
   if (G >= 32) return 1;
-  return g_diff_split ? g_diff_split : 2;
+  return g_diff_split ? g_diff_split : 1;
 }
 
 static int diff_setup(vmas_world *w, int32_t T, int32_t K, vmas::DiffParams *p) {

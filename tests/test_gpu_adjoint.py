@@ -36,8 +36,8 @@ def _relerr(got, ref):
 
 @pytest.fixture(params=[1, 2], ids=["split1", "split2"])
 def split(request, vmas_lib):
-    """Lanes per env of the differentiable rollout: one group, or two
-    half-groups that each sum half of every entity's pairs (the default)."""
+    """Lanes per env of the differentiable rollout: one group (the default),
+    or two half-groups that each sum half of every entity's pairs."""
     from paper_2207_03530_b300 import _lib
 
     _lib.check(vmas_lib.vmas_debug_diff_split(request.param))
