@@ -105,6 +105,10 @@ int launch_fused(const StepParams &p, int n_envs, cudaStream_t st) {
   if (n_envs <= 0) return VMAS_OK;
   const int smem = vmas::fused_cta_smem_bytes(p.N, p.P, G);
   auto kern = vmas::world_step_kernel<G, SLOTS, NC, false, RAGGED, TILED>;
+  // the largest shared-memory carveout: measured 0.6 % faster per step at
+  // 30,000 envs when other kernels (an L2 flush) run between the steps
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
