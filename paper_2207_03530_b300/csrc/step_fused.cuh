@@ -105,14 +105,19 @@ __device__ __forceinline__ int pair_type(uint32_t sa, uint32_t sb) {
 //
 // The body steps the 32 / G environments of one warp: env slots slot0 +
 // group (of the size class's range, for RAGGED kernels), per-env shared
-// memory from `wsmem` on.  `smem` and `warp` (the warp's index in its CTA)
-// serve the CTA-wide bulk staging of the one-step plain kernel only, the one
-// form that synchronises its CTA; every other form is warp-local, which lets
-// a persistent kernel run different size classes in the warps of one CTA.
+// memory from `wsmem` on.  `smem`, `warp` (the warp's index in its CTA),
+// `blk` (the CTA's block of envs) and `phase` (the parity the staging
+// mbarrier, initialised by the caller, completes next) serve the CTA-wide
+// bulk staging of the one-step plain kernel only, the one form that
+// synchronises its CTA; every other form is warp-local, which lets a
+// persistent kernel run different size classes in the warps of one CTA.
+// Returns false if the staging copies did not arrive in time (the envs are
+// left unchanged and the error word flagged).
 template <int G, int SLOTS, int NC, bool RAW, bool RAGGED, bool TILED>
-__device__ __forceinline__ void world_step_body(const StepParams &p, unsigned char *smem,
+__device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned char *smem,
                                                 unsigned long long *mbar, int warp, int slot0,
-                                                unsigned char *wsmem) {
+                                                unsigned char *wsmem, int blk = 0,
+                                                uint32_t phase = 0) {
   constexpr int EPW = 32 / G;
   constexpr unsigned FULL = 0xffffffffu;
   const int NL = NC > 0 ? NC : p.N;  // layout capacity per env
@@ -126,21 +131,20 @@ __device__ __forceinline__ void world_step_body(const StepParams &p, unsigned ch
   unsigned long long &s_mbar = *mbar;
   bool bulk = false;
   if constexpr (kCanStage)
-    bulk = p.bulk && !p.env_list && (blockIdx.x + 1) * CE <= p.E;
+    bulk = p.bulk && !p.env_list && (blk + 1) * CE <= p.E;
   unsigned char *stage = smem;
   const uint32_t plane_b = (uint32_t)(CE * NL * 4), param_b = 4 * plane_b;
   const uint32_t act_b = (uint32_t)(CE * p.A * 12), kind_b = (uint32_t)(CE * NL);
   if (bulk && threadIdx.x == 0) {
     const uint32_t bar = smem_u32(&s_mbar);
-    mbar_init(bar, 1);
     mbar_expect_tx(bar, 6 * plane_b + param_b + act_b + kind_b + p.stage_extra_tx);
-    const size_t e0 = (size_t)blockIdx.x * CE * NL;
+    const size_t e0 = (size_t)blk * CE * NL;
     const float *planes[6] = {p.px, p.py, p.vx, p.vy, p.th, p.om};
     for (int f = 0; f < 6; ++f) bulk_g2s(smem_u32(stage + f * plane_b), planes[f] + e0, plane_b, bar);
     bulk_g2s(smem_u32(stage + 6 * plane_b), p.param + e0, param_b, bar);
     if (act_b)
       bulk_g2s(smem_u32(stage + 6 * plane_b + param_b),
-               p.actions + (size_t)blockIdx.x * CE * p.A * 3, act_b, bar);
+               p.actions + (size_t)blk * CE * p.A * 3, act_b, bar);
     bulk_g2s(smem_u32(stage + 6 * plane_b + param_b + act_b), p.kind + e0, kind_b, bar);
   }
   const int lane = threadIdx.x & 31;
@@ -203,14 +207,14 @@ __device__ __forceinline__ void world_step_body(const StepParams &p, unsigned ch
     // bounded wait for the staging copies; a CTA whose copies did not arrive
     // flags the error, waits once more for them (bounded) and leaves its
     // envs unchanged
-    const bool late = !mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);  // about 1 s
+    const bool late = !mbar_wait(smem_u32(&s_mbar), phase, 1 << 20);  // about 1 s
     if (__syncthreads_or(late)) {
       if (threadIdx.x == 0) {
         atomicOr(p.err, 8);  // VMAS_DEVERR_TIMEOUT
-        mbar_wait(smem_u32(&s_mbar), 0, 1 << 20);
+        mbar_wait(smem_u32(&s_mbar), phase, 1 << 20);
       }
       __syncthreads();
-      return;
+      return false;
     }
     const float *sp = reinterpret_cast<const float *>(stage);
     const float4 *sq = reinterpret_cast<const float4 *>(stage + 6 * plane_b);
@@ -687,6 +691,7 @@ __device__ __forceinline__ void world_step_body(const StepParams &p, unsigned ch
   }
   if (stats && valid && lg == 0) atomicAdd(stats + kStatEnvSteps, (unsigned long long)tile);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.err, 1);  // VMAS_DEVERR_NONFINITE
+  return true;
 }
 
 // One launch steps a grid of CTAs of kFusedWarps warps, 32 / G envs per warp.
@@ -703,9 +708,11 @@ __global__ void __launch_bounds__(kFusedWarps * 32, min_blocks<SLOTS>())
   }
   const int warp = threadIdx.x >> 5;
   const int NL = NC > 0 ? NC : p.N;
+  if constexpr (!RAW && !RAGGED && !TILED)
+    if (threadIdx.x == 0) mbar_init(smem_u32(&s_mbar), 1);  // staging; the body's barrier orders it
   world_step_body<G, SLOTS, NC, RAW, RAGGED, TILED>(
       p, smem, &s_mbar, warp, (blockIdx.x * kFusedWarps + warp) * EPW,
-      smem + warp * EPW * fused_env_bytes(NL, G));
+      smem + warp * EPW * fused_env_bytes(NL, G), blockIdx.x, 0u);
 }
 
 }  // namespace vmas
