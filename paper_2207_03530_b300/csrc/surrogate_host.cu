@@ -155,18 +155,20 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   g.vec_b = out_bf && al16(out_bf) && ldc_b % 8 == 0;
   CUtensorMap ma, mb;
   if (!tc_map(&ma, A, M, K, lda, sur::kTcM) || !tc_map(&mb, B, N, K, ldb, g.n_pad)) return false;
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
+  // SM count and the shared-memory opt-in, once per process (thread-safe
+  // initialisation); 0 when the set-up failed (the warp-mma GEMM then runs)
+  static const int n_sm = []() {
+    int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(sur::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              sur::tc_smem_bytes(2, 128)) != cudaSuccess) {
       cudaGetLastError();
-      n_sm = 0;
-      return false;
+      return 0;
     }
-  }
+    return sms;
+  }();
+  if (!n_sm) return false;
   const int tiles = (M + sur::kTcM - 1) / sur::kTcM;
   const int grid = std::min(tiles, 2 * n_sm);
   sur::gemm_tc_kernel<<<grid, 128, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, g);

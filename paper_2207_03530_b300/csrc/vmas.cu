@@ -163,23 +163,27 @@ template <int MINB>
 int launch_ragged_persistent_b(vmas::RaggedQueueParams q, cudaStream_t st) {
   q.slab = vmas::persist_slab_bytes();
   const int smem = vmas::kFusedWarps * q.slab;
-  static int resident = 0, sms = 0;  // per process and budget: one device model
-  if (!resident) {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(vmas::ragged_persistent_kernel<MINB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    }
+  // resident CTAs per SM and SM count, found once per process (thread-safe
+  // initialisation; the process is assumed to use one GPU model)
+  struct Occ { cudaError_t err; int resident, sms; };
+  static const Occ occ = [smem]() {
+    Occ o{cudaSuccess, 1, 1};
     int dev = 0;
-    VMAS_CUDA(cudaGetDevice(&dev));
-    VMAS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    VMAS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &resident, vmas::ragged_persistent_kernel<MINB>, vmas::kFusedWarps * 32, smem));
-    if (resident < 1) resident = 1;
-  }
+    if (smem > 48 * 1024)
+      o.err = cudaFuncSetAttribute(vmas::ragged_persistent_kernel<MINB>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (o.err == cudaSuccess) o.err = cudaGetDevice(&dev);
+    if (o.err == cudaSuccess) o.err = cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (o.err == cudaSuccess)
+      o.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &o.resident, vmas::ragged_persistent_kernel<MINB>, vmas::kFusedWarps * 32, smem);
+    if (o.resident < 1) o.resident = 1;
+    return o;
+  }();
+  if (occ.err != cudaSuccess) return cuda_fail(occ.err, "ragged_persistent_kernel set-up");
   // one wave of resident CTAs, fewer when there are fewer items than warps
   const int need = (q.n_items + vmas::kFusedWarps - 1) / vmas::kFusedWarps;
-  const int grid = std::min(need, sms * resident);
+  const int grid = std::min(need, occ.sms * occ.resident);
   vmas::ragged_persistent_kernel<MINB><<<grid, vmas::kFusedWarps * 32, smem, st>>>(q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "ragged_persistent_kernel launch");
