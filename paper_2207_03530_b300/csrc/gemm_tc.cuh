@@ -54,6 +54,9 @@ struct TcGemmArgs {
   int ldc_b;
   int *err;            // device error word
   int vec_f, vec_b;    // 16-byte stores allowed (aligned bases, ldc_f % 4, ldc_b % 8)
+  // test hook: extra transaction bytes every A-tile barrier waits for, which
+  // no copy delivers, so that its bounded wait runs out (0 in normal use)
+  uint32_t extra_tx;
 };
 
 __host__ __device__ inline int tc_smem_bytes(int katoms, int n_pad) {
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(128, 1)
   int issued[2] = {0, 0}, committed[2] = {0, 0};
   auto load_a = [&](int i) {  // thread 0: tile of local index i into stage i & 1
     const int s = i & 1, row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM;
-    mbar_expect_tx(full0 + 8 * s, a_bytes);
+    mbar_expect_tx(full0 + 8 * s, a_bytes + g.extra_tx);
     for (int a = 0; a < KA; ++a)
       tma_load_2d(smem_u32(sA + (s * KA + a) * kTcAtom), &tmA, 64 * a, row, full0 + 8 * s);
     ++issued[s];

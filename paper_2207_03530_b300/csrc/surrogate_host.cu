@@ -29,6 +29,7 @@ constexpr int kOffW2T = 0, kOffW1T = 128 * 128, kOffWe2T = kOffW1T + 80 * 128,
 // 1: the warp-mma GEMM only (for A/B comparisons).  Process-wide.
 int g_gemm_engine = 0;
 std::atomic<long long> g_tc_launches{0};  // tcgen05 GEMM launches so far
+std::atomic<int> g_tc_timeout_test{0};    // vmas_debug_gemm_timeout
 
 }  // namespace
 
@@ -153,6 +154,7 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   g.err = err;
   g.vec_f = out_f32 && al16(out_f32) && ldc_f % 4 == 0;
   g.vec_b = out_bf && al16(out_bf) && ldc_b % 8 == 0;
+  g.extra_tx = g_tc_timeout_test.load() ? 16u : 0u;
   CUtensorMap ma, mb;
   if (!tc_map(&ma, A, M, K, lda, sur::kTcM) || !tc_map(&mb, B, N, K, ldb, g.n_pad)) return false;
   // SM count and the shared-memory opt-in, once per process (thread-safe
@@ -709,6 +711,11 @@ int vmas_debug_gemm_engine(int32_t engine, int64_t *tc_launches) {
     return fail(VMAS_EINVAL, "engine must be -1, 0 or 1");
   if (engine >= 0) g_gemm_engine = engine;
   if (tc_launches) *tc_launches = g_tc_launches.load();
+  return VMAS_OK;
+}
+
+int vmas_debug_gemm_timeout(int32_t on) {
+  g_tc_timeout_test = on ? 1 : 0;
   return VMAS_OK;
 }
 
