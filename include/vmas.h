@@ -330,9 +330,9 @@ int vmas_debug_stage_timeout(vmas_world *world, int32_t on);
 /* Diagnostic: the cosine and sine the step uses for a body angle, for n
  * device angles d_theta into device d_cos_sin [n][2] (cos, sin); the
  * library's own range reduction and series, absolute error about 1e-7 for
- * |theta| up to 1.6e6 rad (beyond that the error grows in proportion to
- * |theta|; past about 1e15 rad, and for inf or NaN, the result is a unit
- * vector with no relation to theta). */
+ * |theta| up to 2e6 rad (beyond that the error grows with |theta|).  For
+ * any input, huge, inf or NaN angles included, the result is a unit vector
+ * (to that accuracy); far beyond the range it bears no relation to theta. */
 int vmas_debug_body_axes(const float *d_theta, float *d_cos_sin, int32_t n, void *stream);
 
 /* ---- Allocation-free step --------------------------------------------

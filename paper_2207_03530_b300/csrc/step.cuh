@@ -55,37 +55,26 @@ __device__ __forceinline__ bool pair_active(uint32_t ki, uint32_t kj) {
 }
 
 // cos and sin of a body angle, written out (no library call): Cody-Waite
-// reduction r = th - k pi/2 with pi/2 split in three floats (1.5703125 and
-// 4.8387050628662109e-4 have 8 and 12 significant bits, so k times them is
-// exact for |k| < 2^12, i.e. |th| below about 6,400 rad), then the Taylor
-// series of sin to r^9 and cos to r^10 on |r| <= pi/4 (truncation below
-// 2e-9) and the quadrant k mod 4.  Angles beyond that range (a body spun for
-// a long rollout) take the same reduction in FP64 with pi/2 split in three
-// doubles of 33, 33 and 53 significant bits (k times the first two exact
-// for |k| < 2^20, i.e. |th| below about 1.6e6 rad; beyond, the error grows
-// in proportion to |th|; past about 1e15 rad, and for inf or NaN, the result
-// is a unit vector with no relation to th).
-// Absolute error about 1e-7.  Shared by every kernel that needs a body frame.
+// reduction r = th - k pi/2 with a fused multiply-add, then the Taylor series
+// of sin to r^9 and cos to r^10 and the quadrant k mod 4.  pi/2 is split in
+// two floats, P1 = fl(pi/2) and P2 = fl(pi/2 - P1).  The fma forms k P1
+// exactly, and th - k P1 is then a multiple of 2^-23 (of 2^-24 when
+// |th| < 1) below 2 (below 1) in magnitude, so the first step is exact
+// while k is within one of th's quadrant; the split's error, |k| * 3e-15,
+// and the second step's rounding
+// stay below 1e-8 for |th| up to about 2e6 rad.  Over that range k, rounded
+// from th * fl(2/pi), is off the nearest quadrant by at most 0.15, so
+// |r| <= 0.97, where the series truncate below 2e-8.  Absolute error about
+// 1e-7 up to 2e6 rad; beyond it grows with |th|.  r is clamped to [-1, 1],
+// so for any input (huge, inf or NaN angles included) the result stays a
+// unit vector to that accuracy.  Shared by every kernel that needs a body
+// frame.
 __device__ __forceinline__ void body_axes(float th, float &c, float &s) {
-  float k = rintf(th * 0.63661977236758134f);  // 2 / pi
-  float r;
-  int q;
-  if (fabsf(k) < 4096.f) {
-    r = fmaf(-k, 1.5703125f, th);
-    r = fmaf(-k, 4.8387050628662109e-4f, r);
-    r = fmaf(-k, -4.3711388286737929e-8f, r);
-    q = ((int)k) & 3;
-  } else {
-    const double t = (double)th;
-    const double kd = rint(t * 0.63661977236758134308);
-    double rd = fma(-kd, 0x1.921fb544p+0, t);
-    rd = fma(-kd, 0x1.0b4611a6p-34, rd);
-    rd = fma(-kd, 0x1.3198a2e037073p-69, rd);
-    // beyond about 1e15 rad (and for inf or NaN) the reduction has lost
-    // every digit: take r = 0, so the result stays a unit vector
-    r = fabs(rd) <= 0.8 ? (float)rd : 0.f;
-    q = __double2int_rz(kd - 4.0 * floor(kd * 0.25)) & 3;  // k mod 4; NaN gives 0
-  }
+  const float k = rintf(th * 0.63661977236758134f);  // 2 / pi
+  float r = fmaf(-k, 1.57079637050628662109375f, th);   // P1 = 0x1.921fb6p+0
+  r = fmaf(-k, -4.37113882867379300296306610107421875e-8f, r);  // P2 = -0x1.777a5cp-25
+  r = fminf(fmaxf(r, -1.f), 1.f);  // NaN becomes -1
+  const int q = __float2int_rz(k) & 3;  // saturating conversion: defined for every k
   const float z = r * r;
   const float ps = fmaf(fmaf(fmaf(2.7557319223985891e-6f, z, -1.9841269841269841e-4f), z,
                              8.3333333333333333e-3f), z, -1.6666666666666667e-1f);

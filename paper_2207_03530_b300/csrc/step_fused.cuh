@@ -408,6 +408,49 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
       constexpr int D = NC > 0 ? NC / 2 : (G * SLOTS) / 2;  // at most 64
       constexpr bool kOneMask = SLOTS * D <= 64;
       constexpr bool kMask = kOneMask || RAGGED;
+      // Kernels compiled for a fixed count, where the record area holds the
+      // per-lane lists and NC boxes side by side, test axis-aligned bounding
+      // boxes instead of circles.  A fixed wall's bounding circle covers most
+      // of the world, so with circles nearly every (body, wall) pair reached
+      // the bit walk, where only the exact carrier test removed it; a box is
+      // tight around a body that cannot turn.  Each entity publishes {x, y,
+      // half width, half height}: a rotatable body the square around its
+      // bounding circle (any angle it takes before the next build fits), a
+      // body that cannot turn its own box from its frame, each grown by the
+      // rounding allowance of the circle test; the half height is negative
+      // for a body that neither moves nor turns (two such bodies never
+      // interact) and the half width -1e30 for a body that does not collide.
+      // A pair is kept when the boxes grown by the skin overlap: that holds
+      // for every pair that can touch before the next build, so the list
+      // keeps every pair the circles kept that can touch, in the same order,
+      // and the contacts and results are bitwise the same.
+      constexpr int kLcBytes = (2 * G * kLaneCand + 15) & ~15;  // the per-lane lists
+      constexpr bool kAabb = NC > 0 && kOneMask && kLcBytes + 16 * NC <= kRecCap * 20;
+      float4 *s_ab = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) + kLcBytes);
+      if constexpr (kAabb) {
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int a = lg + G * s;
+          if (valid && a < N) {
+            const uint32_t ka = kd[s];
+            float4 ab = make_float4(x[s], y[s], -1e30f, 0.f);
+            if (ka & kCollidable) {
+              const float rb = s_mi[VIDX(a, N, 29)].z;
+              const float eps = 1e-5f * (rb + fabsf(x[s]) + fabsf(y[s]));
+              float hx = rb, hy = rb;
+              if (!(ka & kRotatable) && (ka & 3u) != kSphere) {
+                const float4 g = s_ng[VIDX(a, N, 30)];  // {cos, sin, ha, hb}
+                hx = g.z * fabsf(g.x) + g.w * fabsf(g.y);
+                hy = g.z * fabsf(g.y) + g.w * fabsf(g.x);
+              }
+              ab.z = hx + eps;
+              ab.w = (ka & (kMovable | kRotatable)) ? hy + eps : -(hy + eps);
+            }
+            s_ab[VIDX(a, N, 31)] = ab;
+          }
+        }
+        __syncwarp();
+      }
       if (kMask && valid) {
         const int dmax = (N - 1) / 2;
         auto pass1 = [&](int s) {
@@ -430,7 +473,20 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
             return (kb & kCollidable) && (a_moves || (kb & (kMovable | kRotatable))) &&
                    !(dx * dx + dy * dy > lim * lim);
           };
-          if constexpr (NC > 0) {
+          if constexpr (kAabb) {
+            const float4 aa = s_ab[VIDX(a, N, 32)];
+            const float hxa = aa.z + p.skin, hya = fabsf(aa.w) + p.skin;
+            const bool fixed_a = aa.w < 0.f;
+            auto boxes = [&](int d) {
+              const int b = a + d >= N ? a + d - N : a + d;
+              const float4 bb = s_ab[VIDX(b, N, 33)];
+              return (fabsf(aa.x - bb.x) <= hxa + bb.z) & (fabsf(aa.y - bb.y) <= hya + fabsf(bb.w)) &
+                     !(fixed_a & (bb.w < 0.f));
+            };
+#pragma unroll
+            for (int d = 1; d <= D; ++d)
+              m |= (unsigned long long)(d <= dlast && boxes(d)) << (d - 1);
+          } else if constexpr (NC > 0) {
 #pragma unroll
             for (int d = 1; d <= D; ++d)
               m |= (unsigned long long)(d <= dlast && circle(d)) << (d - 1);

@@ -307,9 +307,10 @@ def test_body_axes_accuracy(vmas_lib):
 
     rng = np.random.default_rng(0)
     th = np.concatenate([rng.uniform(-7, 7, 50000), rng.uniform(-2000, 2000, 50000),
-                         rng.uniform(-1.6e6, 1.6e6, 50000),
+                         rng.uniform(-2e6, 2e6, 50000),
                          np.array([0, 1e-30, np.pi / 4, -np.pi / 4, np.pi / 2, np.pi, 4000.0,
-                                   6433.0, 6434.0, 6435.0, -6435.0, 1e4, -1e5, 1e6, 1.6e6])])
+                                   6433.0, 6434.0, 6435.0, -6435.0, 1e4, -1e5, 1e6, 1.6e6,
+                                   -2e6, 2e6])])
     th = th.astype(np.float32)
     d_th = torch.from_numpy(th).cuda()
     out = torch.empty((len(th), 2), device="cuda")
@@ -320,7 +321,7 @@ def test_body_axes_accuracy(vmas_lib):
     err = max(np.abs(cs[:, 0] - np.cos(t64)).max(), np.abs(cs[:, 1] - np.sin(t64)).max())
     assert err <= 1.5e-7, err
     # beyond the stated range the result stays a defined, bounded value
-    far = np.array([3e6, -1e9, 3.4e38, -3.4e38, np.inf, np.nan], np.float32)
+    far = np.array([3e6, -1e9, 1e15, 3.4e38, -3.4e38, np.inf, -np.inf, np.nan], np.float32)
     d_far = torch.from_numpy(far).cuda()
     out = torch.empty((len(far), 2), device="cuda")
     _lib.check(vmas_lib.vmas_debug_body_axes(d_far.data_ptr(), out.data_ptr(), len(far),
