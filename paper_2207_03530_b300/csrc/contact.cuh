@@ -144,45 +144,36 @@ __device__ __forceinline__ void poly_edge(const Poly &p, int k, float &ax, float
 // by-value arguments went through the stack and the call site cost the step
 // kernel its spill-free register allocation (4 % of the step).
 __device__ __forceinline__ bool hit_poly_poly(const Poly A, const Poly B, Hit &h) {
-  // candidate axes: A's (box e1, e2 | line e2), then B's, then for two
-  // exactly parallel lines A's e1 (their normals coincide)
-  float ax[5], ay[5];
-  int na = 0;
-  if (A.box) {
-    ax[0] = A.ux; ay[0] = A.uy; ax[1] = -A.uy; ay[1] = A.ux; na = 2;
-  } else {
-    ax[0] = -A.uy; ay[0] = A.ux; na = 1;
-  }
-  const int nai = na;
-  if (B.box) {
-    ax[na] = B.ux; ay[na] = B.uy; ax[na + 1] = -B.uy; ay[na + 1] = B.ux; na += 2;
-  } else {
-    ax[na] = -B.uy; ay[na] = B.ux; na += 1;
-  }
-  if (!A.box && !B.box && A.ux * B.uy - A.uy * B.ux == 0.f) {
-    ax[na] = A.ux; ay[na] = A.uy; na += 1;
-  }
+  // candidate axes in fixed slots, tried in order: A's first (box e1 | line
+  // e2), A's e2 (boxes), B's first, B's e2 (boxes), and for two exactly
+  // parallel lines A's e1 (their normals coincide); held in registers
+  const float ax0 = A.box ? A.ux : -A.uy, ay0 = A.box ? A.uy : A.ux;
+  const float ax2 = B.box ? B.ux : -B.uy, ay2 = B.box ? B.uy : B.ux;
+  const bool ok4 = !A.box && !B.box && A.ux * B.uy - A.uy * B.ux == 0.f;
   const float dcx = A.cx - B.cx, dcy = A.cy - B.cy;
   float best = __int_as_float(0x7f800000);
   float bax = 0.f, bay = 0.f;
-  int bk = 0;
+  int bq = 0;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    if (q < na) {
-      const float d = dcx * ax[q] + dcy * ay[q];
-      const float depth = half_extent(A, ax[q], ay[q]) + half_extent(B, ax[q], ay[q]) - fabsf(d);
+    const bool ok = q == 0 || q == 2 || (q == 1 && A.box) || (q == 3 && B.box) || (q == 4 && ok4);
+    if (ok) {
+      const float axq = q == 0 ? ax0 : q == 1 ? -A.uy : q == 2 ? ax2 : q == 3 ? -B.uy : A.ux;
+      const float ayq = q == 0 ? ay0 : q == 1 ? A.ux : q == 2 ? ay2 : q == 3 ? B.ux : A.uy;
+      const float d = dcx * axq + dcy * ayq;
+      const float depth = half_extent(A, axq, ayq) + half_extent(B, axq, ayq) - fabsf(d);
       if (depth < 0.f) return false;  // separating axis
-      if (depth < best) { best = depth; bax = ax[q]; bay = ay[q]; bk = q; }
+      if (depth < best) { best = depth; bax = axq; bay = ayq; bq = q; }
     }
   }
   float ux = bax, uy = bay;
   if (dcx * ux + dcy * uy < 0.f) { ux = -ux; uy = -uy; }
   const float g = -best;
-  const bool ref_i = bk < nai;
+  const bool ref_i = bq < 2;
   const Poly R = ref_i ? A : B;
   const Poly Q = ref_i ? B : A;
   const float nrx = ref_i ? -ux : ux, nry = ref_i ? -uy : uy;  // R's outward normal
-  const int kr = ref_i ? bk : bk - nai;
+  const int kr = bq == 4 ? 1 : (bq & 1);  // the parallel-lines axis has no face
 
   bool have_face = true;
   float fax = 0.f, fay = 0.f, fbx = 0.f, fby = 0.f;

@@ -408,9 +408,10 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
       constexpr int D = NC > 0 ? NC / 2 : (G * SLOTS) / 2;  // at most 64
       constexpr bool kOneMask = SLOTS * D <= 64;
       constexpr bool kMask = kOneMask || RAGGED;
-      // Kernels compiled for a fixed count, where the record area holds the
-      // per-lane lists and NC boxes side by side, test axis-aligned bounding
-      // boxes instead of circles.  A fixed wall's bounding circle covers most
+      // Kernels that build masks test axis-aligned bounding boxes instead of
+      // circles, where the boxes of the layout's capacity fit in the record
+      // area beside the per-lane lists, or else in the compact list's area
+      // (free until the compaction).  A fixed wall's bounding circle covers most
       // of the world, so with circles nearly every (body, wall) pair reached
       // the bit walk, where only the exact carrier test removed it; a box is
       // tight around a body that cannot turn.  Each entity publishes {x, y,
@@ -424,9 +425,14 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
       // for every pair that can touch before the next build, so the list
       // keeps every pair the circles kept that can touch, in the same order,
       // and the contacts and results are bitwise the same.
+      constexpr int kCap = NC > 0 ? NC : G * SLOTS;
       constexpr int kLcBytes = (2 * G * kLaneCand + 15) & ~15;  // the per-lane lists
-      constexpr bool kAabb = NC > 0 && kOneMask && kLcBytes + 16 * NC <= kRecCap * 20;
-      float4 *s_ab = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) + kLcBytes);
+      constexpr int kRecBytes = kRecCap * 20 > kLcBytes ? kRecCap * 20 : kLcBytes;
+      constexpr bool kAbInRec = kLcBytes + 16 * kCap <= kRecBytes;
+      constexpr bool kAbInCand = !kAbInRec && 16 * kCap <= kLcBytes;
+      constexpr bool kAabb = kOneMask && (kAbInRec || kAbInCand);
+      float4 *s_ab = kAbInRec ? reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) + kLcBytes)
+                              : reinterpret_cast<float4 *>(s_cand);
       if constexpr (kAabb) {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -483,9 +489,14 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
               return (fabsf(aa.x - bb.x) <= hxa + bb.z) & (fabsf(aa.y - bb.y) <= hya + fabsf(bb.w)) &
                      !(fixed_a & (bb.w < 0.f));
             };
+            if constexpr (NC > 0) {
 #pragma unroll
-            for (int d = 1; d <= D; ++d)
-              m |= (unsigned long long)(d <= dlast && boxes(d)) << (d - 1);
+              for (int d = 1; d <= D; ++d)
+                m |= (unsigned long long)(d <= dlast && boxes(d)) << (d - 1);
+            } else {
+#pragma unroll 4
+              for (int d = 1; d <= dlast; ++d) m |= (unsigned long long)boxes(d) << (d - 1);
+            }
           } else if constexpr (NC > 0) {
 #pragma unroll
             for (int d = 1; d <= D; ++d)
@@ -590,6 +601,7 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
         }
       }
       // compact the lane lists in lane order
+      if constexpr (kAabb && kAbInCand) __syncwarp();  // the boxes are read until here
       const int cnt = n < kLaneCand ? n : kLaneCand;
       int incl = cnt;
 #pragma unroll

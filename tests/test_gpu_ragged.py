@@ -233,9 +233,17 @@ PERSIST_LANES = [8, 8, 16, 32, 32]  # the persistent schedule's fixed lanes per 
 def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed, schedule):
     """Every size class in one persistent launch (warps take one warp's worth
     of envs at a time from an atomic work queue, largest class first):
-    against the FP64 oracle, and bitwise equal to the per-class launches
-    with the same lanes per class, stepped one at a time and in tiled,
-    graph-captured rollouts (replayed twice)."""
+    against the FP64 oracle, and equal to the per-class launches with the
+    same lanes per class, stepped one at a time and in tiled, graph-captured
+    rollouts (replayed twice).
+
+    The two schedules run the same step body compiled into different
+    kernels, and the compiler may fuse a multiply and an add into one fma in
+    one kernel and not the other, so they agree to rounding, not always
+    bitwise (one env of 300 differed by 3e-8 after 14 steps; built without
+    automatic fma contraction, every env agreed bitwise).  An env the queue
+    skipped or stepped twice would be off by a whole step's motion, about
+    1e-3, so the 1e-6 bound still checks the queue."""
     sc, counts = scenes.ragged_scene(300, seed)
     act = scenes.make_actions(sc, 8, seed)
     per, pers = _ragged(sc, counts), _ragged(sc, counts)
@@ -248,7 +256,7 @@ def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed, s
         per.step(pact[t])
         pers.step(pact[t])
     a, b = per.state().cpu().numpy(), pers.state().cpu().numpy()
-    assert np.array_equal(a, b)
+    assert np.abs(a - b).max() <= 1e-6
     got, sel = _unpack_state(b, counts, sc.n_entities)
     ref = orc.step(sc, sc.init_state, act[:2], threads=8)
     assert normwise_err(got[sel], ref[sel]).max() <= TOL
@@ -256,7 +264,7 @@ def test_persistent_schedule_matches_oracle_and_per_class(vmas_lib, orc, seed, s
         rw.set_tuning(None if rw is pers else PERSIST_LANES, 3)
         rw.rollout(pact[2:])
         rw.rollout(pact[2:])  # replay of the captured graph
-    assert np.array_equal(per.state().cpu().numpy(), pers.state().cpu().numpy())
+    assert np.abs(per.state().cpu().numpy() - pers.state().cpu().numpy()).max() <= 1e-6
     for rw in (per, pers):
         rw.check()
         rw.close()
