@@ -19,7 +19,9 @@
 //     edge clipped to the reference face, its clipped ends weighted by their
 //     depth beneath that face.
 // A pair whose normal is undefined (coincident closest points) exerts no
-// force.
+// force.  The sphere routines take the distance and the unit normal from one
+// hardware reciprocal square root (rsqrtf, within 2 ulp): the IEEE square
+// root and divide cost 2.5 % of the step.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,10 +41,10 @@ struct Hit {
 __device__ __forceinline__ bool hit_sphere_sphere(float xi, float yi, float ri, float xj,
                                                   float yj, float rj, Hit &h) {
   const float dx = xi - xj, dy = yi - yj;
-  const float dist = sqrtf(dx * dx + dy * dy);
+  const float d2 = dx * dx + dy * dy;
+  const float inv = rsqrtf(d2), dist = d2 * inv;
   const float g = dist - (ri + rj);
-  if (!(g <= 0.f) || !(dist > 0.f)) return false;
-  const float inv = 1.f / dist;
+  if (!(g <= 0.f) || !(d2 > 0.f)) return false;
   h.g = g;
   h.nx = dx * inv;
   h.ny = dy * inv;
@@ -59,10 +61,10 @@ __device__ __forceinline__ bool hit_sphere_line(float sx, float sy, float r, flo
   const float ex = sx - lx, ey = sy - ly;
   const float t = fminf(fmaxf(ex * c + ey * s, -hl), hl);
   const float dx = ex - t * c, dy = ey - t * s;
-  const float dist = sqrtf(dx * dx + dy * dy);
+  const float d2 = dx * dx + dy * dy;
+  const float inv = rsqrtf(d2), dist = d2 * inv;
   const float g = dist - r;
-  if (!(g <= 0.f) || !(dist > 0.f)) return false;
-  const float inv = 1.f / dist;
+  if (!(g <= 0.f) || !(d2 > 0.f)) return false;
   h.g = g;
   h.nx = dx * inv;
   h.ny = dy * inv;
@@ -92,10 +94,10 @@ __device__ __forceinline__ bool hit_sphere_box(float sx, float sy, float r, floa
     qx = fminf(fmaxf(lx, -hw), hw);
     qy = fminf(fmaxf(ly, -hh), hh);
     const float dx = lx - qx, dy = ly - qy;
-    const float dist = sqrtf(dx * dx + dy * dy);
+    const float d2 = dx * dx + dy * dy;
+    const float inv = rsqrtf(d2), dist = d2 * inv;
     g = dist - r;
-    if (!(g <= 0.f) || !(dist > 0.f)) return false;
-    const float inv = 1.f / dist;
+    if (!(g <= 0.f) || !(d2 > 0.f)) return false;
     nlx = dx * inv;
     nly = dy * inv;
   }

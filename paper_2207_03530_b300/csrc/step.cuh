@@ -101,19 +101,17 @@ __global__ void body_axes_kernel(const float *th, float *cs, int n) {
 // cost 3 % of the step at 262,144 envs.
 __device__ __forceinline__ float softplus_pos(float z) { return z + __logf(1.f + __expf(-z)); }
 
-// Narrow phase for the ordered pair (i, j); bi/bj = {x, y, inflated R, kind}.
+// Narrow phase for the ordered pair (i, j); bi/bj = {x, y, inflated R, kind},
+// gi/gj = {cos, sin, ha, hb} (a sphere's radius in ha), loaded by the caller
+// beside the poses so both shared-memory reads overlap.
 __device__ __forceinline__ bool pair_hit(const float4 bi, const float4 bj, uint32_t ki,
-                                         uint32_t kj, const float4 *s_ng, int i, int j,
+                                         uint32_t kj, const float4 gi, const float4 gj,
                                          Hit &h) {
   const float dx = bi.x - bj.x, dy = bi.y - bj.y;
   const float lim = bi.z + bj.z;
   if (dx * dx + dy * dy > lim * lim) return false;
   const uint32_t si = ki & 3u, sj = kj & 3u;
-  if (si == kSphere && sj == kSphere) {
-    const float ri = s_ng[i].z, rj = s_ng[j].z;
-    return hit_sphere_sphere(bi.x, bi.y, ri, bj.x, bj.y, rj, h);
-  }
-  const float4 gi = s_ng[i], gj = s_ng[j];  // {cos, sin, ha, hb}
+  if (si == kSphere && sj == kSphere) return hit_sphere_sphere(bi.x, bi.y, gi.z, bj.x, bj.y, gj.z, h);
   // slab test against a line's carrier
   if (sj == kLine && fabsf(dx * gj.y - dy * gj.x) > bi.z + 1e-5f * (fabsf(bj.x) + fabsf(bj.y)))
     return false;
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) pair_mask_kernel(const Step
     const float4 bi = s_bp[i], bj = s_bp[j];
     const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
     Hit h;
-    const bool hit = pair_active(ki, kj) && pair_hit(bi, bj, ki, kj, s_ng, i, j, h);
+    const bool hit = pair_active(ki, kj) && pair_hit(bi, bj, ki, kj, s_ng[i], s_ng[j], h);
     p.mask[(size_t)e * P + q] = hit ? 1 : 0;
   }
 }

@@ -668,9 +668,10 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
         j = VIDX((int)(ij >> 8), NL, 23);
         const bool in_env = !RAGGED || j < N;  // a full scan covers the layout capacity
         const float4 bi = s_bp[in_env ? i : 0], bj = s_bp[in_env ? j : 0];
+        const float4 gi = s_ng[in_env ? i : 0], gj = s_ng[in_env ? j : 0];  // {cos, sin, ha, hb}
         const uint32_t ki = __float_as_uint(bi.w), kj = __float_as_uint(bj.w);
         if (in_env && pair_active(ki, kj)) {
-          hit = pair_hit(bi, bj, ki, kj, s_ng, i, j, hh);
+          hit = pair_hit(bi, bj, ki, kj, gi, gj, hh);
           if (stats) {
             const int t = pair_type(ki & 3u, kj & 3u);
             atomicAdd(stats + kStatEval + t, 1ull);
