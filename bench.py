@@ -1080,42 +1080,60 @@ def run_small(args):
 
 
 def run_lidar(args):
-    """LIDAR on the paper-scale scene: 20 agents x 32 rays per env."""
+    """LIDAR on the paper-scale scene: 20 agents x 32 rays per env, with the
+    culled kernel (the default) and, for comparison, every ray against every
+    body."""
     import torch
 
-    from paper_2207_03530_b300 import World, build, scenes
+    from paper_2207_03530_b300 import World, _lib, build, scenes
 
     build.build()
     torch.cuda.set_device(0)
+    L = _lib.load()
     sc = scenes.paper_scene(args.envs, args.seed)
     w = World(sc)
-    for _ in range(max(3, args.warmup)):
-        w.lidar(32, 1.0)
-    torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cs = ClockSampler(torch.device("cuda", 0))
-    with cs:
-        a.record()
-        for _ in range(args.steps):
-            w.lidar(32, 1.0)
-        b.record()
-        torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
+
+    def timed(cull):
+        _lib.check(L.vmas_debug_lidar_cull(1 if cull else 0))
+        try:
+            for _ in range(max(3, args.warmup)):
+                w.lidar(32, 1.0)
+            torch.cuda.synchronize()
+            with cs:
+                a.record()
+                for _ in range(args.steps):
+                    w.lidar(32, 1.0)
+                b.record()
+                torch.cuda.synchronize()
+        finally:
+            _lib.check(L.vmas_debug_lidar_cull(1))
+        return a.elapsed_time(b) / args.steps
+
+    ms_full = timed(False)
+    ms = timed(True)
     rays = args.envs * sc.n_actuated * 32
     w.close()
-    # bodies each ray is tested against: every other collidable entity (the
-    # casters are spheres)
+    # every-ray kernel: bodies each ray is tested against (every other
+    # collidable entity; the casters are spheres or boxes)
     coll = (np.asarray(sc.flags[0]) & scenes.COLLIDABLE) != 0
     shape = np.asarray(sc.shape[0])
     ops = (LIDAR_OPS["ray"] + LIDAR_OPS["sphere"] * (int((coll & (shape == 0)).sum()) - 1)
            + LIDAR_OPS["box"] * int((coll & (shape == 1)).sum())
            + LIDAR_OPS["line"] * int((coll & (shape == 2)).sum()))
-    value = rays / (ms / 1e3)
+    value, full_value = rays / (ms / 1e3), rays / (ms_full / 1e3)
+    # algorithmic bytes per ray: its reading, and its share of the env's
+    # inputs (x, y, angle, packed parameters, kind byte of every entity)
+    b_ray = 4.0 + sc.n_entities * (3 * 4 + 16 + 1) / (sc.n_actuated * 32)
     print(json.dumps({"form": "lidar", "metric": "rays/s", "value": value,
                       "unit": "rays/s", "ms_per_call": ms, "env_scans_per_s": args.envs / (ms / 1e3),
-                      "roofline": _alu_roofline(ops, value, "instruction-issue-bound: 88 % of "
-                                                "issue slots, ALU pipe 68 %, 32 warp "
-                                                "instructions per ray (ncu: lidar_kernel)"),
+                      "roofline": _hbm_roofline(b_ray, value, "culled kernel; instruction-issue-"
+                                                "bound, not HBM-bound (ncu: lidar_cull_kernel)"),
+                      "every_ray": {"value": full_value, "ms_per_call": ms_full,
+                                    "roofline": _alu_roofline(ops, full_value,
+                                                              "instruction-issue-bound (ncu: "
+                                                              "lidar_kernel)")},
                       "clocks": cs.summary(), "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "%d envs x 20 agents x 32 rays vs 24 bodies"
                                              % args.envs}}), flush=True)

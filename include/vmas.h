@@ -289,6 +289,14 @@ int vmas_ragged_get_schedule(const vmas_ragged *world, int32_t *schedule);
  * kernel on `stream`. */
 int vmas_lidar(vmas_world *world, int32_t n_rays, float max_range, float *d_out, void *stream);
 
+/* Diagnostic: which LIDAR kernel vmas_lidar runs (process-wide).  on != 0
+ * (the default): the culled kernel, where n_actuated x n_rays <= 3072 --
+ * each (body, caster) pair tests only the rays within the body's angular arc
+ * (bounding circle or segment endpoints, one ray of slack each side), with
+ * the same per-ray routines, so the readings are the same minima.  on == 0:
+ * every ray against every body.  Always VMAS_OK. */
+int vmas_debug_lidar_cull(int32_t on);
+
 /* ---- Differentiable rollout (sphere worlds) -----------------------------
  * Loss per env = sum over its actuated entities k of |x_k(T) - goal_k|^2
  * after n_steps world steps from the world's current state (which is left

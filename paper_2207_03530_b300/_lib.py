@@ -34,7 +34,7 @@ SYMBOLS = (
     "vmas_sur_get_params", "vmas_sur_set_mode", "vmas_sur_forward", "vmas_sur_loss_grad", "vmas_sur_adam",
     "vmas_sur_train_grad", "vmas_sur_train_step", "vmas_sur_step", "vmas_sur_debug_features", "vmas_debug_gemm_bf16",
     "vmas_sur_check", "vmas_debug_gemm_engine", "vmas_debug_diff_split",
-    "vmas_debug_gemm_timeout",
+    "vmas_debug_gemm_timeout", "vmas_debug_lidar_cull",
 )
 STATS_COUNT = 16
 STATS_NAMES = ("env_steps", "rebuilds", "candidates",
@@ -161,6 +161,7 @@ def load():
         "vmas_debug_gemm_engine": ([i32, vp], ctypes.c_int),
         "vmas_debug_diff_split": ([i32], ctypes.c_int),
         "vmas_debug_gemm_timeout": ([i32], ctypes.c_int),
+        "vmas_debug_lidar_cull": ([i32], ctypes.c_int),
         "vmas_debug_gemm_bf16": ([i32, i32, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp,
                                   i32, vp], ctypes.c_int),
     }

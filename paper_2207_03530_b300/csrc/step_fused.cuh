@@ -409,30 +409,36 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
       constexpr bool kOneMask = SLOTS * D <= 64;
       constexpr bool kMask = kOneMask || RAGGED;
       // Kernels that build masks test axis-aligned bounding boxes instead of
-      // circles, where the boxes of the layout's capacity fit in the record
-      // area beside the per-lane lists, or else in the compact list's area
-      // (free until the compaction).  A fixed wall's bounding circle covers most
-      // of the world, so with circles nearly every (body, wall) pair reached
-      // the bit walk, where only the exact carrier test removed it; a box is
-      // tight around a body that cannot turn.  Each entity publishes {x, y,
-      // half width, half height}: a rotatable body the square around its
-      // bounding circle (any angle it takes before the next build fits), a
-      // body that cannot turn its own box from its frame, each grown by the
-      // rounding allowance of the circle test; the half height is negative
-      // for a body that neither moves nor turns (two such bodies never
-      // interact) and the half width -1e30 for a body that does not collide.
-      // A pair is kept when the boxes grown by the skin overlap: that holds
-      // for every pair that can touch before the next build, so the list
-      // keeps every pair the circles kept that can touch, in the same order,
-      // and the contacts and results are bitwise the same.
+      // circles.  A fixed wall's bounding circle covers most of the world, so
+      // with circles nearly every (body, wall) pair reached the bit walk,
+      // where only the exact carrier test removed it; a box is tight around
+      // a body that cannot turn.  Each entity publishes {x, y, half width,
+      // half height}: a rotatable body the square around its bounding circle
+      // (any angle it takes before the next build fits), a body that cannot
+      // turn its own box from its frame, each grown by the rounding allowance
+      // of the circle test; the half height is negative for a body that
+      // neither moves nor turns (two such bodies never interact) and the half
+      // width -1e30 for a body that does not collide.  A pair is kept when
+      // the boxes grown by the skin overlap: that holds for every pair that
+      // can touch before the next build, so the list keeps every pair the
+      // circles kept that can touch, in the same order, and the contacts and
+      // results are bitwise the same.  A kernel compiled for a fixed count
+      // keeps the boxes in the record area beside the lane lists and wraps
+      // partner a + d modulo N (the compiler resolves the wrap for a known
+      // N); one with a runtime count writes them twice, at a and at a + N,
+      // so the partner needs no wrap (4 % on the ragged rollout, 1 % slower
+      // for the fixed count), filling the record and compact-list areas,
+      // which the lane lists and the compaction only write after every mask
+      // is built.
       constexpr int kCap = NC > 0 ? NC : G * SLOTS;
-      constexpr int kLcBytes = (2 * G * kLaneCand + 15) & ~15;  // the per-lane lists
+      constexpr int kLcBytes = (2 * G * kLaneCand + 15) & ~15;  // lane lists; compact list
       constexpr int kRecBytes = kRecCap * 20 > kLcBytes ? kRecCap * 20 : kLcBytes;
-      constexpr bool kAbInRec = kLcBytes + 16 * kCap <= kRecBytes;
-      constexpr bool kAbInCand = !kAbInRec && 16 * kCap <= kLcBytes;
-      constexpr bool kAabb = kOneMask && (kAbInRec || kAbInCand);
-      float4 *s_ab = kAbInRec ? reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) + kLcBytes)
-                              : reinterpret_cast<float4 *>(s_cand);
+      constexpr bool kTwice = NC == 0;
+      constexpr bool kAabb = kOneMask && (kTwice ? 32 * kCap <= kRecBytes + kLcBytes
+                                                 : kLcBytes + 16 * kCap <= kRecBytes);
+      float4 *s_ab = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) +
+                                                (kTwice ? 0 : kLcBytes));  // [N] or [2 N]
+      [[maybe_unused]] const int NB = kTwice ? 2 * N : N;  // bound of the checked build
       if constexpr (kAabb) {
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
@@ -452,12 +458,13 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
               ab.z = hx + eps;
               ab.w = (ka & (kMovable | kRotatable)) ? hy + eps : -(hy + eps);
             }
-            s_ab[VIDX(a, N, 31)] = ab;
+            s_ab[VIDX(a, NB, 31)] = ab;
+            if constexpr (kTwice) s_ab[VIDX(a + N, NB, 34)] = ab;
           }
         }
         __syncwarp();
       }
-      if (kMask && valid) {
+      if constexpr (kMask) {
         const int dmax = (N - 1) / 2;
         auto pass1 = [&](int s) {
           unsigned long long m = 0ull;
@@ -480,12 +487,12 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
                    !(dx * dx + dy * dy > lim * lim);
           };
           if constexpr (kAabb) {
-            const float4 aa = s_ab[VIDX(a, N, 32)];
+            const float4 aa = s_ab[VIDX(a, NB, 32)];
             const float hxa = aa.z + p.skin, hya = fabsf(aa.w) + p.skin;
             const bool fixed_a = aa.w < 0.f;
             auto boxes = [&](int d) {
-              const int b = a + d >= N ? a + d - N : a + d;
-              const float4 bb = s_ab[VIDX(b, N, 33)];
+              const int b = kTwice || a + d < N ? a + d : a + d - N;  // (a + d) mod N
+              const float4 bb = s_ab[VIDX(b, NB, 33)];
               return (fabsf(aa.x - bb.x) <= hxa + bb.z) & (fabsf(aa.y - bb.y) <= hya + fabsf(bb.w)) &
                      !(fixed_a & (bb.w < 0.f));
             };
@@ -543,10 +550,13 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
         };
         if constexpr (kOneMask) {
           unsigned long long m = 0ull;
+          if (valid) {
 #pragma unroll
-          for (int s = 0; s < SLOTS; ++s) m |= pass1(s) << (s * D);
-          walk(m, 0);
-        } else {
+            for (int s = 0; s < SLOTS; ++s) m |= pass1(s) << (s * D);
+          }
+          if constexpr (kAabb && kTwice) __syncwarp();  // every box read: lane lists may overwrite them
+          if (valid) walk(m, 0);
+        } else if (valid) {
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) walk(pass1(s), s);
         }
@@ -601,7 +611,6 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
         }
       }
       // compact the lane lists in lane order
-      if constexpr (kAabb && kAbInCand) __syncwarp();  // the boxes are read until here
       const int cnt = n < kLaneCand ? n : kLaneCand;
       int incl = cnt;
 #pragma unroll

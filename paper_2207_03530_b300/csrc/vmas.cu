@@ -1006,6 +1006,9 @@ int vmas_debug_diff_split(int32_t split) {
   return VMAS_OK;
 }
 
+// culled LIDAR kernel unless a comparison switched it off
+static bool g_lidar_cull = true;
+
 int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, void *stream) {
   if (!w) return fail(VMAS_EINVAL, "world is NULL");
   if (n_rays < 1 || !(max_range >= 0) || !std::isfinite(max_range))
@@ -1025,9 +1028,19 @@ int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, voi
   p.param = w->param;
   p.kind = w->kind;
   p.out = d_out;
-  const size_t smem = (size_t)vmas::lidar_smem_bytes(w->N);
-  vmas::lidar_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
+  if (g_lidar_cull && (int64_t)w->A * n_rays <= vmas::kLidarCullMaxRays) {
+    const size_t smem = (size_t)vmas::lidar_cull_smem_bytes(w->N, w->A, n_rays);
+    vmas::lidar_cull_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
+  } else {
+    const size_t smem = (size_t)vmas::lidar_smem_bytes(w->N);
+    vmas::lidar_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
+  }
   VMAS_CUDA(cudaGetLastError());
+  return VMAS_OK;
+}
+
+int vmas_debug_lidar_cull(int32_t on) {
+  g_lidar_cull = on != 0;
   return VMAS_OK;
 }
 

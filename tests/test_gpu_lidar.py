@@ -97,3 +97,56 @@ def test_lidar_rays_parallel_to_box_faces_and_walls(vmas_lib, orc):
     assert np.abs(got - ref).max() <= 2e-5
     assert abs(got[0, 0, 0] - 0.4) <= 1e-6 and abs(ref[0, 0, 0] - 0.4) <= 1e-6
     assert got[0, 1, 0] == 2.0 and ref[0, 1, 0] == 2.0
+
+
+def _both_kernels(sc, n_rays, rng_max, state=None):
+    """The culled kernel (default) and every ray against every body."""
+    from paper_2207_03530_b300 import World, _lib
+
+    L = _lib.load()
+    w = World(sc)
+    if state is not None:
+        w.set_state(torch.from_numpy(state).cuda())
+    culled = w.lidar(n_rays, rng_max).cpu().numpy()
+    _lib.check(L.vmas_debug_lidar_cull(0))
+    try:
+        full = w.lidar(n_rays, rng_max).cpu().numpy()
+    finally:
+        _lib.check(L.vmas_debug_lidar_cull(1))
+    w.close()
+    return culled, full
+
+
+@pytest.mark.parametrize("make,n_rays,rng", [
+    (lambda: scenes.paper_scene(2000, 4, dense=True), 32, 1.0),
+    (lambda: scenes.paper_scene(2000, 5), 7, 3.0),
+    (lambda: scenes.mixed_scene(500, 6), 64, 0.6),
+    (lambda: scenes.small_scene(256, 2), 1, 2.0),
+    (lambda: scenes.paper_scene(500, 7, dense=True), 96, 0.05),
+])
+def test_culled_lidar_equals_every_ray(vmas_lib, make, n_rays, rng):
+    """Each (body, caster) pair testing only the rays within the body's arc
+    gives the readings of testing every ray against every body: the same
+    routines on the same ray directions, so equal up to the compiler's fma
+    contraction in the two kernels (measured: equal bitwise)."""
+    sc = make()
+    culled, full = _both_kernels(sc, n_rays, rng)
+    assert np.abs(culled - full).max() <= 1e-6
+    assert (culled < rng).mean() > 0.01 or rng < 0.1  # the rays do hit things
+    print("\n[culled LIDAR] %s, %d rays: %.4f of readings bitwise equal"
+          % (sc.name, n_rays, float((culled == full).mean())))
+
+
+def test_culled_lidar_large_angles_and_overlaps(vmas_lib):
+    """Casters spun to large angles (their rays are then tested in full:
+    fl(th + step r) strays from the ray's nominal direction) and casters
+    whose origin lies inside another body (every ray reads 0)."""
+    sc = scenes.paper_scene(400, 8, dense=True)
+    st = sc.init_state.copy()
+    rs = np.random.default_rng(8)
+    st[:, :, 4] += rs.choice([0.0, 7e3, -3e5, 2e6], size=st.shape[:2]).astype(np.float32)
+    # the first agent of every fourth env sits on the second one's centre
+    st[::4, 0, 0:2] = st[::4, 1, 0:2] + 0.01
+    culled, full = _both_kernels(sc, 32, 1.5, state=st)
+    assert np.abs(culled - full).max() <= 1e-6
+    assert (culled[::4, 0] == 0).all() and (culled[::4, 1] == 0).all()
