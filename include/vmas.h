@@ -290,7 +290,8 @@ int vmas_ragged_get_schedule(const vmas_ragged *world, int32_t *schedule);
 int vmas_lidar(vmas_world *world, int32_t n_rays, float max_range, float *d_out, void *stream);
 
 /* Diagnostic: which LIDAR kernel vmas_lidar runs (process-wide).  on != 0
- * (the default): the culled kernel, where n_actuated x n_rays <= 3072 --
+ * (the default): the culled kernel, where n_actuated x n_rays <= 3072
+ * and its shared arrays fit 48 KB --
  * each (body, caster) pair tests only the rays within the body's angular arc
  * (bounding circle or segment endpoints, one ray of slack each side), with
  * the same per-ray routines, so the readings are the same minima.  on == 0:

@@ -142,10 +142,18 @@ __device__ __forceinline__ void lidar_setup(const LidarParams &p, int e, float4 
   __syncthreads();
 }
 
-// Direction of ray r of a caster at angle th: the same rounding in both
-// kernels (one fused multiply-add for the angle).
-__device__ __forceinline__ void lidar_ray_dir(float th, float step, int r, float &dx, float &dy) {
-  body_axes(__fmaf_rn(step, (float)r, th), dx, dy);
+// Direction of ray r of a caster with frame (c0, s0): the frame rotated by
+// r * step, whose cos and sin (cr, sr) come from body_axes(r * step).  The
+// rounding is pinned (explicit fma and products), so both kernels cast the
+// same rays, and the ray angles follow the caster's frame exactly whatever
+// the size of its angle.
+__device__ __forceinline__ void lidar_ray_rot(float step, int r, float &cr, float &sr) {
+  body_axes(__fmul_rn(step, (float)r), cr, sr);
+}
+__device__ __forceinline__ void lidar_ray_dir(float c0, float s0, float cr, float sr, float &dx,
+                                              float &dy) {
+  dx = __fmaf_rn(c0, cr, -__fmul_rn(s0, sr));
+  dy = __fmaf_rn(s0, cr, __fmul_rn(c0, sr));
 }
 
 __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
@@ -171,8 +179,10 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
       const int i = s_agent[k];
       const int self = s_slot[i];  // the caster's own slot is skipped
       const float ox = p.px[eb + i], oy = p.py[eb + i];
-      float dx, dy;
-      lidar_ray_dir(p.th[eb + i], step, r, dx, dy);
+      float c0, s0, cr, sr, dx, dy;
+      body_axes(p.th[eb + i], c0, s0);
+      lidar_ray_rot(step, r, cr, sr);
+      lidar_ray_dir(c0, s0, cr, sr, dx, dy);
 #pragma unroll 4
       for (int q = 0; q < b0; ++q) {
         const float4 b = s_pose[q];
@@ -203,21 +213,20 @@ __global__ void __launch_bounds__(128) lidar_kernel(const LidarParams p) {
 // their bounding circle, centre direction +- an upper bound of asin(R / d),
 // segments the arc between their endpoints.  The arc is widened by the
 // angle errors (an arctangent within 0.0016 rad, the tests' own rounding at
-// a grazing ray, the caster's frame and the rounding of its ray angles),
-// and a pair tests the rays inside it.  A pair whose body lies
-// beyond the range, by its bounding circle or its closest point, is skipped
-// (every entry distance exceeds the range, which the reading keeps); an
-// origin inside a sphere or a box reads 0 on every ray, as there.  A pair
-// tests every ray when the origin lies inside the bounding circle, when a
-// segment's arc approaches pi, or when the caster's angle is so large that
-// fl(th + step r) may stray from its ray by a quarter of a spacing.
+// a grazing ray, the caster's frame and the rounding of its ray directions,
+// which are the caster's frame rotated by 2 pi r / R), and a pair tests the
+// rays inside it.  A pair whose body lies beyond the range, by its bounding
+// circle or its closest point, is skipped (every entry distance exceeds the
+// range, which the reading keeps); an origin inside a sphere or a box reads
+// 0 on every ray, as there.  A pair tests every ray when the origin lies
+// inside the bounding circle or when a segment's arc approaches pi.
 // Minima are taken with atomicMin on order-preserving keys in shared
 // memory, so the reading is the minimum whatever the order.
 
 constexpr int kLidarCullMaxRays = 3072;  // n_actuated x n_rays held in shared memory
 
 __host__ __device__ inline int lidar_cull_smem_bytes(int N, int A, int R) {
-  return align16(lidar_smem_bytes(N)) + A * R * 12;  // + directions, keys
+  return align16(lidar_smem_bytes(N)) + A * R * 12 + R * 8;  // + directions, rotations, keys
 }
 
 // Order-preserving keys of floats: a < b exactly when key(a) < key(b)
@@ -255,7 +264,8 @@ __device__ __forceinline__ bool lidar_arc(float phi, float half, float phi0, flo
   u = fminf(fmaxf(u, 0.f), (float)R);  // rounding; NaN becomes 0 (w then decides)
   // the rays whose angle lies within the arc widened by the angle errors:
   // 0.0016 rad from the arctangent at each edge, 1e-5 rad for the tests'
-  // own rounding at a grazing ray, and 1 % of a spacing for fl(th + step r)
+  // own rounding at a grazing ray, and 1 % of a spacing for the rounding
+  // of the ray directions (about 2e-7 rad)
   const float w = half * inv_step + 0.0025f * inv_step + 0.01f;
   if (!(w < 0.5f * (float)R)) return false;  // wide, or not a number: every ray
   r_lo = (int)ceilf(u - w);   // in (-R / 2, R]
@@ -263,14 +273,17 @@ __device__ __forceinline__ bool lidar_arc(float phi, float half, float phi0, flo
   return r_hi - r_lo + 1 < R;
 }
 
-__global__ void __launch_bounds__(128) lidar_cull_kernel(const LidarParams p) {
+// 16 CTAs per SM (32 registers): the kernel is issue-bound and wants every warp
+__global__ void __launch_bounds__(128, 16) lidar_cull_kernel(const LidarParams p) {
   extern __shared__ __align__(16) unsigned char lsm[];
   float4 *s_pose = reinterpret_cast<float4 *>(lsm);            // [N] by list slot
   float2 *s_half = reinterpret_cast<float2 *>(s_pose + p.N);   // [N] by list slot
   uint8_t *s_kind = reinterpret_cast<uint8_t *>(s_half + p.N);  // [N] by entity
   const int AR = p.A * p.R;
+  // 8-byte arrays first, then the 4-byte ones (every start stays aligned)
   float2 *s_dir = reinterpret_cast<float2 *>(lsm + align16(lidar_smem_bytes(p.N)));  // [A][R]
-  uint32_t *s_key = reinterpret_cast<uint32_t *>(s_dir + AR);                         // [A][R]
+  float2 *s_rot = s_dir + AR;                                                          // [R]
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(s_rot + p.R);                         // [A][R]
   __shared__ int s_ent[VMAS_LIDAR_MAX_ENTITIES];
   __shared__ int s_slot[VMAS_LIDAR_MAX_ENTITIES];
   __shared__ int s_agent[VMAS_LIDAR_MAX_ENTITIES];
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(128) lidar_cull_kernel(const LidarParams p) {
   __shared__ int s_nact;
   __shared__ float s_ox[VMAS_LIDAR_MAX_ENTITIES], s_oy[VMAS_LIDAR_MAX_ENTITIES];
   __shared__ float s_phi0[VMAS_LIDAR_MAX_ENTITIES];  // direction of the caster's ray 0
-  __shared__ int s_every[VMAS_LIDAR_MAX_ENTITIES];   // 1: the caster's rays are not culled
+  __shared__ float2 s_frame[VMAS_LIDAR_MAX_ENTITIES];  // the caster's (cos, sin)
   const int e = blockIdx.x;
   const size_t eb = (size_t)e * p.N;
   lidar_setup(p, e, s_pose, s_half, s_kind, s_ent, s_slot, s_agent, s_start, &s_nact);
@@ -292,17 +305,22 @@ __global__ void __launch_bounds__(128) lidar_cull_kernel(const LidarParams p) {
     s_ox[k] = p.px[eb + i];
     s_oy[k] = p.py[eb + i];
     s_phi0[k] = atan2f(sn, c);
-    // fl(th + step r) is within ulp(|th| + 2 pi) / 2 of th + step r: cull
-    // only while that stays below 1 % of a spacing
-    s_every[k] = !((fabsf(th) + 6.3f) * 6e-8f < 0.01f * step);
+    s_frame[k] = make_float2(c, sn);
   }
+  for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+    float cr, sr;
+    lidar_ray_rot(step, r, cr, sr);
+    s_rot[r] = make_float2(cr, sr);
+  }
+  __syncthreads();
   // a warp per caster, its rays across the lanes (no division per item)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int k = warp; k < p.A; k += nwarps) {
-    const float th = k < nact ? p.th[eb + s_agent[k]] : 0.f;
+    const float2 fr = k < nact ? s_frame[k] : make_float2(1.f, 0.f);
     for (int r = lane; r < p.R; r += 32) {
       float dx = 1.f, dy = 0.f;
-      if (k < nact) lidar_ray_dir(th, step, r, dx, dy);
+      const float2 ro = s_rot[r];
+      if (k < nact) lidar_ray_dir(fr.x, fr.y, ro.x, ro.y, dx, dy);
       s_dir[k * p.R + r] = make_float2(dx, dy);
       s_key[k * p.R + r] = lidar_key(p.range);
     }
@@ -321,7 +339,7 @@ __global__ void __launch_bounds__(128) lidar_cull_kernel(const LidarParams p) {
     const float2 hs = s_half[q];
     const int shape = q < b0 ? 0 : (q < l0 ? 1 : 2);
     const float px = b.x - ox, py = b.y - oy;  // centre seen from the origin
-    bool every = s_every[k] != 0;
+    bool every = false;
     float phi, half;
     if (shape == 2) {
       // segment: its closest point against the range, its endpoints for the arc

@@ -1028,7 +1028,9 @@ int vmas_lidar(vmas_world *w, int32_t n_rays, float max_range, float *d_out, voi
   p.param = w->param;
   p.kind = w->kind;
   p.out = d_out;
-  if (g_lidar_cull && (int64_t)w->A * n_rays <= vmas::kLidarCullMaxRays) {
+  // the culled kernel where its shared arrays fit the default 48 KB
+  if (g_lidar_cull && (int64_t)w->A * n_rays <= vmas::kLidarCullMaxRays &&
+      vmas::lidar_cull_smem_bytes(w->N, w->A, n_rays) <= 48 * 1024) {
     const size_t smem = (size_t)vmas::lidar_cull_smem_bytes(w->N, w->A, n_rays);
     vmas::lidar_cull_kernel<<<w->E, 128, smem, as_stream(stream)>>>(p);
   } else {

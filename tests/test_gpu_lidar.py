@@ -123,6 +123,8 @@ def _both_kernels(sc, n_rays, rng_max, state=None):
     (lambda: scenes.mixed_scene(500, 6), 64, 0.6),
     (lambda: scenes.small_scene(256, 2), 1, 2.0),
     (lambda: scenes.paper_scene(500, 7, dense=True), 96, 0.05),
+    (lambda: scenes.mixed_scene(300, 9), 7, 1.0),  # odd n_actuated x n_rays (11 x 7)
+    (lambda: scenes.small_scene(64, 3), 1000, 2.0),  # 4 x 1000 rays: the every-ray kernel
 ])
 def test_culled_lidar_equals_every_ray(vmas_lib, make, n_rays, rng):
     """Each (body, caster) pair testing only the rays within the body's arc
