@@ -430,14 +430,18 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
       // for the fixed count), filling the record and compact-list areas,
       // which the lane lists and the compaction only write after every mask
       // is built.
+      // Kernels with one mask per slot (ragged classes of 3 or 4 slots of 16
+      // or 32 lanes) keep a single copy there when two do not fit, and build
+      // every slot's mask before the first lane list is written.
       constexpr int kCap = NC > 0 ? NC : G * SLOTS;
       constexpr int kLcBytes = (2 * G * kLaneCand + 15) & ~15;  // lane lists; compact list
       constexpr int kRecBytes = kRecCap * 20 > kLcBytes ? kRecCap * 20 : kLcBytes;
-      constexpr bool kTwice = NC == 0;
-      constexpr bool kAabb = kOneMask && (kTwice ? 32 * kCap <= kRecBytes + kLcBytes
-                                                 : kLcBytes + 16 * kCap <= kRecBytes);
+      constexpr bool kBeside = NC > 0 && kLcBytes + 16 * kCap <= kRecBytes;  // after the lane lists
+      constexpr bool kTwice = !kBeside && 32 * kCap <= kRecBytes + kLcBytes;
+      constexpr bool kOnce = !kBeside && !kTwice && 16 * kCap <= kRecBytes + kLcBytes;
+      constexpr bool kAabb = kMask && (kBeside || kTwice || kOnce);
       float4 *s_ab = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(s_rec) +
-                                                (kTwice ? 0 : kLcBytes));  // [N] or [2 N]
+                                                (kBeside ? kLcBytes : 0));  // [N] or [2 N]
       [[maybe_unused]] const int NB = kTwice ? 2 * N : N;  // bound of the checked build
       if constexpr (kAabb) {
 #pragma unroll
@@ -554,8 +558,17 @@ __device__ __forceinline__ bool world_step_body(const StepParams &p, unsigned ch
 #pragma unroll
             for (int s = 0; s < SLOTS; ++s) m |= pass1(s) << (s * D);
           }
-          if constexpr (kAabb && kTwice) __syncwarp();  // every box read: lane lists may overwrite them
+          if constexpr (kAabb && !kBeside) __syncwarp();  // every box read: lane lists may overwrite them
           if (valid) walk(m, 0);
+        } else if constexpr (kAabb) {
+          unsigned long long ms[SLOTS];
+#pragma unroll
+          for (int s = 0; s < SLOTS; ++s) ms[s] = valid ? pass1(s) : 0ull;
+          __syncwarp();  // every box read: lane lists may overwrite them
+          if (valid) {
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) walk(ms[s], s);
+          }
         } else if (valid) {
 #pragma unroll
           for (int s = 0; s < SLOTS; ++s) walk(pass1(s), s);
