@@ -433,7 +433,10 @@ int vmas_sur_get_params(vmas_surrogate *sur, float *h_params);
  * chip (sphere world only; box worlds always take the layered path);
  * VMAS_SUR_LAYERED: one GEMM launch per layer over all envs, with the
  * activations in device memory (the path training uses).  Both round at the
- * same points. */
+ * same points.  The layered path runs the edge MLP on the neighbour slots in
+ * use only (compacted in slot order on the device); it reads their count
+ * back to size the edge GEMMs, so each layered forward (inference or
+ * training) synchronises `stream` once. */
 enum { VMAS_SUR_FUSED = 0, VMAS_SUR_LAYERED = 1 };
 int vmas_sur_set_mode(vmas_surrogate *sur, int32_t mode);
 /* The network on the world's current state: d_out [n_envs * nodes][8]

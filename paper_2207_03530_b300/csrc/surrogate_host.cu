@@ -54,6 +54,12 @@ struct vmas_surrogate {
   bf16 *d_outbf = nullptr, *g128bf = nullptr, *gebf = nullptr;
   float *part = nullptr, *loss_part = nullptr, *save = nullptr, *target = nullptr;
   int *list = nullptr, *list_len = nullptr;
+  // compact edges: the used neighbour slots, in slot-major order
+  bf16 *edgec = nullptr;                         // [RK][16] features of the used slots
+  int *epos = nullptr, *emap = nullptr;          // [RK] slot -> position (-1), position -> slot
+  int *escan = nullptr, *etotal = nullptr;       // block sums; the count
+  int *h_total = nullptr;                        // pinned host copy of the count
+  int n_edges = 0;                               // used slots of the last forward
 };
 
 namespace {
@@ -64,8 +70,10 @@ void free_sur(vmas_surrogate *s) {
                   s->he,    s->zin,   s->h1,     s->h2,     s->mask,   s->ze2,    s->out,
                   s->ze1,   s->z1,    s->z2,     s->d_out,  s->g128,   s->d_zin,  s->ge,
                   s->d_outbf, s->g128bf, s->gebf, s->part,  s->loss_part, s->save, s->target,
-                  s->list,  s->list_len, s->pbfT, s->err};
+                  s->list,  s->list_len, s->pbfT, s->err, s->edgec, s->epos, s->emap,
+                  s->escan, s->etotal};
   for (void *q : ptrs) cudaFree(q);
+  if (s->h_total) cudaFreeHost(s->h_total);
   delete s;
 }
 
@@ -274,15 +282,31 @@ int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool t
   const bf16 *W = s->pbf;
   const float *P = s->p32;
   int rc;
-  // edge MLP
-  if ((rc = gemm(st, false, true, RK, 64, 16, s->edge, 16, W + kOffWe1, 16, P + kOffbe1, 1,
-                 train ? s->ze1 : nullptr, 64, s->he, 64, nullptr, 1, s->err)))
-    return rc;
-  if ((rc = gemm(st, false, true, RK, 64, 64, s->he, 64, W + kOffWe2, 64, P + kOffbe2, 0, s->ze2,
-                 64, nullptr, 0, nullptr, 1, s->err)))
-    return rc;
-  sur::aggregate_kernel<<<blocks_for((size_t)R * 80, 256), 256, 0, st>>>(R, s->ze2, s->mask,
-                                                                          s->node, s->zin);
+  // the used neighbour slots, compacted; their count comes back to the host
+  // (one stream synchronisation) to size the edge GEMMs
+  const int nb = (int)blocks_for((size_t)RK, sur::kScanBlock);
+  sur::edge_scan_blocks_kernel<<<nb, sur::kScanThreads, 0, st>>>((size_t)RK, s->mask, s->epos,
+                                                                 s->escan);
+  sur::edge_scan_sums_kernel<<<1, 1024, 0, st>>>(nb, s->escan, s->etotal);
+  sur::edge_compact_kernel<<<blocks_for((size_t)RK, 256), 256, 0, st>>>(
+      (size_t)RK, s->epos, s->escan, s->edge, s->edgec, s->emap);
+  VMAS_CUDA(cudaGetLastError());
+  VMAS_CUDA(cudaMemcpyAsync(s->h_total, s->etotal, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VMAS_CUDA(cudaStreamSynchronize(st));
+  const int RE = *s->h_total;
+  if (RE < 0 || RE > RK) return fail(VMAS_EDEVICE, "edge count out of range");
+  s->n_edges = RE;
+  // edge MLP on the used slots
+  if (RE > 0) {
+    if ((rc = gemm(st, false, true, RE, 64, 16, s->edgec, 16, W + kOffWe1, 16, P + kOffbe1, 1,
+                   train ? s->ze1 : nullptr, 64, s->he, 64, nullptr, 1, s->err)))
+      return rc;
+    if ((rc = gemm(st, false, true, RE, 64, 64, s->he, 64, W + kOffWe2, 64, P + kOffbe2, 0, s->ze2,
+                   64, nullptr, 0, nullptr, 1, s->err)))
+      return rc;
+  }
+  sur::aggregate_compact_kernel<<<blocks_for((size_t)R * 80, 256), 256, 0, st>>>(
+      R, s->ze2, s->mask, s->epos, s->node, s->zin);
   VMAS_CUDA(cudaGetLastError());
   // node MLP
   if ((rc = gemm(st, false, true, R, 128, 80, s->zin, 80, W + kOffW1, 80, P + kOffb1, 1,
@@ -299,7 +323,7 @@ int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool t
 // sur_forward with train = true), for E envs of `nodes` rows each.
 int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *target, float *d_loss,
                  cudaStream_t st) {
-  const int R = E * nodes, RK = R * sur::kK;
+  const int R = E * nodes;
   const float count = (float)E * (float)(sur::kAgents * 4 + (nodes - sur::kAgents) * 6);
   float *G = s->grad;
   const bf16 *W = s->pbf;
@@ -348,25 +372,27 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
   if ((rc = gemm(st, false, true, R, 80, 128, s->g128bf, 128, s->pbfT + kOffW1T, 128, nullptr, 0,
                  s->d_zin, 80, nullptr, 0, nullptr, 1, s->err)))
     return rc;
-  // edge layer 2 (through the masked sum)
-  sur::edge_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>(R, s->d_zin, s->mask,
-                                                                           s->ze2, s->ge, s->gebf);
+  // edge layer 2 (through the masked sum), on the used slots of the forward
+  const int RE = s->n_edges;
+  if (RE == 0) return VMAS_OK;  // no edge: the edge weights' gradients stay zero
+  sur::edge_back_compact_kernel<<<blocks_for((size_t)RE * 64, 256), 256, 0, st>>>(
+      R, RE, s->d_zin, s->mask, s->emap, s->ze2, s->ge, s->gebf);
   VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 64, 64, RK, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
+  if ((rc = gemm(st, true, false, 64, 64, RE, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
                  nullptr, 0, s->part, sp)))
     return rc;
-  if ((rc = col_sum(st, G + kOffbe2, s->ge, RK, 64, s->part))) return rc;
-  if ((rc = gemm(st, false, true, RK, 64, 64, s->gebf, 64, s->pbfT + kOffWe2T, 64, nullptr, 0, s->ge,
+  if ((rc = col_sum(st, G + kOffbe2, s->ge, RE, 64, s->part))) return rc;
+  if ((rc = gemm(st, false, true, RE, 64, 64, s->gebf, 64, s->pbfT + kOffWe2T, 64, nullptr, 0, s->ge,
                  64, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // edge layer 1
-  sur::gelu_back_kernel<<<blocks_for((size_t)RK * 64, 256), 256, 0, st>>>((size_t)RK * 64, s->ge,
+  sur::gelu_back_kernel<<<blocks_for((size_t)RE * 64, 256), 256, 0, st>>>((size_t)RE * 64, s->ge,
                                                                           s->ze1, s->ge, s->gebf);
   VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 64, 16, RK, s->gebf, 64, s->edge, 16, nullptr, 0, G + kOffWe1, 16,
+  if ((rc = gemm(st, true, false, 64, 16, RE, s->gebf, 64, s->edgec, 16, nullptr, 0, G + kOffWe1, 16,
                  nullptr, 0, s->part, sp)))
     return rc;
-  return col_sum(st, G + kOffbe1, s->ge, RK, 64, s->part);
+  return col_sum(st, G + kOffbe1, s->ge, RE, 64, s->part);
 }
 
 int refresh_transposed(vmas_surrogate *s, cudaStream_t st);
@@ -464,7 +490,10 @@ int vmas_sur_create(int32_t max_envs, vmas_surrogate **out) {
       dalloc(&s->ze2, RK * 64) && dalloc(&s->out, R * 8) &&
       dalloc(&s->part, (size_t)kSplitCap * 128 * 128) && dalloc(&s->loss_part, R * 8 / 256 + 1) &&
       dalloc(&s->list, (size_t)max_envs) && dalloc(&s->list_len, 1) &&
-      dalloc(&s->pbfT, kTransposed) && dalloc(&s->err, 4);
+      dalloc(&s->pbfT, kTransposed) && dalloc(&s->err, 4) && dalloc(&s->edgec, RK * 16) &&
+      dalloc(&s->epos, RK) && dalloc(&s->emap, RK) &&
+      dalloc(&s->escan, RK / sur::kScanBlock + 1) && dalloc(&s->etotal, 1) &&
+      cudaHostAlloc((void **)&s->h_total, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_sur(s);
