@@ -256,6 +256,20 @@ __device__ __forceinline__ float bounding_radius(const float4 pr, uint32_t kind)
   return (kind & 3u) == 1u ? sqrtf(pr.z * pr.z + pr.w * pr.w) : pr.z;
 }
 
+// 16 floats as 16 bfloat16 (round to nearest even) in two 16-byte stores;
+// dst is 32-byte aligned (a row of 16).
+__device__ __forceinline__ void store_bf16x16(bf16 *dst, const float (&v)[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);  // .x at the lower address
+    w[q] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+  d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 __global__ void features_kernel(const FeatureArgs f) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int R = f.E * f.nodes;
@@ -287,30 +301,39 @@ __global__ void features_kernel(const FeatureArgs f) {
     nf[13] = 0.1f * f.om[b + i];
     nf[14] = 0.01f * a[2] * pi.y;
   }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) f.node[(size_t)r * 16 + q] = __float2bfloat16_rn(nf[q]);
-  // the K nearest other nodes within the radius (ties: lower index first)
+  store_bf16x16(f.node + (size_t)r * 16, nf);
+  // the K nearest other nodes within the radius (ties: lower index first),
+  // kept sorted in registers: +inf marks an empty place, and a new distance
+  // goes after every kept one that is not larger (insertion, unrolled)
   float bd[kK];
   int bj[kK];
-  int n = 0;
+#pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    bd[k] = __int_as_float(0x7f800000);
+    bj[k] = 0;
+  }
   for (int j = 0; j < f.nodes; ++j) {
     if (j == i) continue;
     const float dx = f.px[b + j] - x, dy = f.py[b + j] - y;
     const float d = sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
     if (!(d < kRadius)) continue;
-    int p = n;  // insertion position among the n kept (n <= K)
-    while (p > 0 && bd[p - 1] > d) --p;
-    if (p >= kK) continue;
-    const int last = n < kK ? n : kK - 1;
-    for (int q = last; q > p; --q) {
-      bd[q] = bd[q - 1];
-      bj[q] = bj[q - 1];
+#pragma unroll
+    for (int q = kK - 1; q > 0; --q) {
+      const bool mv = bd[q - 1] > d;          // the place below is larger: it moves up
+      const bool put = !mv && bd[q] > d;      // d belongs here
+      bj[q] = mv ? bj[q - 1] : (put ? j : bj[q]);
+      bd[q] = mv ? bd[q - 1] : (put ? d : bd[q]);
     }
-    bd[p] = d;
-    bj[p] = j;
-    if (n < kK) ++n;
+    if (bd[0] > d) {
+      bd[0] = d;
+      bj[0] = j;
+    }
   }
-  for (int k = 0; k < kK; ++k) {
+  int n = 0;
+#pragma unroll
+  for (int k = 0; k < kK; ++k) n += bd[k] < kRadius ? 1 : 0;
+#pragma unroll
+  for (int k = 0; k < kK; ++k) {  // unrolled: bd and bj stay in registers
     const size_t row = (size_t)k * R + r;
     float v[16];
 #pragma unroll
@@ -336,8 +359,7 @@ __global__ void features_kernel(const FeatureArgs f) {
       }
       mk = 1.f;
     }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) f.edge[row * 16 + q] = __float2bfloat16_rn(v[q]);
+    store_bf16x16(f.edge + row * 16, v);
     f.mask[row] = mk;
   }
 }
