@@ -445,23 +445,34 @@ __global__ void edge_compact_kernel(size_t n, int *pos, const int *bsum, const b
 }
 
 // zin[r] = [node[r], bf(sum_k mask[k][r] gelu(ze2[pos[k][r]]))] (80 wide), the
-// messages read from the compact edge array in slot order.
-__global__ void aggregate_compact_kernel(int R, const float *ze2c, const float *mask,
-                                         const int *pos, const bf16 *node, bf16 *zin) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)R * 80) return;
-  const size_t r = t / 80;
-  const int c = (int)(t % 80);
-  if (c < 16) {
-    zin[t] = node[r * 16 + c];
-    return;
-  }
-  float s = 0.f;
+// messages read from the compact edge array in slot order.  One warp per
+// row: lanes 0..K-1 fetch the slots' flags and positions (shared by
+// shuffles), lane l sums message columns 2l and 2l + 1 (one 8-byte load per
+// slot in use) and lanes 0..7 copy the node features.
+__global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const float *ze2c,
+                                                                const float *mask, const int *pos,
+                                                                const bf16 *node, bf16 *zin) {
+  const size_t r = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= (size_t)R) return;  // whole warps leave together
+  const float mk = lane < kK ? mask[(size_t)lane * R + r] : 0.f;
+  const int pk = lane < kK && mk != 0.f ? pos[(size_t)lane * R + r] : 0;
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
   for (int k = 0; k < kK; ++k) {
-    const size_t rk = (size_t)k * R + r;
-    if (mask[rk] != 0.f) s += mask[rk] * gelu(ze2c[(size_t)pos[rk] * 64 + (c - 16)]);
+    const float m = __shfl_sync(0xffffffffu, mk, k);
+    const int q = __shfl_sync(0xffffffffu, pk, k);
+    if (m != 0.f) {
+      const float2 z = reinterpret_cast<const float2 *>(ze2c + (size_t)q * 64)[lane];
+      s0 += m * gelu(z.x);
+      s1 += m * gelu(z.y);
+    }
   }
-  zin[t] = __float2bfloat16_rn(s);
+  bf16 *out = zin + r * 80;
+  if (lane < 8)
+    reinterpret_cast<uint32_t *>(out)[lane] = reinterpret_cast<const uint32_t *>(node + r * 16)[lane];
+  const __nv_bfloat162 h = __floats2bfloat162_rn(s0, s1);
+  reinterpret_cast<__nv_bfloat162 *>(out + 16)[lane] = h;
 }
 
 // Edge-message gradient on the compact array: d_ze2[e][c] =
