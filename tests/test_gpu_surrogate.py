@@ -625,3 +625,41 @@ def test_trained_box_surrogate_50_step_error(vmas_lib):
     assert err["trained"][0] < err["plain_s1"][0]
     sur.close()
     untrained.close()
+
+
+def test_no_edges_layered_forward_and_gradient(vmas_lib):
+    """Agents on a grid 0.45 apart have no neighbour within 0.3: the layered
+    path then runs no edge GEMM at all (its compacted edge list is empty).
+    The forward still matches the reference, and the edge weights'
+    gradients are exactly zero."""
+    E = 8
+    sc = scenes.surrogate_scene(E, 4)
+    st = sc.init_state.copy()
+    g = (np.arange(4) - 1.5) * 0.45
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    st[:, :16, 0] = gx.ravel()
+    st[:, :16, 1] = gy.ravel()
+    st[:, :16, 2:4] = np.random.default_rng(4).uniform(-0.5, 0.5, (E, 16, 2))
+    sc = sc.with_state(st.astype(np.float32))
+    act = scenes.make_actions(sc, 1, 6)[0]
+    st64, S = _ref_inputs(sc)
+    node, edge, mask = S.features(st64, act.astype(np.float64), sc.size_a[:, :16], sc.mass[:, :16])
+    assert mask.sum() == 0
+    w64 = _weights(3)
+    ref = S.forward(w64, node, edge, mask)
+    w, sur, out = _cuda_forward(sc, w64, act, "layered")
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= FWD_TOL
+    target = np.random.default_rng(2).normal(0, 1, (E * 16, 4)).astype(np.float32)
+    loss_r, g_r = S.loss_and_grad(w64, node, edge, mask, target.astype(np.float64))
+    loss, grad = sur.loss_grad(w, torch.from_numpy(act).cuda(), torch.from_numpy(target).cuda())
+    assert float(loss.item()) == pytest.approx(loss_r, rel=LOSS_TOL)
+    from paper_2207_03530_b300.surrogate import unflatten
+
+    gr = unflatten(grad.cpu().numpy())
+    for k in ("We1", "be1", "We2", "be2"):
+        assert not gr[k].any(), k
+    for k in ("W1", "b1", "W2", "b2", "W3"):
+        e = np.linalg.norm(gr[k] - g_r[k]) / max(np.linalg.norm(g_r[k]), 1e-12)
+        assert e <= GRAD_TOL, (k, e)
+    w.close()
+    sur.close()
