@@ -306,7 +306,10 @@ int vmas_debug_lidar_cull(int32_t on);
  * semi-implicit Euler (Eq. 1) over all substeps; the contact mask is held
  * piecewise constant (no term from the force jump at gap 0).  Requires every
  * entity to be a sphere, n_entities <= 32 and no speed cap (VMAS_EINVAL
- * otherwise).
+ * otherwise).  Each entity's pair sums visit its candidate partners (pairs
+ * within 4 x the world's skin of touching, rebuilt when a body may have moved
+ * half of that) in ascending order, so the loss and gradient do not depend
+ * on the skin, only speed does.
  *   d_actions [n_steps][n_envs][n_actuated][3], d_goals [n_envs][n_actuated][2];
  *   d_ckpt    [ceil(n_steps / ckpt_every)][n_envs][n_entities][4] (x y vx vy at
  *             steps 0, ckpt_every, ...), written by vmas_diff_rollout and read

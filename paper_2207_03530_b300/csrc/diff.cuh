@@ -20,8 +20,10 @@
 // Layout: groups of SPL G lanes (G = 4, 8, 16 or 32, the smallest power of
 // two >= N; SPL = 1 or 2), one environment per group and 32 / (SPL G) per
 // warp, entity i in lane i of each of its SPL half-groups (N <= 32).  With
-// SPL = 1 the pair sums of entity i run over j = 0 .. N-1 in order, the same
-// order as a serial loop over canonical pairs; with SPL = 2 the two halves
+// SPL = 1 the pair sums of entity i run over its candidate partners j in
+// ascending order (a bitmask of the pairs within r_i + r_j + skin, rebuilt
+// when a body may have moved half the skin; the pairs left out cannot touch,
+// so the sums equal a serial loop over all pairs); with SPL = 2 the two halves
 // of the group sum j < ceil(N/2) and the rest, and one shuffle adds the two
 // partial sums (both halves then hold the same bits), which shortens each
 // substep's pair loop and doubles the warps a small batch of envs fills (the
@@ -44,6 +46,7 @@ constexpr int kDiffWarps = 4;  // environments per CTA
 struct DiffParams {
   int E, N, A, S, T, K;
   float h, damp, gx, gy, ck, inv_k, c;
+  float skin;  // candidate masks: pairs within rsum + skin at the build
   const float *px, *py, *vx, *vy;  // initial state planes [E * N]
   const float4 *param;             // {1/m, 1/I, r, 0}
   const uint8_t *kind;
@@ -112,39 +115,78 @@ __device__ __forceinline__ DiffLane diff_lane(const DiffParams &p, int e, bool v
   return L;
 }
 
+// Candidate partners of entity `lane` (bit j): active pairs whose centres lie
+// within r_i + r_j + skin at the positions in s_pos (rounded outward by
+// 1e-4 relative).  While no body of the env has moved more than skin / 2
+// since, a pair outside the mask stays farther apart than r_i + r_j, so
+// sphere_force would reject it: the partners in the mask, visited in
+// ascending j, give the same sums as every partner.
+__device__ __forceinline__ unsigned diff_mask(const DiffParams &p, const DiffLane &L, int lane,
+                                              const float2 *s_pos, const uint8_t *s_kind,
+                                              const float *s_r, float x, float y) {
+  unsigned m = 0u;
+  if (L.ok && (L.kd & kCollidable)) {
+    for (int j = 0; j < p.N; ++j) {
+      if (j == lane || !pair_active(L.kd, s_kind[j])) continue;
+      const float2 q = s_pos[j];
+      const float dx = x - q.x, dy = y - q.y, lim = L.r + s_r[j] + p.skin;
+      if (dx * dx + dy * dy <= 1.0001f * (lim * lim)) m |= 1u << j;
+    }
+  }
+  return m;
+}
+
+// Keeps the warp's candidate masks valid at the positions in s_pos: when any
+// body of the warp has moved more than 0.45 skin from where the last build
+// saw it (skin / 2 is the bound; the rest covers rounding), or nothing has
+// been built yet, every lane rebuilds its mask and records its position.
+__device__ __forceinline__ bool diff_refresh(const DiffParams &p, const DiffLane &L, int lane,
+                                             const float2 *s_pos, const uint8_t *s_kind,
+                                             const float *s_r, float x, float y, bool &built,
+                                             float &bx, float &by, unsigned &cm) {
+  const float dx = x - bx, dy = y - by, lim = 0.45f * p.skin;
+  if (!__any_sync(0xffffffffu, !built || dx * dx + dy * dy > lim * lim)) return false;
+  cm = diff_mask(p, L, lane, s_pos, s_kind, s_r, x, y);
+  bx = x;
+  by = y;
+  built = true;
+  return true;
+}
+
 // One forward substep of entity `lane` of its env; s_pos holds every entity's
 // (x, y).  SPL = 2: this lane sums the pairs of its half (`half`) of j and
 // the partner lane (lane ^ G) the other half.
 template <int G, int SPL>
 __device__ __forceinline__ void diff_substep(const DiffParams &p, const DiffLane &L, int lane,
                                              int half, const float2 *s_pos, const uint8_t *s_kind,
-                                             const float *s_r, float fax, float fay, float &x,
-                                             float &y, float &vx, float &vy) {
+                                             const float *s_r, unsigned cm, float fax, float fay,
+                                             float &x, float &y, float &vx, float &vy) {
   float Fx = fax + L.m * p.gx, Fy = fay + L.m * p.gy;
   if constexpr (SPL == 1) {
-    if (L.ok && (L.kd & kCollidable)) {
-      // four partners at a time: their loads and distance tests issue
-      // together; the pairs that pass go through sphere_force in j order
-      for (int j0 = 0; j0 < p.N; j0 += 4) {
-        float2 q[4];
-        float rs[4];
-        bool near[4];
+    // the candidate partners (cm, from diff_mask), four at a time in
+    // ascending j: their loads and distance tests issue together, and the
+    // pairs that pass go through sphere_force in j order
+    unsigned m = cm;
+    while (m) {
+      float2 q[4];
+      float rs[4];
+      bool near[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = j0 + u;
-          const bool in = j < p.N && j != lane && pair_active(L.kd, s_kind[j < p.N ? j : 0]);
-          q[u] = s_pos[j < p.N ? j : 0];
-          rs[u] = L.r + s_r[j < p.N ? j : 0];
-          const float dx = x - q[u].x, dy = y - q[u].y;
-          near[u] = in && !(dx * dx + dy * dy > 1.0001f * (rs[u] * rs[u]));
-        }
+      for (int u = 0; u < 4; ++u) {
+        const bool in = m != 0u;
+        const int j = in ? __ffs(m) - 1 : 0;
+        m &= in ? m - 1u : 0u;
+        q[u] = s_pos[j];
+        rs[u] = L.r + s_r[j];
+        const float dx = x - q[u].x, dy = y - q[u].y;
+        near[u] = in && !(dx * dx + dy * dy > 1.0001f * (rs[u] * rs[u]));
+      }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float fx, fy;
-          if (near[u] && sphere_force(x, y, q[u].x, q[u].y, rs[u], p, fx, fy, nullptr)) {
-            Fx += fx;
-            Fy += fy;
-          }
+      for (int u = 0; u < 4; ++u) {
+        float fx, fy;
+        if (near[u] && sphere_force(x, y, q[u].x, q[u].y, rs[u], p, fx, fy, nullptr)) {
+          Fx += fx;
+          Fy += fy;
         }
       }
     }
@@ -200,6 +242,9 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
     s_kind[ent] = (uint8_t)L.kd;
     s_r[ent] = L.r;
   }
+  unsigned cm = 0u;  // candidate partners (SPL = 1)
+  float bx = 0.f, by = 0.f;
+  bool built = false;
   for (int t = 0; t < p.T; ++t) {
     if (t % p.K == 0 && L.ok && w0) {
       float4 *c = reinterpret_cast<float4 *>(p.ckpt) + ((size_t)(t / p.K) * p.E + e) * p.N + ent;
@@ -214,7 +259,8 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_forward_kernel(const Dif
     for (int s = 0; s < p.S; ++s) {
       if (w0) s_pos[ent] = make_float2(x, y);
       __syncwarp();
-      diff_substep<G, SPL>(p, L, ent, half, s_pos, s_kind, s_r, fax, fay, x, y, vx, vy);
+      if constexpr (SPL == 1) diff_refresh(p, L, ent, s_pos, s_kind, s_r, x, y, built, bx, by, cm);
+      diff_substep<G, SPL>(p, L, ent, half, s_pos, s_kind, s_r, cm, fax, fay, x, y, vx, vy);
       __syncwarp();
     }
   }
@@ -267,6 +313,12 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
     const float4 c = L.ok ? reinterpret_cast<const float4 *>(p.ckpt)[((size_t)seg * p.E + e) * p.N + ent]
                           : make_float4(0.f, 0.f, 0.f, 0.f);
     float x = c.x, y = c.y, vx = c.z, vy = c.w;
+    // candidate masks of the replay (SPL = 1), rebuilt from the checkpoint;
+    // um collects every partner any of them held, so each pair that touches
+    // at some substep of the segment is in um
+    unsigned cm = 0u, um = 0u;
+    float bx = 0.f, by = 0.f;
+    bool built = false;
     int q = 0;
     for (int t = ta; t < tb; ++t) {
       float fax = 0.f, fay = 0.f;
@@ -278,7 +330,11 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
       for (int s = 0; s < p.S; ++s, ++q) {
         if (w0) traj[q * 32 + ent] = make_float2(x, y);
         __syncwarp();
-        diff_substep<G, SPL>(p, L, ent, half, traj + q * 32, s_kind, s_r, fax, fay, x, y, vx, vy);
+        if constexpr (SPL == 1) {
+          if (diff_refresh(p, L, ent, traj + q * 32, s_kind, s_r, x, y, built, bx, by, cm)) um |= cm;
+        }
+        diff_substep<G, SPL>(p, L, ent, half, traj + q * 32, s_kind, s_r, cm, fax, fay, x, y, vx,
+                             vy);
         __syncwarp();
       }
     }
@@ -306,30 +362,34 @@ __global__ void __launch_bounds__(kDiffWarps * 32) diff_backward_kernel(const Di
         if (w0) s_lf[ent] = make_float2(lfx, lfy);
         __syncwarp();
         if constexpr (SPL == 1) {
-          if (L.ok && (L.kd & kCollidable)) {
-            const float2 me = traj[q * 32 + ent];
-            for (int j0 = 0; j0 < p.N; j0 += 4) {  // four partners at a time, as forward
-              float2 o[4];
-              float rs[4];
-              bool near[4];
+          // the partners of um in ascending j, four at a time as forward
+          // (um is 0 for an entity without pairs)
+          unsigned m = um;
+          const float2 me = traj[q * 32 + ent];
+          while (m) {
+            float2 o[4];
+            float rs[4];
+            bool near[4];
+            int js[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int j = j0 + u, jj = j < p.N ? j : 0;
-                const bool in = j < p.N && j != ent && pair_active(L.kd, s_kind[jj]);
-                o[u] = traj[q * 32 + jj];
-                rs[u] = L.r + s_r[jj];
-                const float dx = me.x - o[u].x, dy = me.y - o[u].y;
-                near[u] = in && !(dx * dx + dy * dy > 1.0001f * (rs[u] * rs[u]));
-              }
+            for (int u = 0; u < 4; ++u) {
+              const bool in = m != 0u;
+              const int j = in ? __ffs(m) - 1 : 0;
+              m &= in ? m - 1u : 0u;
+              js[u] = j;
+              o[u] = traj[q * 32 + j];
+              rs[u] = L.r + s_r[j];
+              const float dx = me.x - o[u].x, dy = me.y - o[u].y;
+              near[u] = in && !(dx * dx + dy * dy > 1.0001f * (rs[u] * rs[u]));
+            }
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                float fx, fy, J[3];
-                if (near[u] && sphere_force(me.x, me.y, o[u].x, o[u].y, rs[u], p, fx, fy, J)) {
-                  const float2 lj = s_lf[j0 + u];
-                  const float dx = lfx - lj.x, dy = lfy - lj.y;
-                  lx += J[0] * dx + J[1] * dy;
-                  ly += J[1] * dx + J[2] * dy;
-                }
+            for (int u = 0; u < 4; ++u) {
+              float fx, fy, J[3];
+              if (near[u] && sphere_force(me.x, me.y, o[u].x, o[u].y, rs[u], p, fx, fy, J)) {
+                const float2 lj = s_lf[js[u]];
+                const float dx = lfx - lj.x, dy = lfy - lj.y;
+                lx += J[0] * dx + J[1] * dy;
+                ly += J[1] * dx + J[2] * dy;
               }
             }
           }

@@ -915,6 +915,12 @@ static int diff_setup(vmas_world *w, int32_t T, int32_t K, vmas::DiffParams *p) 
   p->ck = (float)((double)w->c * (double)w->k);
   p->inv_k = (float)(1.0 / (double)w->k);
   p->c = w->c;
+  // candidate masks of the pair sums: 4 x the step's list margin (the mask
+  // build is a pass over all N partners, cheaper than the step's list build,
+  // so a wider margin with fewer rebuilds pays; 2 x to 8 x measured within
+  // 1 % of each other on 4,096 envs of 8 agents + 2 landmarks, 1 x 16 %
+  // slower)
+  p->skin = 4.f * w->skin;
   const size_t EN = (size_t)w->E * w->N;
   p->px = w->planes;
   p->py = w->planes + EN;

@@ -104,6 +104,33 @@ def test_checkpoint_interval_does_not_change_gradient(vmas_lib):
     w.close()
 
 
+@pytest.mark.parametrize("dense,push", [(False, 1.0), (True, 1.0), (True, 6.0)])
+def test_candidate_skin_does_not_change_gradient(vmas_lib, dense, push):
+    """The pair sums visit each entity's candidate partners (pairs within
+    r_i + r_j + skin, rebuilt when a body may have moved half the skin) in
+    ascending order.  A pair left out cannot touch, so every skin gives
+    bitwise the loss and gradient of all pairs (skin 1e4: every pair, never
+    rebuilt); skin 0 and 1e-4 rebuild at almost every substep, and the
+    pushed scene (actions x 6) moves bodies through many rebuilds."""
+    from paper_2207_03530_b300.diff import rollout_loss
+
+    sc, w, act, goals = _setup(96, 21, dense, T=30)
+    g = torch.from_numpy(goals).cuda()
+    out = []
+    for skin in (1e4, None, 0.0, 1e-4, 0.05):
+        if skin is not None:
+            w.skin = skin
+        a = torch.from_numpy(act * np.float32(push)).cuda().requires_grad_(True)
+        loss = rollout_loss(w, a, g, ckpt_every=7)
+        loss.sum().backward()
+        out.append((loss.detach().cpu().numpy(), a.grad.cpu().numpy()))
+    for loss, grad in out[1:]:
+        assert np.array_equal(loss, out[0][0])
+        assert np.array_equal(grad, out[0][1])
+    assert np.abs(out[0][1]).max() > 0
+    w.close()
+
+
 def test_upstream_weights_scale_env_gradients(vmas_lib):
     """d(sum_e w_e loss_e)/d a = w_e d loss_e / d a, env by env."""
     from paper_2207_03530_b300.diff import rollout_loss
