@@ -239,9 +239,9 @@ __global__ void __launch_bounds__(128, 1)
           uint32_t w[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const float x0 = g.act ? gelu(v[2 * q]) : v[2 * q];
-            const float x1 = g.act ? gelu(v[2 * q + 1]) : v[2 * q + 1];
-            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            float2 x = make_float2(v[2 * q], v[2 * q + 1]);
+            if (g.act) x = gelu2(x);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
             w[q] = *reinterpret_cast<const uint32_t *>(&h);
           }
           if (g.vec_b) {

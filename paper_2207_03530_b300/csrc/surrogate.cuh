@@ -61,11 +61,97 @@ __device__ __forceinline__ float one_plus_erf(float x) {
   const float q = poly * t * __expf(-ax * ax);
   return x < 0.f ? q : 2.f - q;
 }
-// gelu(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative
-// (1 + erf(z / sqrt 2)) / 2 + z phi(z).
-__device__ __forceinline__ float gelu(float z) {
-  return 0.5f * z * one_plus_erf(z * 0.70710678118654752f);
+
+// The forward GELU, gelu(z) = z (1 + erf(z / sqrt 2)) / 2, from the same
+// approximation written for z: with a = |z| and x = a / sqrt 2,
+// z (1 + erf(x)) / 2 = max(z, 0) - a q / 2, and
+//   a q / 2 = a e^{-z^2 / 2} (t sum_i (a_i / 2) t^{i-1}),  t = 1 / (1 + (p / sqrt 2) a).
+// Two forms with bitwise the same values: gelu2 on packed pairs (the
+// two-wide FP32 add/mul/fma of sm_100 and later, each half rounded as its
+// scalar operation), gelu on one value with the same operations in the same
+// order (explicitly rounded, so never contracted differently).  The
+// exponential and reciprocal are the hardware approximations.
+constexpr float kGeluP = 0.3275911f * 0.70710678118654752f;
+constexpr float kGeluC = -0.72134752044448170f;  // -log2(e) / 2: e^{-z^2/2} = 2^{C z^2}
+constexpr float kGeluA1 = 0.254829592f * 0.5f, kGeluA2 = -0.284496736f * 0.5f,
+                kGeluA3 = 1.421413741f * 0.5f, kGeluA4 = -1.453152027f * 0.5f,
+                kGeluA5 = 1.061405429f * 0.5f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_splat(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 a = make_float2(fabsf(z.x), fabsf(z.y));
+  const float2 d = f2_fma(a, f2_splat(kGeluP), f2_splat(1.f));
+  const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  const float2 w = f2_mul(f2_mul(z, f2_splat(kGeluC)), z);
+  const float2 e = make_float2(ex2_approx(w.x), ex2_approx(w.y));
+  float2 poly = f2_fma(f2_splat(kGeluA5), t, f2_splat(kGeluA4));
+  poly = f2_fma(poly, t, f2_splat(kGeluA3));
+  poly = f2_fma(poly, t, f2_splat(kGeluA2));
+  poly = f2_fma(poly, t, f2_splat(kGeluA1));
+  const float2 r = f2_mul(f2_mul(a, e), f2_mul(poly, t));
+  return f2_sub(make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f)), r);
+}
+
+__device__ __forceinline__ float gelu(float z) {
+  const float a = fabsf(z);
+  const float t = rcp_approx(__fmaf_rn(a, kGeluP, 1.f));
+  const float e = ex2_approx(__fmul_rn(__fmul_rn(z, kGeluC), z));
+  float poly = __fmaf_rn(kGeluA5, t, kGeluA4);
+  poly = __fmaf_rn(poly, t, kGeluA3);
+  poly = __fmaf_rn(poly, t, kGeluA2);
+  poly = __fmaf_rn(poly, t, kGeluA1);
+  const float r = __fmul_rn(__fmul_rn(a, e), __fmul_rn(poly, t));
+  return __fsub_rn(fmaxf(z, 0.f), r);
+}
+
+// gelu'(z) = (1 + erf(z / sqrt 2)) / 2 + z phi(z).
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * one_plus_erf(z * 0.70710678118654752f) +
          z * 0.39894228040143268f * __expf(-0.5f * z * z);
@@ -463,9 +549,9 @@ __global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const flo
     const float m = __shfl_sync(0xffffffffu, mk, k);
     const int q = __shfl_sync(0xffffffffu, pk, k);
     if (m != 0.f) {
-      const float2 z = reinterpret_cast<const float2 *>(ze2c + (size_t)q * 64)[lane];
-      s0 += m * gelu(z.x);
-      s1 += m * gelu(z.y);
+      const float2 z = gelu2(reinterpret_cast<const float2 *>(ze2c + (size_t)q * 64)[lane]);
+      s0 += m * z.x;
+      s1 += m * z.y;
     }
   }
   bf16 *out = zin + r * 80;

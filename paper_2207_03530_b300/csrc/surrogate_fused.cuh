@@ -10,7 +10,7 @@
 // inlined) overflows the instruction cache and stalls on instruction fetch
 // most of the time, so the slot loop stays rolled (features of all slots are
 // staged in shared memory first) and GELU is one out-of-line routine taking
-// four values.
+// two packed pairs.
 //
 // Arithmetic is that of the layered path (surrogate.cuh): the same rounding
 // points, the same k order inside every dot product (k-tiles ascending), the
@@ -99,38 +99,50 @@ __device__ __forceinline__ void load_b1k2(uint32_t (&b)[4], const bf16 *W, int l
   ldsm_x4(b, W + (lane & 7) * ld + 16 * (kk + (m >> 1)) + (m & 1) * 8);
 }
 
-// GELU of four values, out of line (one copy of the GELU code in the kernel).
-__device__ __noinline__ float4 gelu4(float4 z) {
-  return make_float4(gelu(z.x), gelu(z.y), gelu(z.z), gelu(z.w));
+// bias + GELU on packed pairs, out of line (one copy of the GELU code in the
+// kernel); the pairs' dependency chains interleave inside the routine.
+// Four pairs: c0 (both of its pairs with bias b0) and c1 (bias b1).
+struct Gelu8 {
+  float4 lo, hi;
+};
+__device__ __noinline__ Gelu8 gelu_bias8(float4 c0, float4 c1, float2 b0, float2 b1) {
+  const float2 p0 = gelu2(f2_add(make_float2(c0.x, c0.y), b0));
+  const float2 p1 = gelu2(f2_add(make_float2(c0.z, c0.w), b0));
+  const float2 p2 = gelu2(f2_add(make_float2(c1.x, c1.y), b1));
+  const float2 p3 = gelu2(f2_add(make_float2(c1.z, c1.w), b1));
+  return {make_float4(p0.x, p0.y, p1.x, p1.y), make_float4(p2.x, p2.y, p3.x, p3.y)};
 }
-
-__device__ __noinline__ float2 gelu2(float2 z) { return make_float2(gelu(z.x), gelu(z.y)); }
+// Two pairs: (c.x, c.y) with bias b0, (c.z, c.w) with bias b1.
+__device__ __noinline__ float4 gelu_bias4(float4 c, float2 b0, float2 b1) {
+  const float2 lo = gelu2(f2_add(make_float2(c.x, c.y), b0));
+  const float2 hi = gelu2(f2_add(make_float2(c.z, c.w), b1));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
 
 // bias + GELU of two n-tiles (2 kk, 2 kk + 1), rounded into the A fragment of
 // k-tile kk of the next layer.
 __device__ __forceinline__ void gelu_pack(uint32_t (&a)[4], const float (&c0)[4],
                                           const float (&c1)[4], const float *bias, int kk, int t) {
-  const float b00 = bias[16 * kk + 2 * t], b01 = bias[16 * kk + 2 * t + 1];
-  const float b10 = bias[16 * kk + 8 + 2 * t], b11 = bias[16 * kk + 8 + 2 * t + 1];
-  const float4 g0 = gelu4(make_float4(c0[0] + b00, c0[1] + b01, c0[2] + b00, c0[3] + b01));
-  const float4 g1 = gelu4(make_float4(c1[0] + b10, c1[1] + b11, c1[2] + b10, c1[3] + b11));
-  a[0] = pack_bf16(g0.x, g0.y);
-  a[1] = pack_bf16(g0.z, g0.w);
-  a[2] = pack_bf16(g1.x, g1.y);
-  a[3] = pack_bf16(g1.z, g1.w);
+  const float2 b0 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 2 * t);
+  const float2 b1 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 8 + 2 * t);
+  const Gelu8 g = gelu_bias8(make_float4(c0[0], c0[1], c0[2], c0[3]),
+                             make_float4(c1[0], c1[1], c1[2], c1[3]), b0, b1);
+  a[0] = pack_bf16(g.lo.x, g.lo.y);
+  a[1] = pack_bf16(g.lo.z, g.lo.w);
+  a[2] = pack_bf16(g.hi.x, g.hi.y);
+  a[3] = pack_bf16(g.hi.z, g.hi.w);
 }
 
 // As gelu_pack for rows 0..7 only; rows 8..15 (not in use) become zero.
 __device__ __forceinline__ void gelu_pack_low(uint32_t (&a)[4], const float (&c0)[4],
                                               const float (&c1)[4], const float *bias, int kk,
                                               int t) {
-  const float b00 = bias[16 * kk + 2 * t], b01 = bias[16 * kk + 2 * t + 1];
-  const float b10 = bias[16 * kk + 8 + 2 * t], b11 = bias[16 * kk + 8 + 2 * t + 1];
-  const float2 g0 = gelu2(make_float2(c0[0] + b00, c0[1] + b01));
-  const float2 g1 = gelu2(make_float2(c1[0] + b10, c1[1] + b11));
-  a[0] = pack_bf16(g0.x, g0.y);
+  const float2 b0 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 2 * t);
+  const float2 b1 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 8 + 2 * t);
+  const float4 g = gelu_bias4(make_float4(c0[0], c0[1], c1[0], c1[1]), b0, b1);
+  a[0] = pack_bf16(g.x, g.y);
   a[1] = 0u;
-  a[2] = pack_bf16(g1.x, g1.y);
+  a[2] = pack_bf16(g.z, g.w);
   a[3] = 0u;
 }
 
@@ -331,20 +343,18 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
           mma_bf16(c0, he[kk], bq[0], bq[1]);
           mma_bf16(c1, he[kk], bq[2], bq[3]);
         }
-        const float b00 = be2[16 * jp + 2 * t], b01 = be2[16 * jp + 2 * t + 1];
-        const float b10 = be2[16 * jp + 8 + 2 * t], b11 = be2[16 * jp + 8 + 2 * t + 1];
+        const float2 b0 = *reinterpret_cast<const float2 *>(be2 + 16 * jp + 2 * t);
+        const float2 b1 = *reinterpret_cast<const float2 *>(be2 + 16 * jp + 8 + 2 * t);
         if (low_only) {
-          const float2 g0 = gelu2(make_float2(c0[0] + b00, c0[1] + b01));
-          const float2 g1 = gelu2(make_float2(c1[0] + b10, c1[1] + b11));
-          Macc[2 * jp][0] += mg ? g0.x : 0.f;
-          Macc[2 * jp][1] += mg ? g0.y : 0.f;
-          Macc[2 * jp + 1][0] += mg ? g1.x : 0.f;
-          Macc[2 * jp + 1][1] += mg ? g1.y : 0.f;
+          const float4 g = gelu_bias4(make_float4(c0[0], c0[1], c1[0], c1[1]), b0, b1);
+          Macc[2 * jp][0] += mg ? g.x : 0.f;
+          Macc[2 * jp][1] += mg ? g.y : 0.f;
+          Macc[2 * jp + 1][0] += mg ? g.z : 0.f;
+          Macc[2 * jp + 1][1] += mg ? g.w : 0.f;
         } else {
-          const float4 g0 =
-              gelu4(make_float4(c0[0] + b00, c0[1] + b01, c0[2] + b00, c0[3] + b01));
-          const float4 g1 =
-              gelu4(make_float4(c1[0] + b10, c1[1] + b11, c1[2] + b10, c1[3] + b11));
+          const Gelu8 g8 = gelu_bias8(make_float4(c0[0], c0[1], c0[2], c0[3]),
+                                      make_float4(c1[0], c1[1], c1[2], c1[3]), b0, b1);
+          const float4 g0 = g8.lo, g1 = g8.hi;
           Macc[2 * jp][0] += mg ? g0.x : 0.f;
           Macc[2 * jp][1] += mg ? g0.y : 0.f;
           Macc[2 * jp][2] += mg8 ? g0.z : 0.f;

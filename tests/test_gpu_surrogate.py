@@ -79,7 +79,8 @@ def test_gemm_matches_fp64(vmas_lib, ta, tb, M, N, K):
 
 
 def test_gelu_dense_grid(vmas_lib):
-    """The device GELU (1 + erf by Abramowitz & Stegun 7.1.26) against the
+    """The device GELU (1 + erf by Abramowitz & Stegun 7.1.26, the one-value
+    form in the warp-mma GEMM's epilogue) against the
     FP64 GELU on every bfloat16 value in [-8, 8]: an identity GEMM passes the
     values through exactly, and its GELU epilogue rounds to bfloat16.  The
     roundings agree except where the two values straddle a rounding
@@ -103,6 +104,33 @@ def test_gelu_dense_grid(vmas_lib):
     step = np.abs(ref_bf) * 2.0 ** -7
     assert np.all(np.abs(g - ref_bf) <= np.maximum(step, 2e-7))
     assert np.mean(g == ref_bf) >= 0.99
+
+
+def test_packed_and_scalar_gelu_agree_bitwise(vmas_lib):
+    """The tcgen05 GEMM's epilogue evaluates GELU on packed pairs (gelu2), the
+    warp-mma GEMM's one value at a time (gelu): the same explicitly rounded
+    operations, so on every bfloat16 value in [-8, 8] (passed through
+    exactly by an identity B) their bfloat16 outputs are bitwise equal."""
+    from paper_2207_03530_b300.surrogate import gemm_bf16, set_gemm_engine, tcgen05_gemm_launches
+
+    bits = np.arange(0, 1 << 16, dtype=np.uint32) << 16
+    v = bits.view(np.float32)
+    v = np.unique(v[np.isfinite(v) & (np.abs(v) <= 8.0)])
+    K = 16
+    A = np.zeros(-(-len(v) // K) * K, dtype=np.float32)
+    A[:len(v)] = v
+    a_dev = torch.tensor(A.reshape(-1, K), dtype=torch.bfloat16, device="cuda")
+    eye = torch.eye(K, dtype=torch.bfloat16, device="cuda")  # B[n][k], trans_b
+    n0 = tcgen05_gemm_launches()
+    out_tc, bf_tc = gemm_bf16(a_dev, eye, trans_b=True, gelu=True)
+    assert tcgen05_gemm_launches() == n0 + 1
+    set_gemm_engine("mma")
+    try:
+        out_mma, bf_mma = gemm_bf16(a_dev, eye, trans_b=True, gelu=True)
+    finally:
+        set_gemm_engine("tcgen05")
+    assert torch.equal(out_tc, a_dev.float()) and torch.equal(out_mma, a_dev.float())
+    assert torch.equal(bf_tc.view(torch.int16), bf_mma.view(torch.int16))
 
 
 @pytest.mark.parametrize("M,N,K", [(98304, 64, 16), (32768, 128, 80), (20000, 80, 128),
