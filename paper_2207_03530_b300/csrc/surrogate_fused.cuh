@@ -101,49 +101,81 @@ __device__ __forceinline__ void load_b1k2(uint32_t (&b)[4], const bf16 *W, int l
 
 // bias + GELU on packed pairs, out of line (one copy of the GELU code in the
 // kernel); the pairs' dependency chains interleave inside the routine.
-// Four pairs: c0 (both of its pairs with bias b0) and c1 (bias b1).
-struct Gelu8 {
-  float4 lo, hi;
+// Eight pairs: both pairs of c_i (the two rows of an n-tile fragment) with
+// bias b_i.
+struct Gelu16 {
+  float4 v[4];
 };
-__device__ __noinline__ Gelu8 gelu_bias8(float4 c0, float4 c1, float2 b0, float2 b1) {
+__device__ __noinline__ Gelu16 gelu_bias16(float4 c0, float4 c1, float4 c2, float4 c3, float2 b0,
+                                           float2 b1, float2 b2, float2 b3) {
   const float2 p0 = gelu2(f2_add(make_float2(c0.x, c0.y), b0));
   const float2 p1 = gelu2(f2_add(make_float2(c0.z, c0.w), b0));
   const float2 p2 = gelu2(f2_add(make_float2(c1.x, c1.y), b1));
   const float2 p3 = gelu2(f2_add(make_float2(c1.z, c1.w), b1));
+  const float2 p4 = gelu2(f2_add(make_float2(c2.x, c2.y), b2));
+  const float2 p5 = gelu2(f2_add(make_float2(c2.z, c2.w), b2));
+  const float2 p6 = gelu2(f2_add(make_float2(c3.x, c3.y), b3));
+  const float2 p7 = gelu2(f2_add(make_float2(c3.z, c3.w), b3));
+  return {{make_float4(p0.x, p0.y, p1.x, p1.y), make_float4(p2.x, p2.y, p3.x, p3.y),
+           make_float4(p4.x, p4.y, p5.x, p5.y), make_float4(p6.x, p6.y, p7.x, p7.y)}};
+}
+// Four pairs: (c0.x, c0.y) with bias b0, (c0.z, c0.w) with b1, (c1.x, c1.y)
+// with b2, (c1.z, c1.w) with b3.
+struct Gelu8 {
+  float4 lo, hi;
+};
+__device__ __noinline__ Gelu8 gelu_bias8(float4 c0, float4 c1, float2 b0, float2 b1, float2 b2,
+                                         float2 b3) {
+  const float2 p0 = gelu2(f2_add(make_float2(c0.x, c0.y), b0));
+  const float2 p1 = gelu2(f2_add(make_float2(c0.z, c0.w), b1));
+  const float2 p2 = gelu2(f2_add(make_float2(c1.x, c1.y), b2));
+  const float2 p3 = gelu2(f2_add(make_float2(c1.z, c1.w), b3));
   return {make_float4(p0.x, p0.y, p1.x, p1.y), make_float4(p2.x, p2.y, p3.x, p3.y)};
 }
-// Two pairs: (c.x, c.y) with bias b0, (c.z, c.w) with bias b1.
-__device__ __noinline__ float4 gelu_bias4(float4 c, float2 b0, float2 b1) {
-  const float2 lo = gelu2(f2_add(make_float2(c.x, c.y), b0));
-  const float2 hi = gelu2(f2_add(make_float2(c.z, c.w), b1));
-  return make_float4(lo.x, lo.y, hi.x, hi.y);
+
+__device__ __forceinline__ float4 f4(const float (&c)[4]) {
+  return make_float4(c[0], c[1], c[2], c[3]);
+}
+__device__ __forceinline__ float2 bias_pair(const float *bias, int n) {
+  return *reinterpret_cast<const float2 *>(bias + n);
 }
 
-// bias + GELU of two n-tiles (2 kk, 2 kk + 1), rounded into the A fragment of
-// k-tile kk of the next layer.
-__device__ __forceinline__ void gelu_pack(uint32_t (&a)[4], const float (&c0)[4],
-                                          const float (&c1)[4], const float *bias, int kk, int t) {
-  const float2 b0 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 2 * t);
-  const float2 b1 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 8 + 2 * t);
-  const Gelu8 g = gelu_bias8(make_float4(c0[0], c0[1], c0[2], c0[3]),
-                             make_float4(c1[0], c1[1], c1[2], c1[3]), b0, b1);
-  a[0] = pack_bf16(g.lo.x, g.lo.y);
-  a[1] = pack_bf16(g.lo.z, g.lo.w);
-  a[2] = pack_bf16(g.hi.x, g.hi.y);
-  a[3] = pack_bf16(g.hi.z, g.hi.w);
+// bias + GELU of the n-tiles 2 kk .. 2 kk + 3 (accumulators c[0..3]),
+// rounded into the A fragments of k-tiles kk and kk + 1 of the next layer.
+__device__ __forceinline__ void gelu_pack2(uint32_t (&a0)[4], uint32_t (&a1)[4],
+                                           const float (&c)[4][4], const float *bias, int kk,
+                                           int t) {
+  const Gelu16 g = gelu_bias16(f4(c[0]), f4(c[1]), f4(c[2]), f4(c[3]),
+                               bias_pair(bias, 16 * kk + 2 * t), bias_pair(bias, 16 * kk + 8 + 2 * t),
+                               bias_pair(bias, 16 * kk + 16 + 2 * t),
+                               bias_pair(bias, 16 * kk + 24 + 2 * t));
+  a0[0] = pack_bf16(g.v[0].x, g.v[0].y);
+  a0[1] = pack_bf16(g.v[0].z, g.v[0].w);
+  a0[2] = pack_bf16(g.v[1].x, g.v[1].y);
+  a0[3] = pack_bf16(g.v[1].z, g.v[1].w);
+  a1[0] = pack_bf16(g.v[2].x, g.v[2].y);
+  a1[1] = pack_bf16(g.v[2].z, g.v[2].w);
+  a1[2] = pack_bf16(g.v[3].x, g.v[3].y);
+  a1[3] = pack_bf16(g.v[3].z, g.v[3].w);
 }
 
-// As gelu_pack for rows 0..7 only; rows 8..15 (not in use) become zero.
-__device__ __forceinline__ void gelu_pack_low(uint32_t (&a)[4], const float (&c0)[4],
-                                              const float (&c1)[4], const float *bias, int kk,
-                                              int t) {
-  const float2 b0 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 2 * t);
-  const float2 b1 = *reinterpret_cast<const float2 *>(bias + 16 * kk + 8 + 2 * t);
-  const float4 g = gelu_bias4(make_float4(c0[0], c0[1], c1[0], c1[1]), b0, b1);
-  a[0] = pack_bf16(g.x, g.y);
-  a[1] = 0u;
-  a[2] = pack_bf16(g.z, g.w);
-  a[3] = 0u;
+// As gelu_pack2 for rows 0..7 only; rows 8..15 (not in use) become zero.
+__device__ __forceinline__ void gelu_pack2_low(uint32_t (&a0)[4], uint32_t (&a1)[4],
+                                               const float (&c)[4][4], const float *bias, int kk,
+                                               int t) {
+  const Gelu8 g = gelu_bias8(make_float4(c[0][0], c[0][1], c[1][0], c[1][1]),
+                             make_float4(c[2][0], c[2][1], c[3][0], c[3][1]),
+                             bias_pair(bias, 16 * kk + 2 * t), bias_pair(bias, 16 * kk + 8 + 2 * t),
+                             bias_pair(bias, 16 * kk + 16 + 2 * t),
+                             bias_pair(bias, 16 * kk + 24 + 2 * t));
+  a0[0] = pack_bf16(g.lo.x, g.lo.y);
+  a0[1] = 0u;
+  a0[2] = pack_bf16(g.lo.z, g.lo.w);
+  a0[3] = 0u;
+  a1[0] = pack_bf16(g.hi.x, g.hi.y);
+  a1[1] = 0u;
+  a1[2] = pack_bf16(g.hi.z, g.hi.w);
+  a1[3] = 0u;
 }
 
 // Dense layer of the node MLP: 16 rows, KT k-tiles of input fragments `in`,
@@ -153,16 +185,19 @@ __device__ __forceinline__ void node_layer(uint32_t (&out)[8][4], const uint32_t
                                            const bf16 *W, int ld, const float *bias, int lane,
                                            int t) {
 #pragma unroll
-  for (int kk = 0; kk < 8; ++kk) {
-    float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int kk = 0; kk < 8; kk += 2) {
+    float c[4][4] = {};
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
-      uint32_t bq[4];
-      load_b2(bq, W, ld, 2 * kk, q, lane);
-      mma_bf16(c0, in[q], bq[0], bq[1]);
-      mma_bf16(c1, in[q], bq[2], bq[3]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t bq[4];
+        load_b2(bq, W, ld, 2 * (kk + h), q, lane);
+        mma_bf16(c[2 * h], in[q], bq[0], bq[1]);
+        mma_bf16(c[2 * h + 1], in[q], bq[2], bq[3]);
+      }
     }
-    gelu_pack(out[kk], c0, c1, bias, kk, t);
+    gelu_pack2(out[kk], out[kk + 1], c, bias, kk, t);
   }
 }
 
@@ -323,46 +358,55 @@ __global__ void __launch_bounds__(kFusedWarpsPerCta * 32, 1) sur_fused_kernel(co
       load_a(ae, sedge + k * 16 * kLdX, kLdX, 0, lane);
       uint32_t he[4][4];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t bq[4];
-        load_b2(bq, We1, kLdE1, 2 * kk, 0, lane);
-        mma_bf16(c0, ae, bq[0], bq[1]);
-        mma_bf16(c1, ae, bq[2], bq[3]);
-        if (low_only) gelu_pack_low(he[kk], c0, c1, be1, kk, t);
-        else gelu_pack(he[kk], c0, c1, be1, kk, t);
+      for (int kk = 0; kk < 4; kk += 2) {
+        float c[4][4] = {};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t bq[4];
+          load_b2(bq, We1, kLdE1, 2 * (kk + h), 0, lane);
+          mma_bf16(c[2 * h], ae, bq[0], bq[1]);
+          mma_bf16(c[2 * h + 1], ae, bq[2], bq[3]);
+        }
+        if (low_only) gelu_pack2_low(he[kk], he[kk + 1], c, be1, kk, t);
+        else gelu_pack2(he[kk], he[kk + 1], c, be1, kk, t);
       }
       const bool mg = g < ck, mg8 = g + 8 < ck;
 #pragma unroll
-      for (int jp = 0; jp < 4; ++jp) {
-        float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int jp = 0; jp < 4; jp += 2) {
+        float c[4][4] = {};  // n-tiles 2 jp .. 2 jp + 3
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          uint32_t bq[4];
-          load_b2(bq, We2, kLdE2, 2 * jp, kk, lane);
-          mma_bf16(c0, he[kk], bq[0], bq[1]);
-          mma_bf16(c1, he[kk], bq[2], bq[3]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t bq[4];
+            load_b2(bq, We2, kLdE2, 2 * (jp + h), kk, lane);
+            mma_bf16(c[2 * h], he[kk], bq[0], bq[1]);
+            mma_bf16(c[2 * h + 1], he[kk], bq[2], bq[3]);
+          }
         }
-        const float2 b0 = *reinterpret_cast<const float2 *>(be2 + 16 * jp + 2 * t);
-        const float2 b1 = *reinterpret_cast<const float2 *>(be2 + 16 * jp + 8 + 2 * t);
+        const float2 b0 = bias_pair(be2, 16 * jp + 2 * t), b1 = bias_pair(be2, 16 * jp + 8 + 2 * t);
+        const float2 b2 = bias_pair(be2, 16 * jp + 16 + 2 * t);
+        const float2 b3 = bias_pair(be2, 16 * jp + 24 + 2 * t);
         if (low_only) {
-          const float4 g = gelu_bias4(make_float4(c0[0], c0[1], c1[0], c1[1]), b0, b1);
-          Macc[2 * jp][0] += mg ? g.x : 0.f;
-          Macc[2 * jp][1] += mg ? g.y : 0.f;
-          Macc[2 * jp + 1][0] += mg ? g.z : 0.f;
-          Macc[2 * jp + 1][1] += mg ? g.w : 0.f;
+          const Gelu8 g = gelu_bias8(make_float4(c[0][0], c[0][1], c[1][0], c[1][1]),
+                                     make_float4(c[2][0], c[2][1], c[3][0], c[3][1]), b0, b1, b2, b3);
+          const float4 gv[2] = {g.lo, g.hi};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            Macc[2 * (jp + h)][0] += mg ? gv[h].x : 0.f;
+            Macc[2 * (jp + h)][1] += mg ? gv[h].y : 0.f;
+            Macc[2 * (jp + h) + 1][0] += mg ? gv[h].z : 0.f;
+            Macc[2 * (jp + h) + 1][1] += mg ? gv[h].w : 0.f;
+          }
         } else {
-          const Gelu8 g8 = gelu_bias8(make_float4(c0[0], c0[1], c0[2], c0[3]),
-                                      make_float4(c1[0], c1[1], c1[2], c1[3]), b0, b1);
-          const float4 g0 = g8.lo, g1 = g8.hi;
-          Macc[2 * jp][0] += mg ? g0.x : 0.f;
-          Macc[2 * jp][1] += mg ? g0.y : 0.f;
-          Macc[2 * jp][2] += mg8 ? g0.z : 0.f;
-          Macc[2 * jp][3] += mg8 ? g0.w : 0.f;
-          Macc[2 * jp + 1][0] += mg ? g1.x : 0.f;
-          Macc[2 * jp + 1][1] += mg ? g1.y : 0.f;
-          Macc[2 * jp + 1][2] += mg8 ? g1.z : 0.f;
-          Macc[2 * jp + 1][3] += mg8 ? g1.w : 0.f;
+          const Gelu16 g = gelu_bias16(f4(c[0]), f4(c[1]), f4(c[2]), f4(c[3]), b0, b1, b2, b3);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            Macc[2 * jp + i][0] += mg ? g.v[i].x : 0.f;
+            Macc[2 * jp + i][1] += mg ? g.v[i].y : 0.f;
+            Macc[2 * jp + i][2] += mg8 ? g.v[i].z : 0.f;
+            Macc[2 * jp + i][3] += mg8 ? g.v[i].w : 0.f;
+          }
         }
       }
     }
