@@ -491,9 +491,12 @@ int vmas_sur_check(vmas_surrogate *sur, void *stream, int32_t *bits);
  * (FP32, may be NULL) into d_out_f32 [M][N] (may be NULL) and GELU (gelu != 0)
  * of it rounded into d_out_bf16 [M][N] (may be NULL).  splits > 1 sums K in
  * that many chunks (then no bias, GELU or bfloat16 output).  Untransposed A
- * with transposed B, K a multiple of 16 up to 128, N up to 128 and no split
+ * with transposed B, K a multiple of 8 up to 128, N up to 128 and no split
  * run on the tcgen05 GEMM (tensor memory accumulators, TMA-staged operands);
- * the rest on the warp-level mma GEMM.  It allocates temporary buffers,
+ * transposed A with untransposed B, M and N up to 128, K >= 4096, a split,
+ * no bias on the split-K tcgen05 weight-gradient GEMM (at most `splits`
+ * partial blocks; lda, ldb multiples of 8); the rest on the warp-level mma
+ * GEMM.  It allocates temporary buffers,
  * waits for `stream`, and returns VMAS_EDEVICE if a bounded wait of the
  * tcgen05 GEMM ran out. */
 int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N, int32_t K,

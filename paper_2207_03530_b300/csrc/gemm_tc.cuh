@@ -1,7 +1,7 @@
 // The surrogate's large GEMMs on the 5th-generation tensor cores (sm_103a):
 // C[m, n] = sum_k A[m][k] B[n][k] (+ bias[n], GELU on the bfloat16 copy),
 // bfloat16 operands, FP32 accumulation, for M up to millions of rows (16 per
-// env, or 96 for the edge MLP), N <= 128 and K <= 128 a multiple of 16: the
+// env, or 96 for the edge MLP), N <= 128 and K <= 128 a multiple of 8: the
 // shapes of the network's layers and of their input gradients.
 //
 //   operands  cp.async.bulk.tensor (TMA) 2D tiles into shared memory with the
@@ -9,7 +9,8 @@
 //             stages), the whole of B once per CTA; K past the tensor's end
 //             and rows past M are filled with zeros by the copy engine
 //   MMA       tcgen05.mma kind::f16 (M = 128, N = N rounded up to 16, K = 16
-//             per instruction), issued by one thread, accumulating in TMEM:
+//             per instruction; K = 8 reads zeros in 8..15), issued by one
+//             thread, accumulating in TMEM:
 //             two 128-column accumulators, so the MMAs of tile i + 1 run
 //             while the four warps read tile i back
 //   epilogue  tcgen05.ld (32 lanes x 32 bits: thread t of warp w owns TMEM
@@ -43,7 +44,7 @@ constexpr int kTcMinSmem = 80 * 1024;    // at most two CTAs per SM
 constexpr int kTcWaitTries = 1 << 20;    // polls of at most ~1 us each
 
 struct TcGemmArgs {
-  int M, N, K;         // N <= 128, K <= 128, K % 16 == 0
+  int M, N, K;         // N <= 128, K <= 128, K % 8 == 0
   int n_pad;           // N rounded up to 16: the MMA's N and B's box height
   int katoms;          // ceil(K / 64): 64-element K slices per tile
   const float *bias;   // [N] or null
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(128, 1)
   const int tiles = (g.M + kTcM - 1) / kTcM;
   const int mine = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const uint32_t a_bytes = (uint32_t)(KA * kTcAtom), b_bytes = (uint32_t)(KA * g.n_pad * 128);
-  const int ksteps = g.K / 16;
+  const int ksteps = (g.K + 15) / 16;  // K = 8: the copy engine zero-fills 8..15
   const uint32_t idesc = tc_idesc(kTcM, g.n_pad);
 
   if (tid == 0) {
@@ -288,6 +289,179 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------- weight gradients
+// C[m][n] = sum_k A[k][m] B[k][n] for the weight gradients of the network's
+// layers: M, N <= 128 (a layer's output and input widths), K = the rows of a
+// batch (millions).  Both operands are read as they lie in memory, rows of
+// the batch outermost: the MN-major operand layout of tcgen05.mma (both
+// transpose bits of the instruction descriptor set).
+//
+//   split K    CTA z sums the 64-row blocks [z kb, (z + 1) kb) of K (rows
+//              past K read as zeros) into a TMEM accumulator and writes its
+//              partial [M][N] to part + z M N; sum_partials_kernel adds them
+//   operands   per 64-row block, TMA tiles of 64 rows x 64 columns with the
+//              128-byte swizzle: two for A (columns 0-63, 64-127), one or two
+//              for B; the MN-major layout is then: a row of 64 elements per
+//              128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
+//              the second 64 columns one tile (8 KB) further (leading byte
+//              offset); three stages in a ring, each freed by the commit of
+//              the MMAs that read it
+//   MMA        M = 128 (A's columns; when M <= 64 the upper half of A stays
+//              zero), N = 64 or 128, K = 16 per instruction: 4 per block,
+//              each 16 rows (2 KB) further into the tiles
+//   waits      bounded as in gemm_tc_kernel (error word, drain, TMEM freed)
+constexpr int kWgStages = 3;
+constexpr int kWgTile = 64 * 128;                 // bytes of a 64 x 64 bfloat16 tile
+constexpr int kWgStage = 4 * kWgTile;             // A (2 tiles) + B (2 tiles)
+constexpr int kWgCols = 128;                      // TMEM columns (one accumulator)
+
+struct WgradArgs {
+  int M, N;        // M, N <= 128
+  int n_mma;       // 64 or 128
+  int kb;          // 64-row blocks per CTA
+  int nblocks;     // 64-row blocks of K
+  float *part;     // [gridDim.x][M][N]
+  int *err;
+  int vec;         // N % 4 == 0: 16-byte partial stores
+};
+
+__host__ __device__ inline int wgrad_smem_bytes() {
+  // 1 KB alignment, the stages, 8 KB of slack past the last tile, barriers
+  return 1024 + kWgStages * kWgStage + 8 * 1024 + 128;
+}
+
+// Shared-memory descriptor of an MN-major operand in the 128-byte swizzled
+// layout: 64-element rows 128 B apart, 8-row groups 1024 B apart (stride
+// byte offset), the next 64 columns `lbo` bytes on (leading byte offset).
+__device__ __forceinline__ uint64_t tc_desc_mn(uint32_t addr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+__global__ void __launch_bounds__(128, 2)
+    wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const WgradArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(
+      base + kWgStages * kWgStage + 8 * 1024);  // full[S], empty[S]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2 * kWgStages);
+  const uint32_t full0 = smem_u32(&bar[0]), empty0 = smem_u32(&bar[kWgStages]);
+  const int b0 = (int)blockIdx.x * g.kb;
+  const int nb = max(0, min(g.kb, g.nblocks - b0));  // this CTA's blocks
+  const bool two_a = g.M > 64, two_b = g.n_mma > 64;
+  const uint32_t bytes = (uint32_t)((two_a ? 2 : 1) + (two_b ? 2 : 1)) * kWgTile;
+  const uint32_t idesc = tc_idesc(kTcM, g.n_mma) | (1u << 15) | (1u << 16);
+
+  if (!two_a) {  // the upper 64 columns of A are zero in every stage
+    for (int s = 0; s < kWgStages; ++s)
+      for (int q = tid; q < kWgTile / 16; q += blockDim.x)
+        reinterpret_cast<uint4 *>(base + s * kWgStage + kWgTile)[q] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 2 * kWgStages; ++q) mbar_init(smem_u32(&bar[q]), 1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kWgCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  bool failed = false;
+  int loaded[kWgStages] = {}, committed[kWgStages] = {};
+  if (tid == 0) {
+    auto load = [&](int b) {  // block b of this CTA into stage b % S
+      const int s = b % kWgStages, row = 64 * (b0 + b);
+      unsigned char *st = base + s * kWgStage;
+      mbar_expect_tx(full0 + 8 * s, bytes);
+      tma_load_2d(smem_u32(st), &tmA, 0, row, full0 + 8 * s);
+      if (two_a) tma_load_2d(smem_u32(st + kWgTile), &tmA, 64, row, full0 + 8 * s);
+      tma_load_2d(smem_u32(st + 2 * kWgTile), &tmB, 0, row, full0 + 8 * s);
+      if (two_b) tma_load_2d(smem_u32(st + 3 * kWgTile), &tmB, 64, row, full0 + 8 * s);
+      ++loaded[s];
+    };
+    for (int b = 0; b < nb && b < kWgStages; ++b) load(b);
+    for (int b = 0; b < nb; ++b) {
+      const int s = b % kWgStages;
+      const uint32_t par = (uint32_t)((b / kWgStages) & 1);
+      if (!mbar_wait(full0 + 8 * s, par, kTcWaitTries)) { failed = true; break; }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(base + s * kWgStage), bb0 = a0 + 2 * kWgTile;
+      for (int j = 0; j < 4; ++j)
+        tc_mma(tmem, tc_desc_mn(a0 + 2048u * j, kWgTile), tc_desc_mn(bb0 + 2048u * j, kWgTile),
+               idesc, (b > 0 || j > 0) ? 1u : 0u);
+      tc_commit(empty0 + 8 * s);
+      ++committed[s];
+      if (b + kWgStages < nb) {
+        if (!mbar_wait(empty0 + 8 * s, par, kTcWaitTries)) { failed = true; break; }
+        load(b + kWgStages);
+      }
+    }
+    // the last block's MMAs complete before the accumulator is read
+    if (!failed && nb > 0) {
+      const int s = (nb - 1) % kWgStages;
+      if (!mbar_wait(empty0 + 8 * s, (uint32_t)(((nb - 1) / kWgStages) & 1), kTcWaitTries))
+        failed = true;
+    }
+    if (failed) {
+      atomicOr(g.err, VMAS_DEVERR_TIMEOUT);
+      for (int s = 0; s < kWgStages; ++s) {
+        if (loaded[s] > 0) mbar_wait(full0 + 8 * s, (uint32_t)((loaded[s] - 1) & 1), kTcWaitTries);
+        if (committed[s] > 0)
+          mbar_wait(empty0 + 8 * s, (uint32_t)((committed[s] - 1) & 1), kTcWaitTries);
+      }
+    }
+  }
+  tc_fence_before();
+  failed = __syncthreads_or(failed);
+  tc_fence_after();
+  if (!failed) {
+    // thread t of warp w: accumulator row m = 32 w + t, 16 columns at a time
+    const int m = warp * 32 + lane;
+    float *o = g.part + ((size_t)blockIdx.x * g.M + m) * g.N;
+    for (int c0 = 0; c0 < g.n_mma; c0 += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (nb == 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      }
+      if (m < g.M) {
+        if (g.vec && c0 + 16 <= g.N) {
+#pragma unroll
+          for (int q = 0; q < 16; q += 4)
+            *reinterpret_cast<float4 *>(o + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (c0 + q < g.N) o[c0 + q] = v[q];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols)
                  : "memory");
   }
 }

@@ -17,13 +17,14 @@ namespace sur = vmas::sur;
 using namespace vmas::sur;  // parameter offsets kOff*
 constexpr int kSurParams = vmas::sur::kParams;
 constexpr int kSplitCap = 256;  // split-K / column-sum partial blocks
+constexpr int kWgradMinK = 4096;  // K from which weight gradients take wgrad_tc_kernel
 
 // K-major (transposed) bfloat16 copies of the weights whose products with an
 // upstream gradient are plain row-major GEMMs in the backward, so that they
 // too run on the tensor-core GEMM: W2^T [128][128], W1^T [80][128],
 // We2^T [64][64].
 constexpr int kOffW2T = 0, kOffW1T = 128 * 128, kOffWe2T = kOffW1T + 80 * 128,
-              kTransposed = kOffWe2T + 64 * 64;
+              kOffW3T = kOffWe2T + 64 * 64, kTransposed = kOffW3T + 128 * 8;
 
 // 0: the tcgen05 GEMM wherever the shape allows it (the default);
 // 1: the warp-mma GEMM only (for A/B comparisons).  Process-wide.
@@ -150,7 +151,7 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
              const float *bias, int act, float *out_f32, int ldc_f, bf16 *out_bf, int ldc_b,
              int *err, int *rc) {
   auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-  if (g_gemm_engine != 0 || !err || M < 1 || N < 1 || N > 128 || K < 16 || K > 128 || K % 16 ||
+  if (g_gemm_engine != 0 || !err || M < 1 || N < 1 || N > 128 || K < 8 || K > 128 || K % 8 ||
       lda % 8 || ldb % 8 || !al16(A) || !al16(B))
     return false;
   sur::TcGemmArgs g{};
@@ -188,8 +189,63 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   return true;
 }
 
+// Weight gradient C [M][N] = A^T B with A [K][M], B [K][N] (row-major,
+// leading dimensions lda, ldb) on the tensor cores (wgrad_tc_kernel, split
+// K over at most `cap` CTAs, partials in `part` [cap][M][N], reduced into
+// out [M][N]); false (nothing enqueued) when the shape, the buffers or a
+// tensor map do not allow it.
+bool gemm_tc_wgrad(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const bf16 *B,
+                   int ldb, float *out, float *part, int cap, int *err, int *rc) {
+  auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+  if (g_gemm_engine != 0 || !err || !part || cap < 1 || M < 1 || N < 1 || M > 128 || N > 128 ||
+      K < kWgradMinK || lda < M || ldb < N || lda % 8 || ldb % 8 || !al16(A) || !al16(B))
+    return false;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  // MN-major tiles: 64 columns (128 bytes, the swizzle span) by 64 rows
+  auto map = [&](CUtensorMap *m, const bf16 *p, int width, int ld) {
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)K};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {64u, 64u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  CUtensorMap ma, mb;
+  if (!map(&ma, A, M, lda) || !map(&mb, B, N, ldb)) return false;
+  static const bool smem_ok = []() {
+    const bool ok = cudaFuncSetAttribute(sur::wgrad_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sur::wgrad_smem_bytes()) == cudaSuccess;
+    cudaGetLastError();
+    return ok;
+  }();
+  if (!smem_ok) return false;
+  sur::WgradArgs g{};
+  g.M = M;
+  g.N = N;
+  g.n_mma = N > 64 ? 128 : 64;
+  g.nblocks = (K + 63) / 64;
+  g.kb = (g.nblocks + cap - 1) / cap;              // blocks per CTA
+  const int grid = (g.nblocks + g.kb - 1) / g.kb;  // <= cap, every CTA has a block
+  g.part = part;
+  g.err = err;
+  g.vec = N % 4 == 0;
+  sur::wgrad_tc_kernel<<<grid, 128, sur::wgrad_smem_bytes(), st>>>(ma, mb, g);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    ++g_tc_launches;
+    const size_t MN = (size_t)M * N;
+    sur::sum_partials_kernel<<<blocks_for(MN, 256), 256, 0, st>>>(out, part, grid, MN);
+    e = cudaGetLastError();
+  }
+  *rc = e == cudaSuccess ? VMAS_OK : cuda_fail(e, "wgrad_tc_kernel launch");
+  return true;
+}
+
 // C = A B (+ bias, GELU): on the tensor cores (gemm_tc_kernel) when A is
-// row-major, B stored [N][K], K a multiple of 16 up to 128, N up to 128 and
+// row-major, B stored [N][K], K a multiple of 8 up to 128, N up to 128 and
 // an error word is given; otherwise through gemm_bf16_kernel (warp mma), where
 // `splits` > 1 sums K in chunks into part, reduced into out_f32 (then no
 // bias / bf16 output).
@@ -201,6 +257,10 @@ int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, 
     int rc = VMAS_OK;
     if (gemm_tc(st, M, N, K, A, lda, B, ldb, bias, act, out_f32, ldc_f, out_bf, ldc_b, err, &rc))
       return rc;
+  }
+  if (ta && !tb && splits > 1 && !bias && !act && !out_bf && out_f32 && ldc_f == N) {
+    int rc = VMAS_OK;
+    if (gemm_tc_wgrad(st, M, N, K, A, lda, B, ldb, out_f32, part, splits, err, &rc)) return rc;
   }
   sur::GemmArgs g{};
   g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
@@ -344,18 +404,18 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
   const int sp = kSplitCap;
   // output layer
   if ((rc = gemm(st, true, false, 8, 128, R, s->d_outbf, 8, s->h2, 128, nullptr, 0, G + kOffW3,
-                 128, nullptr, 0, s->part, sp)))
+                 128, nullptr, 0, s->part, sp, s->err)))
     return rc;
   if ((rc = col_sum(st, G + kOffb3, s->d_out, R, 8, s->part))) return rc;
-  if ((rc = gemm(st, false, false, R, 128, 8, s->d_outbf, 8, W + kOffW3, 128, nullptr, 0, s->g128,
-                 128, nullptr, 0)))
+  if ((rc = gemm(st, false, true, R, 128, 8, s->d_outbf, 8, s->pbfT + kOffW3T, 8, nullptr, 0,
+                 s->g128, 128, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // node layer 2
   sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
                                                                            s->z2, s->g128, s->g128bf);
   VMAS_CUDA(cudaGetLastError());
   if ((rc = gemm(st, true, false, 128, 128, R, s->g128bf, 128, s->h1, 128, nullptr, 0, G + kOffW2,
-                 128, nullptr, 0, s->part, sp)))
+                 128, nullptr, 0, s->part, sp, s->err)))
     return rc;
   if ((rc = col_sum(st, G + kOffb2, s->g128, R, 128, s->part))) return rc;
   if ((rc = gemm(st, false, true, R, 128, 128, s->g128bf, 128, s->pbfT + kOffW2T, 128, nullptr, 0,
@@ -366,7 +426,7 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
                                                                            s->z1, s->g128, s->g128bf);
   VMAS_CUDA(cudaGetLastError());
   if ((rc = gemm(st, true, false, 128, 80, R, s->g128bf, 128, s->zin, 80, nullptr, 0, G + kOffW1, 80,
-                 nullptr, 0, s->part, sp)))
+                 nullptr, 0, s->part, sp, s->err)))
     return rc;
   if ((rc = col_sum(st, G + kOffb1, s->g128, R, 128, s->part))) return rc;
   if ((rc = gemm(st, false, true, R, 80, 128, s->g128bf, 128, s->pbfT + kOffW1T, 128, nullptr, 0,
@@ -379,7 +439,7 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
       R, RE, s->d_zin, s->mask, s->emap, s->ze2, s->ge, s->gebf);
   VMAS_CUDA(cudaGetLastError());
   if ((rc = gemm(st, true, false, 64, 64, RE, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
-                 nullptr, 0, s->part, sp)))
+                 nullptr, 0, s->part, sp, s->err)))
     return rc;
   if ((rc = col_sum(st, G + kOffbe2, s->ge, RE, 64, s->part))) return rc;
   if ((rc = gemm(st, false, true, RE, 64, 64, s->gebf, 64, s->pbfT + kOffWe2T, 64, nullptr, 0, s->ge,
@@ -390,7 +450,7 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
                                                                           s->ze1, s->ge, s->gebf);
   VMAS_CUDA(cudaGetLastError());
   if ((rc = gemm(st, true, false, 64, 16, RE, s->gebf, 64, s->edgec, 16, nullptr, 0, G + kOffWe1, 16,
-                 nullptr, 0, s->part, sp)))
+                 nullptr, 0, s->part, sp, s->err)))
     return rc;
   return col_sum(st, G + kOffbe1, s->ge, RE, 64, s->part);
 }
@@ -450,9 +510,12 @@ __global__ void transpose_weights_kernel(const bf16 *w, bf16 *wt) {
   } else if (t < 128 * 128 + 128 * 80) {  // W1 [128][80]
     const int q = t - 128 * 128, o = q / 80, i = q % 80;
     wt[kOffW1T + i * 128 + o] = w[kOffW1 + q];
-  } else if (t < kTransposed) {  // We2 [64][64]
+  } else if (t < kOffW3T) {  // We2 [64][64]
     const int q = t - 128 * 128 - 128 * 80, o = q / 64, i = q % 64;
     wt[kOffWe2T + i * 64 + o] = w[kOffWe2 + q];
+  } else if (t < kTransposed) {  // W3 [8][128]
+    const int q = t - kOffW3T, o = q / 128, i = q % 128;
+    wt[kOffW3T + i * 8 + o] = w[kOffW3 + q];
   }
 }
 

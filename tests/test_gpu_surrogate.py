@@ -134,7 +134,7 @@ def test_packed_and_scalar_gelu_agree_bitwise(vmas_lib):
 
 
 @pytest.mark.parametrize("M,N,K", [(98304, 64, 16), (32768, 128, 80), (20000, 80, 128),
-                                   (4097, 64, 64), (300, 8, 128)])
+                                   (4097, 64, 64), (300, 8, 128), (5000, 128, 8)])
 def test_tcgen05_gemm_large_m(vmas_lib, M, N, K):
     """The tcgen05 GEMM at the layers' shapes (rows = 16 per env, 96 for the
     edge MLP; many 128-row tiles per CTA, a ragged last tile): every row
@@ -183,6 +183,38 @@ def test_gemm_split_k(vmas_lib, splits):
     ref = A.T @ B
     bound = 1e-5 * (np.abs(A.T) @ np.abs(B)) + 1e-7
     assert np.all(np.abs(out.cpu().numpy() - ref) <= bound)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 70000), (128, 80, 70001), (8, 128, 65536),
+                                   (64, 64, 80003), (64, 16, 4096)])
+def test_tcgen05_weight_gradient_gemm(vmas_lib, M, N, K):
+    """Weight gradients A^T B (A [K][M], B [K][N], the layers' widths, K the
+    batch rows) on the split-K tcgen05 kernel with MN-major operands:
+    against FP64 products (FP32 sums in the tensor core and over the
+    partials: within 1e-5 of sum |a||b|) and against the warp-mma GEMM."""
+    from paper_2207_03530_b300.surrogate import gemm_bf16, set_gemm_engine, tcgen05_gemm_launches
+
+    rng = np.random.default_rng(M + N + K)
+    A = _bf(rng.normal(0, 1, (K, M)))
+    B = _bf(rng.normal(0, 1, (K, N)))
+    a_dev = torch.tensor(A, dtype=torch.bfloat16, device="cuda")
+    b_dev = torch.tensor(B, dtype=torch.bfloat16, device="cuda")
+    n0 = tcgen05_gemm_launches()
+    out_tc, _ = gemm_bf16(a_dev, b_dev, trans_a=True, splits=256)
+    assert tcgen05_gemm_launches() == n0 + 1  # the tensor-core kernel ran
+    set_gemm_engine("mma")
+    try:
+        out_mma, _ = gemm_bf16(a_dev, b_dev, trans_a=True, splits=256)
+    finally:
+        set_gemm_engine("tcgen05")
+    assert tcgen05_gemm_launches() == n0 + 1
+    ref = A.T @ B
+    bound = 1e-5 * (np.abs(A.T) @ np.abs(B)) + 1e-7
+    got = out_tc.cpu().numpy()
+    print("\n[wgrad] %d x %d x %d: max err / bound %.3f"
+          % (M, N, K, float((np.abs(got - ref) / bound).max())))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.all(np.abs(got - out_mma.cpu().numpy()) <= 2 * bound)
 
 
 def _sur_scene(E, seed, crowd=1.0):
