@@ -576,14 +576,26 @@ __global__ void edge_back_compact_kernel(int R, int RE, const float *d_zin, cons
   d_zbf[t] = __float2bfloat16_rn(v);
 }
 
-// d_z = d_h * gelu'(z); FP32 copy (bias gradients) and bfloat16 copy (GEMMs).
-__global__ void gelu_back_kernel(size_t n, const float *d_h, const float *z, float *d_z32,
-                                 bf16 *d_zbf) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const float v = d_h[t] * gelu_grad(z[t]);
-  d_z32[t] = v;
-  d_zbf[t] = __float2bfloat16_rn(v);
+// d_z = d_h * gelu'(z) over [M][N] (N <= blockDim.x), with the bias
+// gradient's first stage fused in: block b takes rows [b chunk, (b + 1)
+// chunk), thread n column n, and writes the bfloat16 d_z (for the GEMMs) and
+// the column's partial sum of the FP32 d_z to part[b][n], summed in row
+// order as col_sum_kernel sums them (the FP32 d_z itself is not stored).
+__global__ void gelu_back_sum_kernel(int M, int N, const float *d_h, const float *z, bf16 *d_zbf,
+                                     float *part, int chunk) {
+  const int n = threadIdx.x;
+  if (n >= N) return;
+  const size_t r0 = (size_t)blockIdx.x * chunk;
+  const size_t r1 = min((size_t)M, r0 + chunk);
+  float s = 0.f;
+#pragma unroll 4
+  for (size_t m = r0; m < r1; ++m) {
+    const size_t t = m * N + n;
+    const float v = d_h[t] * gelu_grad(z[t]);
+    d_zbf[t] = __float2bfloat16_rn(v);
+    s += v;
+  }
+  part[(size_t)blockIdx.x * N + n] = s;
 }
 
 // Loss: the mean of (out - y)^2 over the outputs each row uses (4 for an

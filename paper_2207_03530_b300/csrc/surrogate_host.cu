@@ -294,12 +294,15 @@ int gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const bf16 *A, 
 
 // Column sums of x [M][N] (N <= 128) into out [N]: up to 4,096 row chunks
 // summed in parallel, then the chunk sums per column (two stages).
-int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *part) {
-  const int chunks = std::max(1, std::min(4096, (M + 255) / 256));
-  const int chunk = (M + chunks - 1) / chunks;
-  sur::col_sum_kernel<<<chunks, 128, 0, st>>>(part, x, M, N, chunk > 0 ? chunk : 1);
-  VMAS_CUDA(cudaGetLastError());
-  // second stage: 64 groups of chunks, then the groups
+// Row chunks of the first column-sum stage for M rows.
+void col_chunks(int M, int *chunks, int *chunk) {
+  *chunks = std::max(1, std::min(4096, (M + 255) / 256));
+  *chunk = std::max(1, (M + *chunks - 1) / *chunks);
+}
+
+// Stages 2 and 3 of a column sum: the `chunks` partial rows in part [chunks][N]
+// into 64 groups, then the groups into out [N].
+int col_sum_finish(cudaStream_t st, float *out, float *part, int chunks, int N) {
   const int groups = std::min(64, chunks), per = (chunks + groups - 1) / groups;
   float *part2 = part + (size_t)chunks * N;
   sur::col_sum_kernel<<<groups, 128, 0, st>>>(part2, part, chunks, N, per);
@@ -307,6 +310,25 @@ int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *pa
   sur::sum_partials_kernel<<<1, 128, 0, st>>>(out, part2, groups, (size_t)N);
   VMAS_CUDA(cudaGetLastError());
   return VMAS_OK;
+}
+
+// d_zbf = bf(d_h gelu'(z)) over [M][N] (N <= 128) and the bias gradient
+// out [N] = the column sums of the FP32 d_h gelu'(z), in col_sum's order.
+int gelu_back_sum(cudaStream_t st, float *out, const float *d_h, const float *z, bf16 *d_zbf,
+                  int M, int N, float *part) {
+  int chunks, chunk;
+  col_chunks(M, &chunks, &chunk);
+  sur::gelu_back_sum_kernel<<<chunks, 128, 0, st>>>(M, N, d_h, z, d_zbf, part, chunk);
+  VMAS_CUDA(cudaGetLastError());
+  return col_sum_finish(st, out, part, chunks, N);
+}
+
+int col_sum(cudaStream_t st, float *out, const float *x, int M, int N, float *part) {
+  int chunks, chunk;
+  col_chunks(M, &chunks, &chunk);
+  sur::col_sum_kernel<<<chunks, 128, 0, st>>>(part, x, M, N, chunk);
+  VMAS_CUDA(cudaGetLastError());
+  return col_sum_finish(st, out, part, chunks, N);
 }
 
 int sur_check(vmas_surrogate *s, vmas_world *w, const float *d_actions) {
@@ -386,7 +408,6 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
   const int R = E * nodes;
   const float count = (float)E * (float)(sur::kAgents * 4 + (nodes - sur::kAgents) * 6);
   float *G = s->grad;
-  const bf16 *W = s->pbf;
   VMAS_CUDA(cudaMemsetAsync(G, 0, kSurParams * sizeof(float), st));
   if (E == 0) {
     if (d_loss) VMAS_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
@@ -411,24 +432,19 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
                  s->g128, 128, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // node layer 2
-  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
-                                                                           s->z2, s->g128, s->g128bf);
-  VMAS_CUDA(cudaGetLastError());
+  // (the bias gradient first: the weight gradient reuses the partial buffer)
+  if ((rc = gelu_back_sum(st, G + kOffb2, s->g128, s->z2, s->g128bf, R, 128, s->part))) return rc;
   if ((rc = gemm(st, true, false, 128, 128, R, s->g128bf, 128, s->h1, 128, nullptr, 0, G + kOffW2,
                  128, nullptr, 0, s->part, sp, s->err)))
     return rc;
-  if ((rc = col_sum(st, G + kOffb2, s->g128, R, 128, s->part))) return rc;
   if ((rc = gemm(st, false, true, R, 128, 128, s->g128bf, 128, s->pbfT + kOffW2T, 128, nullptr, 0,
                  s->g128, 128, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // node layer 1
-  sur::gelu_back_kernel<<<blocks_for((size_t)R * 128, 256), 256, 0, st>>>((size_t)R * 128, s->g128,
-                                                                           s->z1, s->g128, s->g128bf);
-  VMAS_CUDA(cudaGetLastError());
+  if ((rc = gelu_back_sum(st, G + kOffb1, s->g128, s->z1, s->g128bf, R, 128, s->part))) return rc;
   if ((rc = gemm(st, true, false, 128, 80, R, s->g128bf, 128, s->zin, 80, nullptr, 0, G + kOffW1, 80,
                  nullptr, 0, s->part, sp, s->err)))
     return rc;
-  if ((rc = col_sum(st, G + kOffb1, s->g128, R, 128, s->part))) return rc;
   if ((rc = gemm(st, false, true, R, 80, 128, s->g128bf, 128, s->pbfT + kOffW1T, 128, nullptr, 0,
                  s->d_zin, 80, nullptr, 0, nullptr, 1, s->err)))
     return rc;
@@ -446,13 +462,9 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
                  64, nullptr, 0, nullptr, 1, s->err)))
     return rc;
   // edge layer 1
-  sur::gelu_back_kernel<<<blocks_for((size_t)RE * 64, 256), 256, 0, st>>>((size_t)RE * 64, s->ge,
-                                                                          s->ze1, s->ge, s->gebf);
-  VMAS_CUDA(cudaGetLastError());
-  if ((rc = gemm(st, true, false, 64, 16, RE, s->gebf, 64, s->edgec, 16, nullptr, 0, G + kOffWe1, 16,
-                 nullptr, 0, s->part, sp, s->err)))
-    return rc;
-  return col_sum(st, G + kOffbe1, s->ge, RE, 64, s->part);
+  if ((rc = gelu_back_sum(st, G + kOffbe1, s->ge, s->ze1, s->gebf, RE, 64, s->part))) return rc;
+  return gemm(st, true, false, 64, 16, RE, s->gebf, 64, s->edgec, 16, nullptr, 0, G + kOffWe1, 16,
+              nullptr, 0, s->part, sp, s->err);
 }
 
 int refresh_transposed(vmas_surrogate *s, cudaStream_t st);
