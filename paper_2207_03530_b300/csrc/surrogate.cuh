@@ -562,18 +562,29 @@ __global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const flo
 }
 
 // Edge-message gradient on the compact array: d_ze2[e][c] =
-// d_zin[r][16 + c] mask[rk] gelu'(ze2[e][c]), rk = emap[e], r = rk mod R.
-__global__ void edge_back_compact_kernel(int R, int RE, const float *d_zin, const float *mask,
-                                         const int *emap, const float *ze2c, float *d_z32,
-                                         bf16 *d_zbf) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)RE * 64) return;
-  const size_t e = t / 64;
-  const int c = (int)(t % 64);
-  const size_t rk = (size_t)emap[e], r = rk % (size_t)R;
-  const float v = d_zin[r * 80 + 16 + c] * mask[rk] * gelu_grad(ze2c[t]);
-  d_z32[t] = v;
-  d_zbf[t] = __float2bfloat16_rn(v);
+// d_zin[r][16 + c] mask[rk] gelu'(ze2[e][c]), rk = emap[e], r = rk mod R,
+// as bfloat16 (for the GEMMs), with the bias gradient's first column-sum
+// stage fused in as in gelu_back_sum_kernel: block b takes edge rows
+// [b chunk, (b + 1) chunk), thread c column c (blockDim.x >= 64), and writes
+// the column's partial sum of the FP32 values to part[b][c].
+__global__ void edge_back_sum_kernel(int R, int RE, const float *__restrict__ d_zin,
+                                     const float *__restrict__ mask, const int *__restrict__ emap,
+                                     const float *__restrict__ ze2c, bf16 *__restrict__ d_zbf,
+                                     float *__restrict__ part, int chunk) {
+  const int c = threadIdx.x;
+  if (c >= 64) return;
+  const size_t e0 = (size_t)blockIdx.x * chunk;
+  const size_t e1 = min((size_t)RE, e0 + chunk);
+  float s = 0.f;
+#pragma unroll 4
+  for (size_t e = e0; e < e1; ++e) {
+    const size_t t = e * 64 + c;
+    const size_t rk = (size_t)emap[e], r = rk % (size_t)R;
+    const float v = d_zin[r * 80 + 16 + c] * mask[rk] * gelu_grad(ze2c[t]);
+    d_zbf[t] = __float2bfloat16_rn(v);
+    s += v;
+  }
+  part[(size_t)blockIdx.x * 64 + c] = s;
 }
 
 // d_z = d_h * gelu'(z) over [M][N] (N <= blockDim.x), with the bias
@@ -581,8 +592,9 @@ __global__ void edge_back_compact_kernel(int R, int RE, const float *d_zin, cons
 // chunk), thread n column n, and writes the bfloat16 d_z (for the GEMMs) and
 // the column's partial sum of the FP32 d_z to part[b][n], summed in row
 // order as col_sum_kernel sums them (the FP32 d_z itself is not stored).
-__global__ void gelu_back_sum_kernel(int M, int N, const float *d_h, const float *z, bf16 *d_zbf,
-                                     float *part, int chunk) {
+__global__ void gelu_back_sum_kernel(int M, int N, const float *__restrict__ d_h,
+                                     const float *__restrict__ z, bf16 *__restrict__ d_zbf,
+                                     float *__restrict__ part, int chunk) {
   const int n = threadIdx.x;
   if (n >= N) return;
   const size_t r0 = (size_t)blockIdx.x * chunk;

@@ -318,7 +318,7 @@ int gelu_back_sum(cudaStream_t st, float *out, const float *d_h, const float *z,
                   int M, int N, float *part) {
   int chunks, chunk;
   col_chunks(M, &chunks, &chunk);
-  sur::gelu_back_sum_kernel<<<chunks, 128, 0, st>>>(M, N, d_h, z, d_zbf, part, chunk);
+  sur::gelu_back_sum_kernel<<<chunks, N <= 64 ? 64 : 128, 0, st>>>(M, N, d_h, z, d_zbf, part, chunk);
   VMAS_CUDA(cudaGetLastError());
   return col_sum_finish(st, out, part, chunks, N);
 }
@@ -451,13 +451,17 @@ int sur_backward(vmas_surrogate *s, int E, int nodes, int tw, const float *targe
   // edge layer 2 (through the masked sum), on the used slots of the forward
   const int RE = s->n_edges;
   if (RE == 0) return VMAS_OK;  // no edge: the edge weights' gradients stay zero
-  sur::edge_back_compact_kernel<<<blocks_for((size_t)RE * 64, 256), 256, 0, st>>>(
-      R, RE, s->d_zin, s->mask, s->emap, s->ze2, s->ge, s->gebf);
-  VMAS_CUDA(cudaGetLastError());
+  {  // the bias gradient first: the weight gradient reuses the partial buffer
+    int chunks, chunk;
+    col_chunks(RE, &chunks, &chunk);
+    sur::edge_back_sum_kernel<<<chunks, 64, 0, st>>>(R, RE, s->d_zin, s->mask, s->emap, s->ze2,
+                                                     s->gebf, s->part, chunk);
+    VMAS_CUDA(cudaGetLastError());
+    if ((rc = col_sum_finish(st, G + kOffbe2, s->part, chunks, 64))) return rc;
+  }
   if ((rc = gemm(st, true, false, 64, 64, RE, s->gebf, 64, s->he, 64, nullptr, 0, G + kOffWe2, 64,
                  nullptr, 0, s->part, sp, s->err)))
     return rc;
-  if ((rc = col_sum(st, G + kOffbe2, s->ge, RE, 64, s->part))) return rc;
   if ((rc = gemm(st, false, true, RE, 64, 64, s->gebf, 64, s->pbfT + kOffWe2T, 64, nullptr, 0, s->ge,
                  64, nullptr, 0, nullptr, 1, s->err)))
     return rc;
