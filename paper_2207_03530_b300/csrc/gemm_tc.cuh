@@ -12,10 +12,12 @@
 //             per instruction; K = 8 reads zeros in 8..15), issued by one
 //             thread, accumulating in TMEM:
 //             two 128-column accumulators, so the MMAs of tile i + 1 run
-//             while the four warps read tile i back
+//             while the eight warps read tile i back
 //   epilogue  tcgen05.ld (32 lanes x 32 bits: thread t of warp w owns TMEM
-//             lane 32 w + t, i.e. one output row), bias, FP32 and bfloat16
-//             stores, GELU (the same device function as the warp-mma path)
+//             lane 32 (w % 4) + t, i.e. one output row, and every other
+//             16-column chunk from chunk w / 4 on: two warps per lane
+//             quarter), bias, FP32 and bfloat16 stores, GELU (the same
+//             values as the warp-mma path's)
 //   waits     every mbarrier wait is bounded (about a second); a CTA whose
 //             wait runs out sets VMAS_DEVERR_TIMEOUT in the error word, waits
 //             (bounded) for its copies in flight, frees its TMEM and returns
@@ -42,6 +44,7 @@ constexpr int kTcAtom = kTcM * 128;      // bytes of a 64-wide K slice of a tile
 constexpr int kTcCols = 256;             // TMEM columns per CTA (two accumulators)
 constexpr int kTcMinSmem = 80 * 1024;    // at most two CTAs per SM
 constexpr int kTcWaitTries = 1 << 20;    // polls of at most ~1 us each
+constexpr int kTcThreads = 256;          // 8 warps: two per TMEM lane quarter in the epilogue
 
 struct TcGemmArgs {
   int M, N, K;         // N <= 128, K <= 128, K % 8 == 0
@@ -134,7 +137,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcGemmArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -214,9 +217,12 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     // stage s is free once its MMAs have completed: prefetch tile i + 2
     if (tid == 0 && i + 2 < mine) load_a(i + 2);
-    const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM + warp * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * 128);
-    for (int c0 = 0; c0 < g.n_pad; c0 += 16) {
+    // warp w reads TMEM lane quarter w % 4 (its rows) and every other
+    // 16-column chunk, starting at chunk w / 4
+    const int quarter = warp & 3;
+    const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM + quarter * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 128);
+    for (int c0 = 16 * (warp >> 2); c0 < g.n_pad; c0 += 32) {
       float v[16];
       tc_ld16(tbase + (uint32_t)c0, v);
       if (row < g.M && c0 + 16 <= g.N) {

@@ -182,7 +182,7 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   if (!n_sm) return false;
   const int tiles = (M + sur::kTcM - 1) / sur::kTcM;
   const int grid = std::min(tiles, 2 * n_sm);
-  sur::gemm_tc_kernel<<<grid, 128, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, g);
+  sur::gemm_tc_kernel<<<grid, sur::kTcThreads, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, g);
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++g_tc_launches;
   *rc = e == cudaSuccess ? VMAS_OK : cuda_fail(e, "gemm_tc_kernel launch");
