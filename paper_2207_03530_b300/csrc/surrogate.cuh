@@ -531,34 +531,50 @@ __global__ void edge_compact_kernel(size_t n, int *pos, const int *bsum, const b
 }
 
 // zin[r] = [node[r], bf(sum_k mask[k][r] gelu(ze2[pos[k][r]]))] (80 wide), the
-// messages read from the compact edge array in slot order.  One warp per
-// row: lanes 0..K-1 fetch the slots' flags and positions (shared by
-// shuffles), lane l sums message columns 2l and 2l + 1 (one 8-byte load per
-// slot in use) and lanes 0..7 copy the node features.
+// messages read from the compact edge array in slot order.  Eight lanes per
+// row (four rows per warp): lanes 0..K-1 of the row's group fetch the
+// slots' flags and positions (shared by width-8 shuffles), lane l sums
+// message columns 8l .. 8l + 7 (two 16-byte loads per slot in use) and
+// lanes 0..1 copy the node features.
 __global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const float *ze2c,
                                                                 const float *mask, const int *pos,
                                                                 const bf16 *node, bf16 *zin) {
-  const size_t r = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= (size_t)R) return;  // whole warps leave together
-  const float mk = lane < kK ? mask[(size_t)lane * R + r] : 0.f;
-  const int pk = lane < kK && mk != 0.f ? pos[(size_t)lane * R + r] : 0;
-  float s0 = 0.f, s1 = 0.f;
+  static_assert(kK <= 8, "slot flags are shared within 8 lanes");
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t r = t >> 3;
+  const int ql = threadIdx.x & 7;
+  if ((t & ~(size_t)31) >> 3 >= (size_t)R) return;  // whole warps leave together
+  const bool valid = r < (size_t)R;                  // later groups may have no row
+  const float mk = valid && ql < kK ? mask[(size_t)ql * R + r] : 0.f;
+  const int pk = valid && ql < kK && mk != 0.f ? pos[(size_t)ql * R + r] : 0;
+  float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < kK; ++k) {
-    const float m = __shfl_sync(0xffffffffu, mk, k);
-    const int q = __shfl_sync(0xffffffffu, pk, k);
+    const float m = __shfl_sync(0xffffffffu, mk, k, 8);
+    const int q = __shfl_sync(0xffffffffu, pk, k, 8);
     if (m != 0.f) {
-      const float2 z = gelu2(reinterpret_cast<const float2 *>(ze2c + (size_t)q * 64)[lane]);
-      s0 += m * z.x;
-      s1 += m * z.y;
+      const float4 *src = reinterpret_cast<const float4 *>(ze2c + (size_t)q * 64) + 2 * ql;
+      const float4 za = src[0], zb = src[1];
+      const float2 g[4] = {gelu2(make_float2(za.x, za.y)), gelu2(make_float2(za.z, za.w)),
+                           gelu2(make_float2(zb.x, zb.y)), gelu2(make_float2(zb.z, zb.w))};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        sum[2 * i] += m * g[i].x;
+        sum[2 * i + 1] += m * g[i].y;
+      }
     }
   }
+  if (!valid) return;
   bf16 *out = zin + r * 80;
-  if (lane < 8)
-    reinterpret_cast<uint32_t *>(out)[lane] = reinterpret_cast<const uint32_t *>(node + r * 16)[lane];
-  const __nv_bfloat162 h = __floats2bfloat162_rn(s0, s1);
-  reinterpret_cast<__nv_bfloat162 *>(out + 16)[lane] = h;
+  if (ql < 2)
+    reinterpret_cast<uint4 *>(out)[ql] = reinterpret_cast<const uint4 *>(node + r * 16)[ql];
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(sum[2 * i], sum[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  reinterpret_cast<uint4 *>(out + 16)[ql] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Edge-message gradient on the compact array: d_ze2[e][c] =
