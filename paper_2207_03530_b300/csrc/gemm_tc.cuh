@@ -16,8 +16,9 @@
 //   epilogue  tcgen05.ld (32 lanes x 32 bits: thread t of warp w owns TMEM
 //             lane 32 (w % 4) + t, i.e. one output row, and every other
 //             16-column chunk from chunk w / 4 on: two warps per lane
-//             quarter), bias, FP32 and bfloat16 stores, GELU (the same
-//             values as the warp-mma path's)
+//             quarter), bias, GELU (the same values as the warp-mma
+//             path's); FP32 and bfloat16 outputs staged per warp in shared
+//             memory (32 rows x 32 bytes) and written by TMA tensor stores
 //   waits     every mbarrier wait is bounded (about a second); a CTA whose
 //             wait runs out sets VMAS_DEVERR_TIMEOUT in the error word, waits
 //             (bounded) for its copies in flight, frees its TMEM and returns
@@ -58,14 +59,44 @@ struct TcGemmArgs {
   int ldc_b;
   int *err;            // device error word
   int vec_f, vec_b;    // 16-byte stores allowed (aligned bases, ldc_f % 4, ldc_b % 8)
+  int tma_st;          // outputs written by TMA stores (tensor maps tmC, tmCb valid)
   // test hook: extra transaction bytes every A-tile barrier waits for, which
   // no copy delivers, so that its bounded wait runs out (0 in normal use)
   uint32_t extra_tx;
 };
 
+// Output staging for TMA stores: per warp, 32 rows x 32 bytes (a 16-column
+// bfloat16 chunk, or half of a 16-column FP32 chunk), 128-byte aligned after
+// the barriers.
+constexpr int kTcStage = 32 * 32;
+__host__ __device__ inline int tc_stage_offset(int katoms, int n_pad) {
+  return (2 * katoms * kTcAtom + katoms * n_pad * 128 + 64 + 127) & ~127;
+}
 __host__ __device__ inline int tc_smem_bytes(int katoms, int n_pad) {
-  const int b = 1024 + 2 * katoms * kTcAtom + katoms * n_pad * 128 + 64;
+  const int b = 1024 + tc_stage_offset(katoms, n_pad) + (kTcThreads / 32) * kTcStage;
   return b < kTcMinSmem ? kTcMinSmem : b;
+}
+
+// TMA tensor store of a 2D box from shared memory (bulk group of the
+// issuing thread), the group's commit, and the waits for its shared-memory
+// reads and for its completion.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte
@@ -139,6 +170,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCb,
                    const TcGemmArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -150,6 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned long long *bar =
       reinterpret_cast<unsigned long long *>(sB + KA * g.n_pad * 128);  // full[2], done[2], bfull
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 5);
+  unsigned char *stg = base + tc_stage_offset(KA, g.n_pad) + warp * kTcStage;  // this warp's
   const uint32_t full0 = smem_u32(&bar[0]), done0 = smem_u32(&bar[2]), bfull = smem_u32(&bar[4]);
   const int tiles = (g.M + kTcM - 1) / kTcM;
   const int mine = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -225,7 +258,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int c0 = 16 * (warp >> 2); c0 < g.n_pad; c0 += 32) {
       float v[16];
       tc_ld16(tbase + (uint32_t)c0, v);
-      if (row < g.M && c0 + 16 <= g.N) {
+      if (g.tma_st) {
+        // the whole warp: bias, then each output through the warp's staging
+        // rows (lane l: row l, 32 bytes) and one TMA store of 32 rows x 32
+        // bytes, which the copy engine clips at M and N
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (g.bias && c0 + q < g.N) v[q] += g.bias[c0 + q];
+        const int y0 = row - lane;
+        const bool any = y0 < g.M;  // the warp's rows are not all past M
+        uint4 *srow = reinterpret_cast<uint4 *>(stg + lane * 32);
+        if (g.out_f32 && any) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (c0 + 8 * h < g.N) {  // the same for the whole warp
+              if (lane == 0) bulk_wait_read();  // the buffer's previous store has read it
+              __syncwarp();
+              srow[0] = make_uint4(__float_as_uint(v[8 * h]), __float_as_uint(v[8 * h + 1]),
+                                   __float_as_uint(v[8 * h + 2]), __float_as_uint(v[8 * h + 3]));
+              srow[1] = make_uint4(__float_as_uint(v[8 * h + 4]), __float_as_uint(v[8 * h + 5]),
+                                   __float_as_uint(v[8 * h + 6]), __float_as_uint(v[8 * h + 7]));
+              fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_2d(&tmC, smem_u32(stg), c0 + 8 * h, y0);
+                bulk_commit();
+              }
+            }
+          }
+        }
+        if (g.out_bf && any) {
+          uint32_t w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float2 x = make_float2(v[2 * q], v[2 * q + 1]);
+            if (g.act) x = gelu2(x);
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(x.x, x.y);
+            w[q] = *reinterpret_cast<const uint32_t *>(&hh);
+          }
+          if (lane == 0) bulk_wait_read();
+          __syncwarp();
+          srow[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          srow[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmCb, smem_u32(stg), c0, y0);
+            bulk_commit();
+          }
+        }
+      } else if (row < g.M && c0 + 16 <= g.N) {
         // a full 16-column block of this row
 #pragma unroll
         for (int q = 0; q < 16; ++q)
@@ -278,6 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_before();
     __syncthreads();  // both TMEM accumulators' readers are done before the next MMAs
   }
+  if (g.tma_st && lane == 0) bulk_wait_all();  // this warp's stores are done with its buffer
   if (failed) {
     if (tid == 0) {
       atomicOr(g.err, VMAS_DEVERR_TIMEOUT);

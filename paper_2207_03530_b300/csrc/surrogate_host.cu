@@ -166,6 +166,24 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   g.extra_tx = g_tc_timeout_test.load() ? 16u : 0u;
   CUtensorMap ma, mb;
   if (!tc_map(&ma, A, M, K, lda, sur::kTcM) || !tc_map(&mb, B, N, K, ldb, g.n_pad)) return false;
+  // outputs through TMA stores: boxes of 32 rows x 32 bytes, no swizzle
+  CUtensorMap mc{}, mcb{};
+  {
+    EncodeTiledFn fn = encode_tiled();
+    auto out_map = [&](CUtensorMap *m, void *p, CUtensorMapDataType t, int esize, int ld) {
+      if (!fn || !al16(p) || ((size_t)ld * esize) % 16) return false;
+      const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+      const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+      const cuuint32_t box[2] = {(cuuint32_t)(32 / esize), 32u};
+      const cuuint32_t estr[2] = {1u, 1u};
+      return fn(m, t, 2, p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    g.tma_st = (out_f32 || out_bf) &&
+               (!out_f32 || out_map(&mc, out_f32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ldc_f)) &&
+               (!out_bf || out_map(&mcb, out_bf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ldc_b));
+  }
   // SM count and the shared-memory opt-in, once per process (thread-safe
   // initialisation); 0 when the set-up failed (the warp-mma GEMM then runs)
   static const int n_sm = []() {
@@ -182,7 +200,8 @@ bool gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const
   if (!n_sm) return false;
   const int tiles = (M + sur::kTcM - 1) / sur::kTcM;
   const int grid = std::min(tiles, 2 * n_sm);
-  sur::gemm_tc_kernel<<<grid, sur::kTcThreads, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, g);
+  sur::gemm_tc_kernel<<<grid, sur::kTcThreads, sur::tc_smem_bytes(g.katoms, g.n_pad), st>>>(ma, mb, mc,
+                                                                                          mcb, g);
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++g_tc_launches;
   *rc = e == cudaSuccess ? VMAS_OK : cuda_fail(e, "gemm_tc_kernel launch");
