@@ -745,7 +745,7 @@ __global__ void predict_kernel(const PredictArgs a) {
 // walls at +-1, by at most `limit` (sphere-sphere by centre distance,
 // sphere-box and box-box by the step's own narrow phase, a box against a
 // wall by its deepest corner); every other env is left unchanged and
-// appended to `list`.  One thread per env.
+// appended to `list`.
 struct PredictBoxArgs {
   int E, N;
   float *px, *py, *vx, *vy, *th, *om;
@@ -755,71 +755,100 @@ struct PredictBoxArgs {
   int *list, *list_len;
 };
 
-__global__ void predict_box_kernel(const PredictBoxArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.E) return;
-  constexpr int NB = kNodesMax;
+// One warp per env: lane i < 20 predicts node i (as the state it would
+// write), the 210 overlap tests (16 agents against the walls, 120 agent
+// pairs, 64 agent-box pairs, 4 boxes' corners against the walls, 6 box
+// pairs) are spread over the lanes, and the deepest overlap is their
+// maximum (any order gives the same value).  Over the limit, or any
+// prediction not finite: the env is listed for the plain step; otherwise
+// the lanes write the predicted state.
+constexpr int kPbWarps = 8;  // envs per 256-thread block
+__global__ void __launch_bounds__(256) predict_box_kernel(const PredictBoxArgs a) {
+  constexpr int NB = kNodesMax, NA = kAgents, NX = NB - NA;  // 20 nodes: 16 agents, 4 boxes
+  constexpr int kWall = NA, kPair = kWall + NA * (NA - 1) / 2, kSB = kPair + NA * NX,
+                kCorner = kSB + NX, kItems = kCorner + NX * (NX - 1) / 2;
+  __shared__ float4 s_pose[kPbWarps][NB];  // predicted x, y, cos theta, sin theta
+  __shared__ float2 s_half[kPbWarps][NB];  // radius (agents) or half sizes (boxes)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * kPbWarps + w;
+  if (e >= a.E) return;  // whole warps leave together
   const size_t b = (size_t)e * a.N;
-  float px[NB], py[NB], pvx[NB], pvy[NB], pth[NB], pom[NB];
-  bool finite = true;
-  for (int i = 0; i < NB; ++i) {
-    const float *o = a.out + ((size_t)e * NB + i) * 8;
-    px[i] = fmaf(kXScale, o[0], a.px[b + i]);
-    py[i] = fmaf(kXScale, o[1], a.py[b + i]);
-    pvx[i] = fmaf(kVScale, o[2], a.vx[b + i]);
-    pvy[i] = fmaf(kVScale, o[3], a.vy[b + i]);
-    pth[i] = i < kAgents ? a.th[b + i] : fmaf(kThScale, o[4], a.th[b + i]);
-    pom[i] = i < kAgents ? a.om[b + i] : fmaf(kOmScale, o[5], a.om[b + i]);
-    finite = finite && isfinite(px[i]) && isfinite(py[i]) && isfinite(pvx[i]) &&
-             isfinite(pvy[i]) && isfinite(pth[i]) && isfinite(pom[i]);
+  float px = 0.f, py = 0.f, pvx = 0.f, pvy = 0.f, pth = 0.f, pom = 0.f;
+  bool fin = true;
+  if (lane < NB) {
+    const float *o = a.out + ((size_t)e * NB + lane) * 8;
+    px = fmaf(kXScale, o[0], a.px[b + lane]);
+    py = fmaf(kXScale, o[1], a.py[b + lane]);
+    pvx = fmaf(kVScale, o[2], a.vx[b + lane]);
+    pvy = fmaf(kVScale, o[3], a.vy[b + lane]);
+    pth = lane < NA ? a.th[b + lane] : fmaf(kThScale, o[4], a.th[b + lane]);
+    pom = lane < NA ? a.om[b + lane] : fmaf(kOmScale, o[5], a.om[b + lane]);
+    fin = isfinite(px) && isfinite(py) && isfinite(pvx) && isfinite(pvy) && isfinite(pth) &&
+          isfinite(pom);
+    const float4 pr = a.param[b + lane];
+    const bool box = lane >= NA;
+    s_pose[w][lane] = make_float4(px, py, box ? cosf(pth) : 1.f, box ? sinf(pth) : 0.f);
+    s_half[w][lane] = make_float2(pr.z, pr.w);
   }
+  const bool finite = __all_sync(0xffffffffu, fin);
+  __syncwarp();
   float worst = -1e30f;  // deepest predicted overlap
   if (finite) {
-    for (int i = 0; i < NB; ++i) {
-      const float4 pi = a.param[b + i];
-      if (i < kAgents) {
-        worst = fmaxf(worst, wall_overlap(px[i], py[i], pi.z));
-        for (int j = i + 1; j < kAgents; ++j) {
-          const float dx = px[i] - px[j], dy = py[i] - py[j];
-          worst = fmaxf(worst, pi.z + a.param[b + j].z -
-                                   sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+    const float4 *P = s_pose[w];
+    const float2 *H = s_half[w];
+    for (int it = lane; it < kItems; it += 32) {
+      if (it < kWall) {
+        worst = fmaxf(worst, wall_overlap(P[it].x, P[it].y, H[it].x));
+      } else if (it < kPair) {
+        int q = it - kWall, i = 0;
+        while (q >= NA - 1 - i) {  // pair q of (i, j), i < j < 16, i-major
+          q -= NA - 1 - i;
+          ++i;
         }
-        for (int j = kAgents; j < NB; ++j) {
-          const float4 pj = a.param[b + j];
-          Hit h;
-          if (hit_sphere_box(px[i], py[i], pi.z, px[j], py[j], cosf(pth[j]), sinf(pth[j]), pj.z,
-                             pj.w, h))
-            worst = fmaxf(worst, -h.g);
-        }
-      } else {
-        const float c = cosf(pth[i]), sn = sinf(pth[i]);
+        const int j = i + 1 + q;
+        const float dx = P[i].x - P[j].x, dy = P[i].y - P[j].y;
+        worst = fmaxf(worst, H[i].x + H[j].x - sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+      } else if (it < kSB) {
+        const int i = (it - kPair) / NX, j = NA + (it - kPair) % NX;
+        Hit h;
+        if (hit_sphere_box(P[i].x, P[i].y, H[i].x, P[j].x, P[j].y, P[j].z, P[j].w, H[j].x, H[j].y,
+                           h))
+          worst = fmaxf(worst, -h.g);
+      } else if (it < kCorner) {
+        const int i = NA + it - kSB;
+        const float c = P[i].z, sn = P[i].w;
         for (int k = 0; k < 4; ++k) {  // corners against the walls
-          const float u = (k == 1 || k == 2) ? pi.z : -pi.z, v = k >= 2 ? pi.w : -pi.w;
-          const float cx = px[i] + u * c - v * sn, cy = py[i] + u * sn + v * c;
+          const float u = (k == 1 || k == 2) ? H[i].x : -H[i].x, v = k >= 2 ? H[i].y : -H[i].y;
+          const float cx = P[i].x + u * c - v * sn, cy = P[i].y + u * sn + v * c;
           worst = fmaxf(worst, fmaxf(fmaxf(cx - 1.f, -1.f - cx), fmaxf(cy - 1.f, -1.f - cy)));
         }
-        for (int j = i + 1; j < NB; ++j) {
-          const float4 pj = a.param[b + j];
-          const Poly A{px[i], py[i], c, sn, pi.z, pi.w, true};
-          const Poly B{px[j], py[j], cosf(pth[j]), sinf(pth[j]), pj.z, pj.w, true};
-          Hit h;
-          if (hit_poly_poly(A, B, h)) worst = fmaxf(worst, -h.g);
+      } else {
+        int q = it - kCorner, i = 0;
+        while (q >= NX - 1 - i) {  // box pair q of (i, j), i < j < 4
+          q -= NX - 1 - i;
+          ++i;
         }
+        const int bi = NA + i, bj = NA + i + 1 + q;
+        const Poly A{P[bi].x, P[bi].y, P[bi].z, P[bi].w, H[bi].x, H[bi].y, true};
+        const Poly B{P[bj].x, P[bj].y, P[bj].z, P[bj].w, H[bj].x, H[bj].y, true};
+        Hit h;
+        if (hit_poly_poly(A, B, h)) worst = fmaxf(worst, -h.g);
       }
     }
   }
+  for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
   if (!finite || !(worst <= a.limit)) {
-    a.list[atomicAdd(a.list_len, 1)] = e;
+    if (lane == 0) a.list[atomicAdd(a.list_len, 1)] = e;
     return;
   }
-  for (int i = 0; i < NB; ++i) {
-    a.px[b + i] = px[i];
-    a.py[b + i] = py[i];
-    a.vx[b + i] = pvx[i];
-    a.vy[b + i] = pvy[i];
-    if (i >= kAgents) {
-      a.th[b + i] = pth[i];
-      a.om[b + i] = pom[i];
+  if (lane < NB) {
+    a.px[b + lane] = px;
+    a.py[b + lane] = py;
+    a.vx[b + lane] = pvx;
+    a.vy[b + lane] = pvy;
+    if (lane >= NA) {
+      a.th[b + lane] = pth;
+      a.om[b + lane] = pom;
     }
   }
 }

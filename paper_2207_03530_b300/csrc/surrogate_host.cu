@@ -756,7 +756,7 @@ int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, floa
     a.th = w->planes + 4 * EN; a.om = w->planes + 5 * EN;
     a.param = w->param; a.out = s->out; a.limit = limit;
     a.list = s->list; a.list_len = s->list_len;
-    sur::predict_box_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
+    sur::predict_box_kernel<<<blocks_for(E, sur::kPbWarps), sur::kPbWarps * 32, 0, st>>>(a);
     VMAS_CUDA(cudaGetLastError());
   } else {
     if ((rc = sur_forward(s, w, d_actions, false, st))) return rc;
