@@ -690,6 +690,8 @@ __global__ void adam_kernel(size_t n, float *p, const float *g, float *m, float 
 // predicted agents overlap each other, or the walls at +-1, by at most
 // `limit`; every other env is left unchanged and appended to `list` (the
 // plain step then advances it).  One thread per env.
+constexpr int kPbWarps = 8;  // envs per 256-thread block of the prediction checks
+
 struct PredictArgs {
   int E, N;
   float *px, *py, *vx, *vy;
@@ -704,39 +706,53 @@ __device__ __forceinline__ float wall_overlap(float x, float y, float r) {
   return fmaxf(fmaxf(x + r - 1.f, r - 1.f - x), fmaxf(y + r - 1.f, r - 1.f - y));
 }
 
-__global__ void predict_kernel(const PredictArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.E) return;
+// One warp per env: lane i < 16 predicts agent i and its wall overlap, the
+// 120 agent pairs are spread over the lanes, and a warp max gives the
+// deepest overlap (any order gives the same value).
+__global__ void __launch_bounds__(256) predict_kernel(const PredictArgs a) {
+  constexpr int NA = kAgents, kPairs = NA * (NA - 1) / 2;
+  __shared__ float4 s_p[kPbWarps][NA];  // predicted x, y and the radius
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * kPbWarps + w;
+  if (e >= a.E) return;  // whole warps leave together
   const size_t b = (size_t)e * a.N;
-  float px[kAgents], py[kAgents], pvx[kAgents], pvy[kAgents], rr[kAgents];
+  float px = 0.f, py = 0.f, pvx = 0.f, pvy = 0.f;
   float worst = -1e30f;  // deepest predicted overlap
-  bool finite = true;
-#pragma unroll
-  for (int i = 0; i < kAgents; ++i) {
-    const float *o = a.out + ((size_t)e * kAgents + i) * 8;
-    px[i] = fmaf(kXScale, o[0], a.px[b + i]);
-    py[i] = fmaf(kXScale, o[1], a.py[b + i]);
-    pvx[i] = fmaf(kVScale, o[2], a.vx[b + i]);
-    pvy[i] = fmaf(kVScale, o[3], a.vy[b + i]);
-    rr[i] = a.param[b + i].z;
-    finite = finite && isfinite(px[i]) && isfinite(py[i]) && isfinite(pvx[i]) && isfinite(pvy[i]);
-    worst = fmaxf(worst, wall_overlap(px[i], py[i], rr[i]));
+  bool fin = true;
+  if (lane < NA) {
+    const float *o = a.out + ((size_t)e * NA + lane) * 8;
+    px = fmaf(kXScale, o[0], a.px[b + lane]);
+    py = fmaf(kXScale, o[1], a.py[b + lane]);
+    pvx = fmaf(kVScale, o[2], a.vx[b + lane]);
+    pvy = fmaf(kVScale, o[3], a.vy[b + lane]);
+    const float r = a.param[b + lane].z;
+    fin = isfinite(px) && isfinite(py) && isfinite(pvx) && isfinite(pvy);
+    worst = wall_overlap(px, py, r);
+    s_p[w][lane] = make_float4(px, py, r, 0.f);
   }
-  for (int i = 0; i < kAgents; ++i)
-    for (int j = i + 1; j < kAgents; ++j) {
-      const float dx = px[i] - px[j], dy = py[i] - py[j];
-      worst = fmaxf(worst, rr[i] + rr[j] - sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+  const bool finite = __all_sync(0xffffffffu, fin);
+  __syncwarp();
+  const float4 *P = s_p[w];
+  for (int q0 = lane; q0 < kPairs; q0 += 32) {
+    int q = q0, i = 0;
+    while (q >= NA - 1 - i) {  // pair q of (i, j), i < j < 16, i-major
+      q -= NA - 1 - i;
+      ++i;
     }
+    const int j = i + 1 + q;
+    const float dx = P[i].x - P[j].x, dy = P[i].y - P[j].y;
+    worst = fmaxf(worst, P[i].z + P[j].z - sqrtf(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))));
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
   if (!finite || !(worst <= a.limit)) {
-    a.list[atomicAdd(a.list_len, 1)] = e;
+    if (lane == 0) a.list[atomicAdd(a.list_len, 1)] = e;
     return;
   }
-#pragma unroll
-  for (int i = 0; i < kAgents; ++i) {
-    a.px[b + i] = px[i];
-    a.py[b + i] = py[i];
-    a.vx[b + i] = pvx[i];
-    a.vy[b + i] = pvy[i];
+  if (lane < NA) {
+    a.px[b + lane] = px;
+    a.py[b + lane] = py;
+    a.vx[b + lane] = pvx;
+    a.vy[b + lane] = pvy;
   }
 }
 
@@ -762,7 +778,6 @@ struct PredictBoxArgs {
 // maximum (any order gives the same value).  Over the limit, or any
 // prediction not finite: the env is listed for the plain step; otherwise
 // the lanes write the predicted state.
-constexpr int kPbWarps = 8;  // envs per 256-thread block
 __global__ void __launch_bounds__(256) predict_box_kernel(const PredictBoxArgs a) {
   constexpr int NB = kNodesMax, NA = kAgents, NX = NB - NA;  // 20 nodes: 16 agents, 4 boxes
   constexpr int kWall = NA, kPair = kWall + NA * (NA - 1) / 2, kSB = kPair + NA * NX,

@@ -766,7 +766,7 @@ int vmas_sur_step(vmas_surrogate *s, vmas_world *w, const float *d_actions, floa
     a.px = w->planes; a.py = w->planes + EN; a.vx = w->planes + 2 * EN; a.vy = w->planes + 3 * EN;
     a.param = w->param; a.out = s->out; a.limit = limit;
     a.list = s->list; a.list_len = s->list_len;
-    sur::predict_kernel<<<blocks_for(E, 128), 128, 0, st>>>(a);
+    sur::predict_kernel<<<blocks_for(E, sur::kPbWarps), sur::kPbWarps * 32, 0, st>>>(a);
     VMAS_CUDA(cudaGetLastError());
   }
   // the plain step for the listed envs (grid sized for all; blocks past the
