@@ -289,11 +289,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 }
 
 // Sum of `splits` partial [M][N] blocks (split-K reduction).
-__global__ void sum_partials_kernel(float *out, const float *part, int splits, size_t MN) {
+__global__ void sum_partials_kernel(float *__restrict__ out, const float *__restrict__ part,
+                                    int splits, size_t MN) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= MN) return;
   float s = 0.f;
-  for (int z = 0; z < splits; ++z) s += part[(size_t)z * MN + t];
+#pragma unroll 16
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * MN + t];  // in split order
   out[t] = s;
 }
 
@@ -592,7 +594,7 @@ __global__ void edge_back_sum_kernel(int R, int RE, const float *__restrict__ d_
   const size_t e0 = (size_t)blockIdx.x * chunk;
   const size_t e1 = min((size_t)RE, e0 + chunk);
   float s = 0.f;
-#pragma unroll 4
+#pragma unroll 8
   for (size_t e = e0; e < e1; ++e) {
     const size_t t = e * 64 + c;
     const size_t rk = (size_t)emap[e], r = rk % (size_t)R;
