@@ -511,8 +511,9 @@ int vmas_debug_gemm_bf16(int32_t trans_a, int32_t trans_b, int32_t M, int32_t N,
 int vmas_debug_gemm_engine(int32_t engine, int64_t *tc_launches);
 
 /* Test hook for failure detection without a GPU fault, process-wide: while
- * `on` is set, every A-tile barrier of the tcgen05 GEMM expects 16
- * transaction bytes that no copy delivers, so its bounded waits run out (in
+ * `on` is set, every A-tile barrier of the tcgen05 GEMM, and every stage
+ * barrier of the split-K weight-gradient GEMM, expects 16 transaction bytes
+ * that no copy delivers, so its bounded waits run out (in
  * a few seconds); each CTA then sets VMAS_DEVERR_TIMEOUT, waits (bounded) for
  * its copies, frees its tensor memory and returns, leaving its rows
  * unwritten, and the context stays usable.  Off by default. */

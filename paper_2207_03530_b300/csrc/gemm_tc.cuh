@@ -416,6 +416,7 @@ struct WgradArgs {
   float *part;     // [gridDim.x][M][N]
   int *err;
   int vec;         // N % 4 == 0: 16-byte partial stores
+  uint32_t extra_tx;  // test hook, as in TcGemmArgs (0 in normal use)
 };
 
 __host__ __device__ inline int wgrad_smem_bytes() {
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(128, 2)
     auto load = [&](int b) {  // block b of this CTA into stage b % S
       const int s = b % kWgStages, row = 64 * (b0 + b);
       unsigned char *st = base + s * kWgStage;
-      mbar_expect_tx(full0 + 8 * s, bytes);
+      mbar_expect_tx(full0 + 8 * s, bytes + g.extra_tx);
       tma_load_2d(smem_u32(st), &tmA, 0, row, full0 + 8 * s);
       if (two_a) tma_load_2d(smem_u32(st + kWgTile), &tmA, 64, row, full0 + 8 * s);
       tma_load_2d(smem_u32(st + 2 * kWgTile), &tmB, 0, row, full0 + 8 * s);

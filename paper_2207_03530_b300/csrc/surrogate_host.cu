@@ -251,6 +251,7 @@ bool gemm_tc_wgrad(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda,
   g.part = part;
   g.err = err;
   g.vec = N % 4 == 0;
+  g.extra_tx = g_tc_timeout_test.load() ? 16u : 0u;
   sur::wgrad_tc_kernel<<<grid, 128, sur::wgrad_smem_bytes(), st>>>(ma, mb, g);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {

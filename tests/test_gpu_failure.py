@@ -67,3 +67,31 @@ def test_tcgen05_gemm_wait_runs_out_and_context_survives(vmas_lib):
     ref = a.double() @ bt.double().T
     assert torch.allclose(out.double(), ref, rtol=0, atol=1e-4 * float(ref.abs().max()))
     assert tcgen05_gemm_launches() == n0 + 2
+
+
+def test_tcgen05_weight_gradient_wait_runs_out_and_context_survives(vmas_lib):
+    """The split-K weight-gradient kernel under the same hook: every CTA's
+    first copy barrier waits for 16 bytes that never come, its bounded wait
+    runs out, the error word is set, and the next call is correct."""
+    import numpy as np
+
+    from paper_2207_03530_b300.surrogate import gemm_bf16, tcgen05_gemm_launches
+
+    rng = np.random.default_rng(1)
+    a = torch.tensor(rng.normal(0, 1, (4096, 64)), dtype=torch.bfloat16, device="cuda")
+    b = torch.tensor(rng.normal(0, 1, (4096, 64)), dtype=torch.bfloat16, device="cuda")
+    n0 = tcgen05_gemm_launches()
+    _lib.check(vmas_lib.vmas_debug_gemm_timeout(1))
+    try:
+        with pytest.raises(_lib.VmasError) as ei:
+            gemm_bf16(a, b, trans_a=True, splits=64)
+        assert ei.value.code == _lib.VMAS_EDEVICE
+        assert "bits 8" in str(ei.value), str(ei.value)
+    finally:
+        _lib.check(vmas_lib.vmas_debug_gemm_timeout(0))
+    assert tcgen05_gemm_launches() == n0 + 1
+    out, _ = gemm_bf16(a, b, trans_a=True, splits=64)
+    ref = a.double().T @ b.double()
+    assert torch.allclose(out.double(), ref, rtol=0, atol=1e-4 * float(ref.abs().max()))
+    assert tcgen05_gemm_launches() == n0 + 2
+
