@@ -12,10 +12,10 @@
 //             per instruction; K = 8 reads zeros in 8..15), issued by one
 //             thread, accumulating in TMEM:
 //             two 128-column accumulators, so the MMAs of tile i + 1 run
-//             while the eight warps read tile i back
+//             while the twelve warps read tile i back
 //   epilogue  tcgen05.ld (32 lanes x 32 bits: thread t of warp w owns TMEM
-//             lane 32 (w % 4) + t, i.e. one output row, and every other
-//             16-column chunk from chunk w / 4 on: two warps per lane
+//             lane 32 (w % 4) + t, i.e. one output row, and every third
+//             16-column chunk from chunk w / 4 on: three warps per lane
 //             quarter), bias, GELU (the same values as the warp-mma
 //             path's); FP32 and bfloat16 outputs staged per warp in shared
 //             memory (32 rows x 32 bytes) and written by TMA tensor stores
@@ -45,7 +45,7 @@ constexpr int kTcAtom = kTcM * 128;      // bytes of a 64-wide K slice of a tile
 constexpr int kTcCols = 256;             // TMEM columns per CTA (two accumulators)
 constexpr int kTcMinSmem = 80 * 1024;    // at most two CTAs per SM
 constexpr int kTcWaitTries = 1 << 20;    // polls of at most ~1 us each
-constexpr int kTcThreads = 256;          // 8 warps: two per TMEM lane quarter in the epilogue
+constexpr int kTcThreads = 384;          // 12 warps: three per TMEM lane quarter in the epilogue
 
 struct TcGemmArgs {
   int M, N, K;         // N <= 128, K <= 128, K % 8 == 0
@@ -168,7 +168,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCb,
                    const TcGemmArgs g) {
@@ -250,12 +250,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     // stage s is free once its MMAs have completed: prefetch tile i + 2
     if (tid == 0 && i + 2 < mine) load_a(i + 2);
-    // warp w reads TMEM lane quarter w % 4 (its rows) and every other
+    // warp w reads TMEM lane quarter w % 4 (its rows) and every third
     // 16-column chunk, starting at chunk w / 4
     const int quarter = warp & 3;
     const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kTcM + quarter * 32 + lane;
     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 128);
-    for (int c0 = 16 * (warp >> 2); c0 < g.n_pad; c0 += 32) {
+    for (int c0 = 16 * (warp >> 2); c0 < g.n_pad; c0 += 16 * (kTcThreads / 128)) {
       float v[16];
       tc_ld16(tbase + (uint32_t)c0, v);
       if (g.tma_st) {
