@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const int ksteps = (g.K + 15) / 16;  // K = 8: the copy engine zero-fills 8..15
   const uint32_t idesc = tc_idesc(kTcM, g.n_pad);
 
+  // the bias, zero past N, for the TMA-store epilogue's 16-byte reads
+  __shared__ __align__(16) float s_bias[128];
+  for (int q = tid; q < 128; q += blockDim.x) s_bias[q] = g.bias && q < g.N ? g.bias[q] : 0.f;
   if (tid == 0) {
     for (int q = 0; q < 5; ++q) mbar_init(smem_u32(&bar[q]), 1);
   }
@@ -262,9 +265,17 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         // the whole warp: bias, then each output through the warp's staging
         // rows (lane l: row l, 32 bytes) and one TMA store of 32 rows x 32
         // bytes, which the copy engine clips at M and N
+        if (g.bias) {  // (no bias: nothing added, so -0 stays -0)
+          const float4 *b4 = reinterpret_cast<const float4 *>(s_bias + c0);
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (g.bias && c0 + q < g.N) v[q] += g.bias[c0 + q];
+          for (int q = 0; q < 4; ++q) {
+            const float4 b = b4[q];
+            v[4 * q] += b.x;
+            v[4 * q + 1] += b.y;
+            v[4 * q + 2] += b.z;
+            v[4 * q + 3] += b.w;
+          }
+        }
         const int y0 = row - lane;
         const bool any = y0 < g.M;  // the warp's rows are not all past M
         uint4 *srow = reinterpret_cast<uint4 *>(stg + lane * 32);
