@@ -533,36 +533,43 @@ __global__ void edge_compact_kernel(size_t n, int *pos, const int *bsum, const b
 }
 
 // zin[r] = [node[r], bf(sum_k mask[k][r] gelu(ze2[pos[k][r]]))] (80 wide), the
-// messages read from the compact edge array in slot order.  Eight lanes per
-// row (four rows per warp): lanes 0..K-1 of the row's group fetch the
-// slots' flags and positions (shared by width-8 shuffles), lane l sums
-// message columns 8l .. 8l + 7 (two 16-byte loads per slot in use) and
-// lanes 0..1 copy the node features.
+// messages read from the compact edge array in slot order.  Four lanes per
+// row (eight rows per warp): lane l of the row's group fetches the flags and
+// positions of slots l and l + 4 (shared by width-4 shuffles), sums message
+// columns 16l .. 16l + 15 (four 16-byte loads per slot in use), and lanes
+// 0..1 copy the node features.
 __global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const float *ze2c,
                                                                 const float *mask, const int *pos,
                                                                 const bf16 *node, bf16 *zin) {
-  static_assert(kK <= 8, "slot flags are shared within 8 lanes");
+  static_assert(kK <= 8, "slot flags are shared within 4 lanes, two each");
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t r = t >> 3;
-  const int ql = threadIdx.x & 7;
-  if ((t & ~(size_t)31) >> 3 >= (size_t)R) return;  // whole warps leave together
+  const size_t r = t >> 2;
+  const int ql = threadIdx.x & 3;
+  if ((t & ~(size_t)31) >> 2 >= (size_t)R) return;  // whole warps leave together
   const bool valid = r < (size_t)R;                  // later groups may have no row
-  const float mk = valid && ql < kK ? mask[(size_t)ql * R + r] : 0.f;
-  const int pk = valid && ql < kK && mk != 0.f ? pos[(size_t)ql * R + r] : 0;
-  float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float mk0 = valid && ql < kK ? mask[(size_t)ql * R + r] : 0.f;
+  const int pk0 = valid && ql < kK && mk0 != 0.f ? pos[(size_t)ql * R + r] : 0;
+  const float mk1 = valid && ql + 4 < kK ? mask[(size_t)(ql + 4) * R + r] : 0.f;
+  const int pk1 = valid && ql + 4 < kK && mk1 != 0.f ? pos[(size_t)(ql + 4) * R + r] : 0;
+  float sum[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sum[q] = 0.f;
 #pragma unroll
   for (int k = 0; k < kK; ++k) {
-    const float m = __shfl_sync(0xffffffffu, mk, k, 8);
-    const int q = __shfl_sync(0xffffffffu, pk, k, 8);
+    const float m = __shfl_sync(0xffffffffu, k < 4 ? mk0 : mk1, k & 3, 4);
+    const int q = __shfl_sync(0xffffffffu, k < 4 ? pk0 : pk1, k & 3, 4);
     if (m != 0.f) {
-      const float4 *src = reinterpret_cast<const float4 *>(ze2c + (size_t)q * 64) + 2 * ql;
-      const float4 za = src[0], zb = src[1];
-      const float2 g[4] = {gelu2(make_float2(za.x, za.y)), gelu2(make_float2(za.z, za.w)),
-                           gelu2(make_float2(zb.x, zb.y)), gelu2(make_float2(zb.z, zb.w))};
+      const float4 *src = reinterpret_cast<const float4 *>(ze2c + (size_t)q * 64) + 4 * ql;
+      float4 z[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        sum[2 * i] += m * g[i].x;
-        sum[2 * i + 1] += m * g[i].y;
+      for (int u = 0; u < 4; ++u) z[u] = src[u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 g0 = gelu2(make_float2(z[u].x, z[u].y)), g1 = gelu2(make_float2(z[u].z, z[u].w));
+        sum[4 * u] += m * g0.x;
+        sum[4 * u + 1] += m * g0.y;
+        sum[4 * u + 2] += m * g1.x;
+        sum[4 * u + 3] += m * g1.y;
       }
     }
   }
@@ -570,13 +577,15 @@ __global__ void __launch_bounds__(256) aggregate_compact_kernel(int R, const flo
   bf16 *out = zin + r * 80;
   if (ql < 2)
     reinterpret_cast<uint4 *>(out)[ql] = reinterpret_cast<const uint4 *>(node + r * 16)[ql];
-  uint32_t w[4];
+  uint32_t w[8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(sum[2 * i], sum[2 * i + 1]);
     w[i] = *reinterpret_cast<const uint32_t *>(&h);
   }
-  reinterpret_cast<uint4 *>(out + 16)[ql] = make_uint4(w[0], w[1], w[2], w[3]);
+  uint4 *dst = reinterpret_cast<uint4 *>(out + 16) + 2 * ql;
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 // Edge-message gradient on the compact array: d_ze2[e][c] =

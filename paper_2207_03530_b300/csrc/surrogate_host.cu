@@ -407,7 +407,7 @@ int sur_forward(vmas_surrogate *s, vmas_world *w, const float *d_actions, bool t
                    64, nullptr, 0, nullptr, 1, s->err)))
       return rc;
   }
-  sur::aggregate_compact_kernel<<<blocks_for((size_t)R * 8, 256), 256, 0, st>>>(
+  sur::aggregate_compact_kernel<<<blocks_for((size_t)R * 4, 256), 256, 0, st>>>(
       R, s->ze2, s->mask, s->epos, s->node, s->zin);
   VMAS_CUDA(cudaGetLastError());
   // node MLP
